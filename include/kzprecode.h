@@ -1,0 +1,196 @@
+/*
+ * libkzprecode -- Kaczmarz-type RZF precoders for near-field multiuser
+ * systems with spatial non-stationarity, on one GB300 (sm_103a).
+ *
+ * The library solves, for each right-hand side s (a K-vector of symbols),
+ *
+ *     x = H^H (H H^H + xi I)^-1 s                        (eq. (precoding), Thm. 1)
+ *
+ * without forming or inverting the Gram matrix: it runs a Kaczmarz sweep over
+ * the rows of the consistent system B w = s, B = [H, sqrt(xi) I_K] (eq. (SLE)),
+ * from w = 0, and reads x = m and v = q off w = [m; sqrt(xi) q] (Remark 1).
+ *
+ * Conventions shared by every call:
+ *   - H is K x Nt; row k is user k's channel, non-zero only on its visibility
+ *     region (VR), the contiguous antenna interval
+ *     [vr_offset[k], vr_offset[k] + vr_len[k]) (eqs. (3)-(4), Sec. IV-B).
+ *   - H_packed stores row k's VR slice (vr_len[k] entries) at element
+ *     sum_{j<k} vr_len[j]; entries are interleaved complex64 (kz_cf32).
+ *   - Matrices of right-hand sides and solutions are column-major:
+ *     s is K x nrhs (element (k, j) at s[k + K j]), x is Nt x nrhs,
+ *     v is K x nrhs.  Column j is one independent system (Remark 2).
+ *   - Device pointers are CUDA device memory of the current device; the
+ *     caller owns them.  Host pointers are plain host memory.
+ *   - "stream" is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Solve calls are asynchronous on that stream: their
+ *     device outputs are valid once the stream has been synchronised.
+ *   - Functions return kz_status.  KZ_ERR_INVALID_ARG is returned before any
+ *     work is enqueued; kz_last_error() gives a one-line reason (thread-local).
+ *     Nothing is thrown across this interface.
+ *   - Convergence: every method stops per right-hand side once its relative
+ *     residual ||s - B w|| / ||s|| <= tol (the paper stops on an NMSE against
+ *     the RZF answer, which a solver cannot know) or after max_iter
+ *     iterations.  The per-call device status word (optional) receives
+ *     KZ_STATUS_BIT_NOT_CONVERGED and/or KZ_STATUS_BIT_NUMERIC.
+ */
+#ifndef KZPRECODE_H
+#define KZPRECODE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct {
+    float re, im;
+} kz_cf32;
+
+typedef enum {
+    KZ_OK = 0,
+    KZ_NOT_CONVERGED = 1,    /* some column reached max_iter (outputs still written) */
+    KZ_ERR_INVALID_ARG = 2,  /* bad size, VR, pointer alignment or enum */
+    KZ_ERR_NUMERIC = 3,      /* NaN or Inf in a residual */
+    KZ_ERR_CUDA = 4,         /* a CUDA runtime call failed */
+    KZ_ERR_NOMEM = 5,        /* device allocation failed */
+    KZ_ERR_UNSUPPORTED = 6   /* combination not provided (e.g. BF16 with a row method) */
+} kz_status;
+
+/* Bits the kernels OR into the optional device status word. */
+#define KZ_STATUS_BIT_NOT_CONVERGED 1
+#define KZ_STATUS_BIT_NUMERIC 2
+
+/* Methods.  RK_ENERGY / RK_UNIFORM: Alg. 1 with p_i = ||b_i||^2/||B||_F^2 or 1/K
+ * (Sec. III-A).  GRK: greedy selection with every residual recomputed
+ * (Sec. IV-A).  VR_OGRK: Alg. 2, residuals recomputed only on X_{i(t-1)}.
+ * AHK: aggregation-hyperplane step on all rows (eqs. (update4),
+ * (coefficient)).  VR_OAHK: Alg. 3, unit step on the orthogonal set F
+ * (Prop. 1) followed by an AHK step on the rest V. */
+typedef enum {
+    KZ_RK_ENERGY = 0,
+    KZ_RK_UNIFORM = 1,
+    KZ_GRK = 2,
+    KZ_AHK = 3,
+    KZ_VR_OGRK = 4,
+    KZ_VR_OAHK = 5
+} kz_algo;
+
+/* Row selection for GRK / VR_OGRK.  PAPER: sample p_i = |r_i|^2/||r||^2
+ * (Sec. IV-A, Alg. 2 step 4).  BAIWU: the same sampling restricted to the
+ * greedy set of Bai & Wu cited in Sec. IV-A.  ARGMAX: i = argmax |r_i|^2/||b_i||^2,
+ * lowest index on ties.  Random draws use the SplitMix64 counter-based
+ * generator keyed by (seed, instance, column, iteration). */
+typedef enum { KZ_SEL_PAPER = 0, KZ_SEL_BAIWU = 1, KZ_SEL_ARGMAX = 2 } kz_select;
+
+/* Storage / arithmetic of the iteration.  C64: complex64 H, FP32 arithmetic.
+ * BF16_MIXED (AHK / VR_OAHK only): the residual and projection read a BF16
+ * copy of H with FP32 accumulation, in correction form against a true
+ * residual recomputed from the complex64 H with FP64 accumulation every
+ * refresh period; that recomputation drives the stopping test. */
+typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
+
+typedef struct kz_plan kz_plan;
+typedef struct kz_batch kz_batch;
+
+/* Build the per-channel set-up (step A0): row norms ||h_k||^2, the VR overlap
+ * graph, the non-orthogonal sets X_k (Sec. IV-B, k included), the orthogonal
+ * set F as a maximum independent set of the overlap graph (eq. (max_set);
+ * exact for contiguous VRs by the earliest-end rule), the antenna-tile
+ * covering lists and the device copies of H in the solver's aligned layout
+ * (complex64, plus BF16 when prec == KZ_BF16_MIXED).
+ *   K, Nt: users and antennas, 1 <= K < Nt (Sec. II).
+ *   vr_offset, vr_len: host int32[K]; every VR must satisfy
+ *     vr_len >= 1 and 0 <= vr_offset, vr_offset + vr_len <= Nt.
+ *   H_packed: device kz_cf32[sum vr_len] (layout above), 8-byte aligned.
+ *     It is copied; the caller may free it after this call returns.
+ *   stream: the copies and set-up kernels are enqueued there and the call
+ *     waits for them before returning.
+ * On success *out owns all device memory of the plan until kz_plan_destroy. */
+kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset,
+                         const int32_t* vr_len, const kz_cf32* H_packed, kz_prec prec, void* stream);
+
+/* Release a plan (NULL is ignored).  Not stream-ordered: the caller makes
+ * sure no call using the plan is still running. */
+void kz_plan_destroy(kz_plan* plan);
+
+/* Sizes and sets of a plan, for inspection and tests (host outputs; any
+ * pointer may be NULL).  F receives the orthogonal set (ascending, *nF entries,
+ * room for K); X_ptr (K+1) and X_idx (room for K*K) receive the CSR sets X_k. */
+kz_status kz_plan_query(const kz_plan* plan, int32_t* K, int32_t* Nt, int64_t* sum_len, int32_t* nF,
+                        int32_t* F, int32_t* X_ptr, int32_t* X_idx);
+
+/* Solve nrhs independent systems that share one channel (steps A1-A7).
+ *   s: device K x nrhs;  x: device Nt x nrhs (output, also used as the
+ *   solver's per-iteration aggregate buffer);  v: device K x nrhs output of
+ *   the auxiliary vectors (may be NULL);  iters: device int32[nrhs] (row
+ *   projections for the RK family, iterations for AHK / VR_OAHK);  resid:
+ *   device double[nrhs], the final true relative residual;  status: device
+ *   int32 word the kernel ORs KZ_STATUS_BIT_* into (may be NULL; the caller
+ *   zeroes it).
+ *   xi > 0; tol >= 0; max_iter >= 1; nrhs >= 1.  rhs_per_cta in {0,1,2,4,8}
+ *   (0 = the plan's tuned choice).  refresh: recompute m = H^H q every
+ *   `refresh` iterations (0 = default).
+ * Returns KZ_OK once the work is enqueued. */
+kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
+                     kz_select sel, double tol, int32_t max_iter, uint64_t seed, kz_cf32* x,
+                     kz_cf32* v, int32_t* iters, double* resid, int32_t* status, int32_t rhs_per_cta,
+                     int32_t refresh, void* stream);
+
+/* One item of a batch: a plan with its own right-hand sides and outputs
+ * (layouts as in kz_precode, all device pointers, nrhs columns each). */
+typedef struct {
+    const kz_plan* plan;
+    const kz_cf32* s;
+    kz_cf32* x;
+    kz_cf32* v;      /* may be NULL */
+    int32_t* iters;
+    double* resid;
+    float xi;
+} kz_batch_item;
+
+/* Prepare one persistent launch over n instances of uneven K, Nt and VR
+ * lengths (step A8): copies the instance table to the device, orders the
+ * work (one item = one instance x rhs_per_cta columns) by estimated cost,
+ * largest first, and allocates the work-queue counter.  rhs_per_cta and
+ * threads as in kz_precode (0 = tuned).  The plans and buffers named by the
+ * items must stay valid while the batch is used.  Synchronous. */
+kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n, int32_t nrhs,
+                           kz_algo algo, kz_prec prec, int32_t rhs_per_cta, void* stream);
+
+/* Run a prepared batch: one kernel launch after a 4-byte memset of the
+ * queue counter, no host synchronisation, so it can be captured in a CUDA
+ * graph.  status as in kz_precode (may be NULL). */
+kz_status kz_precode_batched(kz_batch* batch, kz_select sel, double tol, int32_t max_iter,
+                             uint64_t seed, int32_t refresh, int32_t* status, void* stream);
+
+void kz_batch_destroy(kz_batch* batch);
+
+/* Adjoint (implicit differentiation) of Q = (H H^H + xi I)^-1 S, X = H^H Q for
+ * a real loss L.  Given the gradients G_Q (K x nrhs) and G_X (Nt x nrhs) of L
+ * with respect to Q and X (PyTorch's convention for complex tensors: the
+ * first-order change is dL = Re sum conj(G) dZ), it
+ *   1. forms G~ = G_Q + H G_X,
+ *   2. solves (H H^H + xi I) Lambda = G~ with the same Kaczmarz operator
+ *      (VR-OAHK), giving Lambda (K x nrhs) and Y = H^H Lambda (written to y),
+ *   3. contracts grad_H = Q G_X^H - Lambda X^H - Q Y^H on the VR entries only
+ *      (packed like H_packed) and grad_xi = -Re sum conj(Lambda) Q.
+ * Lambda is also dL/dS.  All pointers are device memory; grad_xi is one
+ * float.  tol / max_iter / iters / resid / status as in kz_precode.  The
+ * paper has no gradient; this follows from dA = dxi I + dH H^H + H dH^H. */
+kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q,
+                             const kz_cf32* X, const kz_cf32* G_Q, const kz_cf32* G_X, double tol,
+                             int32_t max_iter, kz_cf32* lambda, kz_cf32* y, kz_cf32* grad_H_packed,
+                             float* grad_xi, int32_t* iters, double* resid, int32_t* status,
+                             void* stream);
+
+/* One-line description of the last error on this thread ("" if none). */
+const char* kz_last_error(void);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+int32_t kz_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KZPRECODE_H */

@@ -1,0 +1,481 @@
+// Persistent AHK / VR-OAHK solver (steps A1, A4-A7 and A9).
+//
+// One CTA owns one work item: one channel and J of its right-hand-side
+// columns.  The iterate m (J x Ntp complex) lives in shared memory for the
+// whole solve; only H is streamed from L2 / HBM.  Per iteration of Alg. 3:
+//
+//   F half-step (eq. (updateor), unit step of Prop. 1): one warp per row of
+//     the orthogonal set computes r_i = b_i - h_i . m - xi q_i, then
+//     m += (r_i / d_i) conj(h_i) on its VR and q_i += r_i / d_i.  F rows have
+//     disjoint VRs, so warps never touch the same m entries.
+//   V half-step (eq. (updatenor)): one warp per V row computes r_i and
+//     phi_i = r_i / d_i; the aggregate u = H_V^H phi_V is formed antenna-major
+//     (each thread owns an antenna pair and loops over the covering V rows of
+//     its 64-antenna tile, no scatter); gamma = phi^H r / (||u||^2 + xi ||phi||^2);
+//     m += gamma u, q_V += gamma phi_V.
+// AHK (eq. (update4) with eq. (coefficient)) is the V half-step over every row.
+//
+// The right-hand side of the row equations is b (= s for C64).  In BF16_MIXED
+// the iteration reads the BF16 copy of H and works in correction form: at
+// each refresh m_ref = H^H q and b = s - H m_ref are recomputed from the
+// complex64 H with FP64 accumulation, m restarts at 0, so the inner residual
+// b - H_bf16 m - xi q differs from the true one only by (H - H_bf16) times the
+// correction.  The refresh's true residual drives the stopping test.
+#include "kz_device.cuh"
+
+namespace {
+
+constexpr int ALGO_OAHK = KZ_VR_OAHK;
+
+template <int J, int NW, bool BF16>
+__global__ void __launch_bounds__(NW * 32) kz_ahk_kernel(const __grid_constant__ KzLaunch L) {
+    extern __shared__ __align__(16) unsigned char kz_smem[];
+    __shared__ KzInst sI;
+    __shared__ float s_part[NW][3 * J];
+    __shared__ float s_tot[3 * J];
+    __shared__ double s_partd[NW][J];
+    __shared__ double s_sn2[J];
+    __shared__ float s_gamma[J];
+    __shared__ int s_iters[J];
+    __shared__ int s_active;
+    __shared__ int s_pending;
+    __shared__ int s_item;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NT = NW * 32;
+    float2* m_s = reinterpret_cast<float2*>(kz_smem);
+    float2* b_s = m_s + (size_t)J * L.Ntp_max;
+    float2* q_s = b_s + (size_t)L.K_max * J;
+    float2* p_s = q_s + (size_t)L.K_max * J;
+    float* d_s = reinterpret_cast<float*>(p_s + (size_t)L.K_max * J);
+    const float tol2 = (float)(L.tol * L.tol);
+    const bool oahk = (L.algo == ALGO_OAHK);
+
+    int static_item = blockIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = L.queue ? atomicAdd(L.queue, 1) : static_item;
+        static_item += gridDim.x;
+        __syncthreads();
+        const int item = s_item;
+        if (item >= L.n_items) break;
+        int2 it;
+        if (L.insts) {
+            it = L.items[item];
+            load_inst(sI, L.insts + it.x);
+        } else {
+            it = make_int2(0, item * J);
+            load_inst(sI, &L.single);
+        }
+        __syncthreads();
+        const KzInst& I = sI;
+        const int K = I.K, Nt = I.Nt, Ntp = I.Ntp, nF = oahk ? I.nF : 0;
+        const int col0 = it.y, ncols = min(J, I.ld - col0);
+        const float xi = I.xi;
+        const int4* trow4 = I.trow4;
+
+        // ---- initialise: m = 0, q = 0, b = s, d = ||h||^2 + xi
+        for (int e = tid; e < J * Ntp; e += NT) m_s[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < K * J; e += NT) {
+            const int i = e / J, j = e % J;
+            b_s[e] = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
+            q_s[e] = make_float2(0.f, 0.f);
+            p_s[e] = make_float2(0.f, 0.f);
+        }
+        for (int i = tid; i < K; i += NT) d_s[i] = I.nrm[i] + xi;
+        __syncthreads();
+        if (warp < J) {
+            double a = 0.0;
+            for (int i = lane; i < K; i += 32) {
+                const float2 v = b_s[i * J + warp];
+                a += (double)v.x * v.x + (double)v.y * v.y;
+            }
+            a = warp_sum_d(a);
+            if (lane == 0) s_sn2[warp] = a;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int act = 0;
+            for (int j = 0; j < ncols; ++j) {
+                s_iters[j] = L.max_iter;
+                if (s_sn2[j] > 0.0) act |= 1 << j;
+                else s_iters[j] = 0;
+            }
+            s_active = act;
+            s_pending = 0;
+        }
+        __syncthreads();
+
+        int t = 0, since_refresh = 0;
+        while (s_active) {
+            const int act = s_active;
+            // ---------------- F half-step (VR-OAHK only)
+            if (oahk) {
+                ++t;
+                for (int f = warp; f < nF; f += NW) {
+                    const int i = I.order[f];
+                    float2 acc[J];
+                    row_dot<J, BF16>(I, i, m_s, Ntp, acc);
+                    float2 g[J];
+                    const float di = d_s[i];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                        const float rx = bv.x - acc[j].x - xi * qv.x;
+                        const float ry = bv.y - acc[j].y - xi * qv.y;
+                        const bool on = (act >> j) & 1;
+                        g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                    }
+                    row_axpy<J, BF16>(I, i, m_s, Ntp, g, lane, 32);
+                    if (lane == 0) {
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            q_s[i * J + j].x += g[j].x;
+                            q_s[i * J + j].y += g[j].y;
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+            // ---------------- V residual, phi = r / d and the scalars of the step
+            const int v0 = nF, vcount = K - nF;
+            float pr[J], pn[J], pp[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) pr[j] = pn[j] = pp[j] = 0.f;
+            for (int v = warp; v < vcount; v += NW) {
+                const int i = I.order[v0 + v];
+                float2 acc[J];
+                row_dot<J, BF16>(I, i, m_s, Ntp, acc);
+                const float di = d_s[i];
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                    const float rx = bv.x - acc[j].x - xi * qv.x;
+                    const float ry = bv.y - acc[j].y - xi * qv.y;
+                    const float r2 = rx * rx + ry * ry;
+                    const bool on = (act >> j) & 1;
+                    const float2 ph = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                    pr[j] += r2;
+                    pn[j] += on ? r2 / di : 0.f;
+                    pp[j] += ph.x * ph.x + ph.y * ph.y;
+                    if (lane == 0) p_s[i * J + j] = ph;
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    s_part[warp][j] = pr[j];
+                    s_part[warp][J + j] = pn[j];
+                    s_part[warp][2 * J + j] = pp[j];
+                }
+            }
+            __syncthreads();
+            if (tid < 3 * J) {
+                float a = 0.f;
+                for (int w = 0; w < NW; ++w) a += s_part[w][tid];
+                s_tot[tid] = a;
+            }
+            __syncthreads();
+            // ---------------- stopping test on the residual at hand (tentative:
+            // a column that passes is confirmed on the true residual first)
+            if (tid == 0) {
+                int a2 = s_active, pend = 0;
+                for (int j = 0; j < ncols; ++j) {
+                    if (!((a2 >> j) & 1)) continue;
+                    const float rn2 = s_tot[j];
+                    if (!(rn2 == rn2) || isinf(rn2)) {
+                        a2 &= ~(1 << j);
+                        s_iters[j] = t;
+                        kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+                    } else if ((double)rn2 <= (double)tol2 * s_sn2[j]) {
+                        pend |= 1 << j;
+                    } else if (!oahk && t >= L.max_iter) {
+                        a2 &= ~(1 << j);  // AHK: t steps done and still above tol
+                        kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
+                    }
+                }
+                s_active = a2;
+                s_pending = pend;
+            }
+            __syncthreads();
+            // ---------------- confirmation: m = H^H q from the complex64 H, the
+            // true residual s - H m - xi q with FP64 accumulation, and the test
+            // again.  In BF16_MIXED this is also the periodic refresh that sets
+            // the correction right-hand side b = s - H m and restarts m at 0.
+            if (s_pending || (BF16 && since_refresh >= L.refresh)) {
+                since_refresh = 0;
+                for (int tile = warp; tile < I.ntiles; tile += NW) {
+                    float2 u0[J], u1[J];
+                    tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+                    const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        m_s[j * Ntp + n] = u0[j];
+                        m_s[j * Ntp + n + 1] = u1[j];
+                    }
+                }
+                __syncthreads();
+                double rp[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) rp[j] = 0.0;
+                for (int i = warp; i < K; i += NW) {
+                    double ar[J], ai[J];
+                    row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
+                        const double bx = (double)sv.x - ar[j], by = (double)sv.y - ai[j];
+                        const float2 qv = q_s[i * J + j];
+                        const double rx = bx - (double)xi * qv.x, ry = by - (double)xi * qv.y;
+                        rp[j] += rx * rx + ry * ry;
+                        if (BF16 && lane == 0) b_s[i * J + j] = make_float2((float)bx, (float)by);
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j) s_partd[warp][j] = rp[j];
+                }
+                __syncthreads();
+                if (tid == 0) {
+                    int a2 = s_active;
+                    const int tested = BF16 ? a2 : s_pending;
+                    for (int j = 0; j < ncols; ++j) {
+                        if (!((tested >> j) & 1) || !((a2 >> j) & 1)) continue;
+                        double rn2 = 0.0;
+                        for (int w = 0; w < NW; ++w) rn2 += s_partd[w][j];
+                        if (!(rn2 == rn2) || isinf(rn2)) {
+                            a2 &= ~(1 << j);
+                            s_iters[j] = t;
+                            kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+                        } else if (rn2 <= L.tol * L.tol * s_sn2[j]) {
+                            a2 &= ~(1 << j);
+                            s_iters[j] = t;
+                        } else if (!oahk && t >= L.max_iter) {
+                            a2 &= ~(1 << j);
+                            kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
+                        }
+                    }
+                    s_active = a2;
+                    s_pending = 0;
+                }
+                if (BF16)
+                    for (int e = tid; e < J * Ntp; e += NT) m_s[e] = make_float2(0.f, 0.f);
+                __syncthreads();
+            }
+            if (!s_active) break;
+            // columns that take the aggregate step this iteration (a column whose
+            // confirmation failed keeps iterating, so nothing stalls)
+            const int stepmask = (!oahk && t >= L.max_iter) ? 0 : s_active;
+            // ---------------- aggregate u = H_V^H phi_V (antenna-major), ||u||^2
+            if (stepmask) {
+                float uu[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) uu[j] = 0.f;
+                for (int tile = warp; tile < I.ntiles; tile += NW) {
+                    const int k0 = I.tptr[tile];
+                    const int k1 = oahk ? k0 + I.tnv[tile] : I.tptr[tile + 1];
+                    if (k0 == k1) continue;
+                    float2 u0[J], u1[J];
+                    tile_accum<J, BF16>(I, trow4, tile, k0, k1, p_s, u0, u1);
+                    const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        if (j < ncols) {
+                            float2* xc = I.x + (size_t)(col0 + j) * Nt;
+                            if (n < Nt) xc[n] = u0[j];
+                            if (n + 1 < Nt) xc[n + 1] = u1[j];
+                        }
+                        uu[j] += u0[j].x * u0[j].x + u0[j].y * u0[j].y + u1[j].x * u1[j].x + u1[j].y * u1[j].y;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < J; ++j) uu[j] = warp_sum(uu[j]);
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j) s_part[warp][j] = uu[j];
+                }
+                __syncthreads();
+                if (tid < J) {
+                    float a = 0.f;
+                    for (int w = 0; w < NW; ++w) a += s_part[w][tid];
+                    const float num = s_tot[J + tid];
+                    const float den = a + xi * s_tot[2 * J + tid];
+                    const bool on = (stepmask >> tid) & 1;
+                    s_gamma[tid] = (on && num > 0.f && den > 0.f) ? num / den : 0.f;
+                }
+                __syncthreads();
+                // ---------------- m += gamma u ; q_V += gamma phi_V
+                for (int tile = warp; tile < I.ntiles; tile += NW) {
+                    const int k0 = I.tptr[tile];
+                    const int k1 = oahk ? k0 + I.tnv[tile] : I.tptr[tile + 1];
+                    if (k0 == k1) continue;
+                    const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float g = s_gamma[j];
+                        if (j < ncols && g != 0.f) {
+                            const float2* xc = I.x + (size_t)(col0 + j) * Nt;
+                            float2* mp = m_s + j * Ntp + n;
+                            if (n < Nt) {
+                                const float2 u = xc[n];
+                                mp[0].x = fmaf(g, u.x, mp[0].x);
+                                mp[0].y = fmaf(g, u.y, mp[0].y);
+                            }
+                            if (n + 1 < Nt) {
+                                const float2 u = xc[n + 1];
+                                mp[1].x = fmaf(g, u.x, mp[1].x);
+                                mp[1].y = fmaf(g, u.y, mp[1].y);
+                            }
+                        }
+                    }
+                }
+                for (int e = tid; e < vcount * J; e += NT) {
+                    const int i = I.order[v0 + e / J], j = e % J;
+                    const float g = s_gamma[j];
+                    const float2 ph = p_s[i * J + j];
+                    q_s[i * J + j].x = fmaf(g, ph.x, q_s[i * J + j].x);
+                    q_s[i * J + j].y = fmaf(g, ph.y, q_s[i * J + j].y);
+                }
+            }
+            if (!oahk) ++t;
+            ++since_refresh;
+            __syncthreads();
+            // ---------------- periodic drift correction m = H^H q (C64)
+            if (!BF16 && L.refresh > 0 && since_refresh >= L.refresh) {
+                since_refresh = 0;
+                for (int tile = warp; tile < I.ntiles; tile += NW) {
+                    float2 u0[J], u1[J];
+                    tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+                    const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        m_s[j * Ntp + n] = u0[j];
+                        m_s[j * Ntp + n + 1] = u1[j];
+                    }
+                }
+                __syncthreads();
+            }
+            if (oahk && t >= L.max_iter) {
+                if (tid == 0) {
+                    for (int j = 0; j < ncols; ++j)
+                        if ((s_active >> j) & 1) kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
+                    s_active = 0;
+                }
+                __syncthreads();
+                break;
+            }
+        }
+
+        // ---- finalise: x = m = H^H q (complex64), true residual with FP64 accumulation
+        for (int tile = warp; tile < I.ntiles; tile += NW) {
+            float2 u0[J], u1[J];
+            tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+            const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                m_s[j * Ntp + n] = u0[j];
+                m_s[j * Ntp + n + 1] = u1[j];
+            }
+        }
+        __syncthreads();
+        {
+            double rp[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) rp[j] = 0.0;
+            for (int i = warp; i < K; i += NW) {
+                double ar[J], ai[J];
+                row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
+                    const float2 qv = q_s[i * J + j];
+                    const double rx = (double)sv.x - ar[j] - (double)xi * qv.x;
+                    const double ry = (double)sv.y - ai[j] - (double)xi * qv.y;
+                    rp[j] += rx * rx + ry * ry;
+                }
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < J; ++j) s_partd[warp][j] = rp[j];
+            }
+        }
+        for (int j = 0; j < ncols; ++j) {
+            float2* xc = I.x + (size_t)(col0 + j) * Nt;
+            for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * Ntp + n];
+            if (I.v) {
+                float2* vc = I.v + (size_t)(col0 + j) * K;
+                for (int i = tid; i < K; i += NT) vc[i] = q_s[i * J + j];
+            }
+        }
+        __syncthreads();
+        if (tid < ncols) {
+            double rn2 = 0.0;
+            for (int w = 0; w < NW; ++w) rn2 += s_partd[w][tid];
+            const double sn2 = s_sn2[tid];
+            I.resid[col0 + tid] = sn2 > 0.0 ? sqrt(rn2 / sn2) : 0.0;
+            I.iters[col0 + tid] = s_iters[tid];
+            if (!(rn2 == rn2)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+        }
+        __syncthreads();
+    }
+}
+
+template <int J, int NW, bool BF16>
+cudaError_t launch_t(const KzLaunch& L, int grid, size_t smem, cudaStream_t st) {
+    auto k = kz_ahk_kernel<J, NW, BF16>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k<<<grid, NW * 32, smem, st>>>(L);
+    return cudaGetLastError();
+}
+
+template <int J, int NW, bool BF16>
+int occ_t(size_t smem) {
+    auto k = kz_ahk_kernel<J, NW, BF16>;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NW * 32, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+template <int NW, bool BF16>
+cudaError_t launch_j(const KzLaunch& L, int J, int grid, size_t smem, cudaStream_t st) {
+    switch (J) {
+        case 1: return launch_t<1, NW, BF16>(L, grid, smem, st);
+        case 2: return launch_t<2, NW, BF16>(L, grid, smem, st);
+        case 4: return launch_t<4, NW, BF16>(L, grid, smem, st);
+        case 8: return launch_t<8, NW, BF16>(L, grid, smem, st);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <int NW, bool BF16>
+int occ_j(int J, size_t smem) {
+    switch (J) {
+        case 1: return occ_t<1, NW, BF16>(smem);
+        case 2: return occ_t<2, NW, BF16>(smem);
+        case 4: return occ_t<4, NW, BF16>(smem);
+        case 8: return occ_t<8, NW, BF16>(smem);
+        default: return 0;
+    }
+}
+
+}  // namespace
+
+size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
+    (void)prec;
+    return (size_t)J * Ntp * sizeof(float2) + 3 * (size_t)K * J * sizeof(float2) + (size_t)K * sizeof(float) + 16;
+}
+
+cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {
+    const bool bf = (L.prec == KZ_BF16_MIXED);
+    if (nw == 8) return bf ? launch_j<8, true>(L, J, grid, smem, st) : launch_j<8, false>(L, J, grid, smem, st);
+    if (nw == 16) return bf ? launch_j<16, true>(L, J, grid, smem, st) : launch_j<16, false>(L, J, grid, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+int kz_occupancy_ahk(int J, int nw, size_t smem, int prec) {
+    const bool bf = (prec == KZ_BF16_MIXED);
+    if (nw == 8) return bf ? occ_j<8, true>(J, smem) : occ_j<8, false>(J, smem);
+    if (nw == 16) return bf ? occ_j<16, true>(J, smem) : occ_j<16, false>(J, smem);
+    return 0;
+}

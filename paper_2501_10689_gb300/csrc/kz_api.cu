@@ -1,0 +1,621 @@
+// C-ABI of libkzprecode: argument checking, the per-channel host set-up
+// (step A0) and the launches.  See include/kzprecode.h for the contract.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "kz_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+constexpr size_t kSmemLimit = 227 * 1024 - 2048;  // dynamic shared memory budget per CTA
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v, cudaStream_t st) {
+    *dst = nullptr;
+    const size_t bytes = std::max<size_t>(v.size(), 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) return e;
+    if (!v.empty()) e = cudaMemcpyAsync(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, st);
+    return e;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return std::max(n, 1);
+}
+
+}  // namespace
+
+void kz_set_error(const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+
+struct kz_plan {
+    int K = 0, Nt = 0, Ntp = 0, ntiles = 0, nF = 0;
+    int64_t sumL = 0, total2 = 0;
+    kz_prec prec = KZ_C64;
+    double sum_nrm = 0.0;
+    std::vector<int> F, xptr, xidx;
+    // device
+    int4* d_rows = nullptr;
+    int* d_rptr = nullptr;
+    int* d_in_off = nullptr;
+    float* d_nrm = nullptr;
+    double* d_nrmd = nullptr;
+    int* d_order = nullptr;
+    int* d_xptr = nullptr;
+    int* d_xidx = nullptr;
+    int* d_tptr = nullptr;
+    int* d_tnv = nullptr;
+    int4* d_trow4 = nullptr;
+    float2* d_Hc = nullptr;
+    __nv_bfloat162* d_Hb = nullptr;
+    float2* d_scratch = nullptr;  // adjoint right-hand side G~ (grown on demand)
+    size_t scratch_elems = 0;
+    int sms = 1;
+
+    ~kz_plan() {
+        void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
+                      d_tptr, d_tnv, d_trow4, d_Hc, d_Hb, d_scratch};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+    }
+
+    KzInst inst() const {
+        KzInst I;
+        memset(&I, 0, sizeof(I));
+        I.K = K;
+        I.Nt = Nt;
+        I.Ntp = Ntp;
+        I.ntiles = ntiles;
+        I.nF = nF;
+        I.rows = d_rows;
+        I.rptr = d_rptr;
+        I.nrm = d_nrm;
+        I.order = d_order;
+        I.xptr = d_xptr;
+        I.xidx = d_xidx;
+        I.tptr = d_tptr;
+        I.tnv = d_tnv;
+        I.trow4 = d_trow4;
+        I.Hc = d_Hc;
+        I.Hb = d_Hb;
+        I.sum_nrm = sum_nrm;
+        return I;
+    }
+};
+
+struct kz_batch {
+    int n = 0, nrhs = 0, J = 1, nw = 16, grid = 1, n_items = 0, Ntp_max = 0, K_max = 0;
+    size_t smem = 0;
+    kz_algo algo = KZ_VR_OAHK;
+    kz_prec prec = KZ_C64;
+    KzInst* d_insts = nullptr;
+    int2* d_items = nullptr;
+    int* d_queue = nullptr;
+    ~kz_batch() {
+        if (d_insts) cudaFree(d_insts);
+        if (d_items) cudaFree(d_items);
+        if (d_queue) cudaFree(d_queue);
+    }
+};
+
+namespace {
+
+bool is_ahk_family(kz_algo a) { return a == KZ_AHK || a == KZ_VR_OAHK; }
+
+bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_VR_OAHK; }
+
+int default_refresh(kz_algo a, kz_prec p) {
+    if (is_ahk_family(a)) return p == KZ_BF16_MIXED ? 6 : 16;
+    return 512;
+}
+
+size_t smem_for(kz_algo a, int J, int Ntp, int K, kz_prec p) {
+    return is_ahk_family(a) ? kz_smem_ahk(J, Ntp, K, p) : kz_smem_kacz(J, Ntp, K);
+}
+
+int occupancy_for(kz_algo a, int J, int nw, size_t smem, kz_prec p) {
+    return is_ahk_family(a) ? kz_occupancy_ahk(J, nw, smem, p) : kz_occupancy_kacz(J, nw, smem);
+}
+
+// J (columns per CTA): the largest of {8, 4, 2, 1} that fits shared memory
+// and still gives every SM a work item; 1 when there are few columns.
+int choose_J(kz_algo a, int nrhs_total_items_base, int Ntp, int K, kz_prec p, int sms, int per_inst_cols) {
+    for (int J : {8, 4, 2}) {
+        if (J > per_inst_cols) continue;
+        if (smem_for(a, J, Ntp, K, p) > kSmemLimit / 2 + 8 * 1024) continue;
+        const long items = (long)nrhs_total_items_base * ((per_inst_cols + J - 1) / J);
+        if (items >= 2L * sms) return J;
+    }
+    return 1;
+}
+
+int choose_nw(int Ntp) { return (Ntp / KZ_TILE) >= 16 ? 16 : 8; }
+
+kz_status check_launch(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+        kz_set_error("%s: %s", what, cudaGetErrorString(e));
+        return KZ_ERR_CUDA;
+    }
+    return KZ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* kz_last_error(void) { return g_err.c_str(); }
+
+int32_t kz_version(void) { return 1 * 10000 + 0 * 100 + 0; }
+
+kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset, const int32_t* vr_len,
+                         const kz_cf32* H_packed, kz_prec prec, void* stream) {
+    g_err.clear();
+    if (!out) {
+        kz_set_error("kz_plan_create: out is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (K < 1 || Nt < 2 || K >= Nt) {
+        kz_set_error("kz_plan_create: need 1 <= K < Nt (got K=%d, Nt=%d)", K, Nt);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!vr_offset || !vr_len || !H_packed) {
+        kz_set_error("kz_plan_create: NULL vr_offset, vr_len or H_packed");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!aligned(H_packed, 8)) {
+        kz_set_error("kz_plan_create: H_packed must be 8-byte aligned");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (prec != KZ_C64 && prec != KZ_BF16_MIXED) {
+        kz_set_error("kz_plan_create: unknown precision %d", (int)prec);
+        return KZ_ERR_INVALID_ARG;
+    }
+    for (int k = 0; k < K; ++k) {
+        const long o = vr_offset[k], L = vr_len[k];
+        if (L < 1 || o < 0 || o + L > Nt) {
+            kz_set_error("kz_plan_create: VR of user %d is [%ld, %ld), outside [0, %d) or empty", k, o, o + L, Nt);
+            return KZ_ERR_INVALID_ARG;
+        }
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    kz_plan* P = new kz_plan();
+    P->K = K;
+    P->Nt = Nt;
+    P->prec = prec;
+    P->sms = sm_count();
+    P->Ntp = ((Nt + (Nt & 1)) + KZ_TILE - 1) / KZ_TILE * KZ_TILE;
+    P->ntiles = P->Ntp / KZ_TILE;
+
+    // aligned rows
+    std::vector<int4> rows(K);
+    std::vector<int> rptr(K), in_off(K);
+    int64_t acc = 0, acc_in = 0;
+    for (int k = 0; k < K; ++k) {
+        const int o = vr_offset[k], e = vr_offset[k] + vr_len[k];
+        const int a = o & ~1, b = (e + 1) & ~1;
+        rows[k] = make_int4(a, b - a, o, e);
+        rptr[k] = (int)acc;
+        in_off[k] = (int)acc_in;
+        acc += b - a;
+        acc_in += vr_len[k];
+    }
+    if (acc >= (int64_t)1 << 31) {
+        delete P;
+        kz_set_error("kz_plan_create: channel too large (%lld aligned entries)", (long long)acc);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    P->total2 = acc;
+    P->sumL = acc_in;
+
+    // orthogonal set F: earliest-end greedy on the VR intervals (exact maximum
+    // independent set of an interval graph); ties: later start, then lower index.
+    std::vector<int> idx(K);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::sort(idx.begin(), idx.end(), [&](int x, int y) {
+        const int ex = vr_offset[x] + vr_len[x], ey = vr_offset[y] + vr_len[y];
+        if (ex != ey) return ex < ey;
+        if (vr_offset[x] != vr_offset[y]) return vr_offset[x] > vr_offset[y];
+        return x < y;
+    });
+    std::vector<char> inF(K, 0);
+    long last_end = -1;
+    for (int k : idx) {
+        if (last_end < 0 || vr_offset[k] >= last_end) {
+            inF[k] = 1;
+            last_end = vr_offset[k] + vr_len[k];
+        }
+    }
+    for (int k = 0; k < K; ++k)
+        if (inF[k]) P->F.push_back(k);
+    P->nF = (int)P->F.size();
+    // solve order: F rows then V rows, each by decreasing VR length (balances
+    // the round-robin assignment of rows to warps)
+    std::vector<int> order;
+    std::vector<int> Vrows;
+    for (int k = 0; k < K; ++k)
+        if (!inF[k]) Vrows.push_back(k);
+    auto by_len = [&](int x, int y) { return vr_len[x] != vr_len[y] ? vr_len[x] > vr_len[y] : x < y; };
+    order = P->F;
+    std::sort(order.begin(), order.end(), by_len);
+    std::sort(Vrows.begin(), Vrows.end(), by_len);
+    order.insert(order.end(), Vrows.begin(), Vrows.end());
+
+    // X_k: users whose VR overlaps user k's (k included), via a sweep over starts
+    std::vector<int> by_start(K);
+    std::iota(by_start.begin(), by_start.end(), 0);
+    std::sort(by_start.begin(), by_start.end(), [&](int x, int y) { return vr_offset[x] < vr_offset[y]; });
+    std::vector<std::vector<int>> X(K);
+    for (int k = 0; k < K; ++k) X[k].push_back(k);
+    for (int ii = 0; ii < K; ++ii) {
+        const int x = by_start[ii];
+        const long ex = (long)vr_offset[x] + vr_len[x];
+        for (int jj = ii + 1; jj < K; ++jj) {
+            const int y = by_start[jj];
+            if (vr_offset[y] >= ex) break;
+            X[x].push_back(y);
+            X[y].push_back(x);
+        }
+    }
+    P->xptr.assign(K + 1, 0);
+    for (int k = 0; k < K; ++k) {
+        std::sort(X[k].begin(), X[k].end());
+        P->xptr[k + 1] = P->xptr[k] + (int)X[k].size();
+    }
+    P->xidx.reserve(P->xptr[K]);
+    for (int k = 0; k < K; ++k) P->xidx.insert(P->xidx.end(), X[k].begin(), X[k].end());
+
+    // covering lists per 64-antenna tile (aligned intervals), V rows first
+    std::vector<std::vector<int>> tv(P->ntiles), tf(P->ntiles);
+    for (int k = 0; k < K; ++k) {
+        const int a = rows[k].x, b = rows[k].x + rows[k].y;
+        for (int t = a / KZ_TILE; t <= (b - 1) / KZ_TILE; ++t) (inF[k] ? tf[t] : tv[t]).push_back(k);
+    }
+    std::vector<int> tptr(P->ntiles + 1, 0), tnv(P->ntiles, 0);
+    std::vector<int4> trow4;
+    for (int t = 0; t < P->ntiles; ++t) {
+        tnv[t] = (int)tv[t].size();
+        for (int pass = 0; pass < 2; ++pass)
+            for (int k : (pass == 0 ? tv[t] : tf[t])) trow4.push_back(make_int4(k, rptr[k] - rows[k].x, rows[k].x, rows[k].x + rows[k].y));
+        tptr[t + 1] = (int)trow4.size();
+    }
+
+    cudaError_t e = cudaSuccess;
+#define KZ_TRY(x)                                            \
+    do {                                                     \
+        e = (x);                                             \
+        if (e != cudaSuccess) {                              \
+            kz_set_error("kz_plan_create: %s", cudaGetErrorString(e)); \
+            delete P;                                        \
+            return e == cudaErrorMemoryAllocation ? KZ_ERR_NOMEM : KZ_ERR_CUDA; \
+        }                                                    \
+    } while (0)
+    KZ_TRY(upload(&P->d_rows, rows, st));
+    KZ_TRY(upload(&P->d_rptr, rptr, st));
+    KZ_TRY(upload(&P->d_in_off, in_off, st));
+    KZ_TRY(upload(&P->d_order, order, st));
+    KZ_TRY(upload(&P->d_xptr, P->xptr, st));
+    KZ_TRY(upload(&P->d_xidx, P->xidx, st));
+    KZ_TRY(upload(&P->d_tptr, tptr, st));
+    KZ_TRY(upload(&P->d_tnv, tnv, st));
+    KZ_TRY(upload(&P->d_trow4, trow4, st));
+    KZ_TRY(cudaMalloc((void**)&P->d_Hc, std::max<int64_t>(acc, 2) * sizeof(float2)));
+    if (prec == KZ_BF16_MIXED) KZ_TRY(cudaMalloc((void**)&P->d_Hb, std::max<int64_t>(acc, 2) * sizeof(__nv_bfloat162)));
+    KZ_TRY(cudaMalloc((void**)&P->d_nrm, K * sizeof(float)));
+    KZ_TRY(cudaMalloc((void**)&P->d_nrmd, K * sizeof(double)));
+    KZ_TRY(kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, K, acc, P->d_Hc,
+                        P->d_Hb, st));
+    KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, st));
+    std::vector<double> nrm(K);
+    KZ_TRY(cudaMemcpyAsync(nrm.data(), P->d_nrmd, K * sizeof(double), cudaMemcpyDeviceToHost, st));
+    KZ_TRY(cudaStreamSynchronize(st));
+#undef KZ_TRY
+    P->sum_nrm = 0.0;
+    for (double v : nrm) P->sum_nrm += v;
+    *out = P;
+    return KZ_OK;
+}
+
+void kz_plan_destroy(kz_plan* plan) { delete plan; }
+
+kz_status kz_plan_query(const kz_plan* P, int32_t* K, int32_t* Nt, int64_t* sum_len, int32_t* nF, int32_t* F,
+                        int32_t* X_ptr, int32_t* X_idx) {
+    g_err.clear();
+    if (!P) {
+        kz_set_error("kz_plan_query: plan is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (K) *K = P->K;
+    if (Nt) *Nt = P->Nt;
+    if (sum_len) *sum_len = P->sumL;
+    if (nF) *nF = P->nF;
+    if (F) std::copy(P->F.begin(), P->F.end(), F);
+    if (X_ptr) std::copy(P->xptr.begin(), P->xptr.end(), X_ptr);
+    if (X_idx) std::copy(P->xidx.begin(), P->xidx.end(), X_idx);
+    return KZ_OK;
+}
+
+static kz_status check_solve_args(const char* fn, const kz_plan* plan, int nrhs, float xi, int algo, int sel,
+                                  double tol, int max_iter, int J, int refresh) {
+    if (!plan) {
+        kz_set_error("%s: plan is NULL", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (nrhs < 1) {
+        kz_set_error("%s: nrhs must be >= 1", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!(xi > 0.f) || !std::isfinite(xi)) {
+        kz_set_error("%s: xi must be positive and finite", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!valid_algo(algo)) {
+        kz_set_error("%s: unknown algorithm %d", fn, algo);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (sel < KZ_SEL_PAPER || sel > KZ_SEL_ARGMAX) {
+        kz_set_error("%s: unknown selection rule %d", fn, sel);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!(tol >= 0.0) || max_iter < 1) {
+        kz_set_error("%s: need tol >= 0 and max_iter >= 1", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (J != 0 && J != 1 && J != 2 && J != 4 && J != 8) {
+        kz_set_error("%s: rhs_per_cta must be 0, 1, 2, 4 or 8", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (refresh < 0) {
+        kz_set_error("%s: refresh must be >= 0", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    return KZ_OK;
+}
+
+kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
+                     double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
+                     double* resid, int32_t* status, int32_t rhs_per_cta, int32_t refresh, void* stream) {
+    g_err.clear();
+    kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter, rhs_per_cta, refresh);
+    if (rc != KZ_OK) return rc;
+    if (!s || !x || !iters || !resid) {
+        kz_set_error("kz_precode: s, x, iters and resid are required");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!aligned(s, 8) || !aligned(x, 8) || (v && !aligned(v, 8)) || !aligned(resid, 8) || !aligned(iters, 4)) {
+        kz_set_error("kz_precode: misaligned output or input pointer");
+        return KZ_ERR_INVALID_ARG;
+    }
+    const kz_prec prec = plan->prec;
+    const bool bf = (prec == KZ_BF16_MIXED);
+    if (bf && !is_ahk_family(algo)) {
+        kz_set_error("kz_precode: BF16_MIXED is provided for AHK and VR_OAHK only");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    const int J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
+    const int nw = choose_nw(plan->Ntp);
+    const size_t smem = smem_for(algo, J, plan->Ntp, plan->K, prec);
+    if (smem > kSmemLimit) {
+        kz_set_error("kz_precode: channel needs %zu bytes of shared memory per CTA (limit %zu); use fewer columns per CTA",
+                     smem, kSmemLimit);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    KzLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.single = plan->inst();
+    L.single.xi = xi;
+    L.single.ld = nrhs;
+    L.single.s = reinterpret_cast<const float2*>(s);
+    L.single.x = reinterpret_cast<float2*>(x);
+    L.single.v = reinterpret_cast<float2*>(v);
+    L.single.iters = iters;
+    L.single.resid = resid;
+    L.insts = nullptr;
+    L.items = nullptr;
+    L.n_items = (nrhs + J - 1) / J;
+    L.queue = nullptr;
+    L.algo = algo;
+    L.sel = sel;
+    L.prec = prec;
+    L.tol = tol;
+    L.max_iter = max_iter;
+    L.refresh = refresh ? refresh : default_refresh(algo, prec);
+    L.seed = seed;
+    L.status = status;
+    L.Ntp_max = plan->Ntp;
+    L.K_max = plan->K;
+    const int occ = std::max(1, occupancy_for(algo, J, nw, smem, prec));
+    const int grid = std::min(L.n_items, plan->sms * occ);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = is_ahk_family(algo) ? kz_launch_ahk(L, J, nw, grid, smem, st) : kz_launch_kacz(L, J, nw, grid, smem, st);
+    return check_launch(e, "kz_precode launch");
+}
+
+kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n, int32_t nrhs, kz_algo algo,
+                           kz_prec prec, int32_t rhs_per_cta, void* stream) {
+    g_err.clear();
+    if (!out || !items || n < 1 || nrhs < 1) {
+        kz_set_error("kz_batch_prepare: need out, items, n >= 1 and nrhs >= 1");
+        return KZ_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!valid_algo(algo) || (prec != KZ_C64 && prec != KZ_BF16_MIXED)) {
+        kz_set_error("kz_batch_prepare: unknown algorithm or precision");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (prec == KZ_BF16_MIXED && !is_ahk_family(algo)) {
+        kz_set_error("kz_batch_prepare: BF16_MIXED is provided for AHK and VR_OAHK only");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    if (rhs_per_cta != 0 && rhs_per_cta != 1 && rhs_per_cta != 2 && rhs_per_cta != 4 && rhs_per_cta != 8) {
+        kz_set_error("kz_batch_prepare: rhs_per_cta must be 0, 1, 2, 4 or 8");
+        return KZ_ERR_INVALID_ARG;
+    }
+    int Ntp_max = 0, K_max = 0, sms = sm_count();
+    for (int b = 0; b < n; ++b) {
+        const kz_batch_item& it = items[b];
+        if (!it.plan || !it.s || !it.x || !it.iters || !it.resid || !(it.xi > 0.f)) {
+            kz_set_error("kz_batch_prepare: item %d is missing a plan, buffer or positive xi", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        if (prec == KZ_BF16_MIXED && it.plan->prec != KZ_BF16_MIXED) {
+            kz_set_error("kz_batch_prepare: item %d's plan has no BF16 copy", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        Ntp_max = std::max(Ntp_max, it.plan->Ntp);
+        K_max = std::max(K_max, it.plan->K);
+    }
+    kz_batch* B = new kz_batch();
+    B->n = n;
+    B->nrhs = nrhs;
+    B->algo = algo;
+    B->prec = prec;
+    B->Ntp_max = Ntp_max;
+    B->K_max = K_max;
+    B->J = rhs_per_cta ? rhs_per_cta : choose_J(algo, n, Ntp_max, K_max, prec, sms, nrhs);
+    B->nw = choose_nw(Ntp_max);
+    B->smem = smem_for(algo, B->J, Ntp_max, K_max, prec);
+    if (B->smem > kSmemLimit) {
+        delete B;
+        kz_set_error("kz_batch_prepare: largest channel needs %zu bytes of shared memory per CTA", smem_for(algo, rhs_per_cta ? rhs_per_cta : 1, Ntp_max, K_max, prec));
+        return KZ_ERR_UNSUPPORTED;
+    }
+    std::vector<KzInst> insts(n);
+    std::vector<std::pair<double, int2>> work;
+    for (int b = 0; b < n; ++b) {
+        const kz_batch_item& it = items[b];
+        KzInst I = it.plan->inst();
+        I.inst = b;
+        I.xi = it.xi;
+        I.ld = nrhs;
+        I.s = reinterpret_cast<const float2*>(it.s);
+        I.x = reinterpret_cast<float2*>(it.x);
+        I.v = reinterpret_cast<float2*>(it.v);
+        I.iters = it.iters;
+        I.resid = it.resid;
+        insts[b] = I;
+        const double cost = (double)it.plan->total2 + 4.0 * it.plan->Ntp;
+        for (int c = 0; c < nrhs; c += B->J) work.push_back({cost, make_int2(b, c)});
+    }
+    std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<int2> witems(work.size());
+    for (size_t w = 0; w < work.size(); ++w) witems[w] = work[w].second;
+    B->n_items = (int)witems.size();
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = upload(&B->d_insts, insts, st);
+    if (e == cudaSuccess) e = upload(&B->d_items, witems, st);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) {
+        delete B;
+        kz_set_error("kz_batch_prepare: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? KZ_ERR_NOMEM : KZ_ERR_CUDA;
+    }
+    const int occ = std::max(1, occupancy_for(algo, B->J, B->nw, B->smem, prec));
+    B->grid = std::min(B->n_items, sms * occ);
+    *out = B;
+    return KZ_OK;
+}
+
+kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max_iter, uint64_t seed,
+                             int32_t refresh, int32_t* status, void* stream) {
+    g_err.clear();
+    if (!B) {
+        kz_set_error("kz_precode_batched: batch is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (sel < KZ_SEL_PAPER || sel > KZ_SEL_ARGMAX || !(tol >= 0.0) || max_iter < 1 || refresh < 0) {
+        kz_set_error("kz_precode_batched: bad selection rule, tol, max_iter or refresh");
+        return KZ_ERR_INVALID_ARG;
+    }
+    KzLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.insts = B->d_insts;
+    L.items = B->d_items;
+    L.n_items = B->n_items;
+    L.queue = B->d_queue;
+    L.algo = B->algo;
+    L.sel = sel;
+    L.prec = B->prec;
+    L.tol = tol;
+    L.max_iter = max_iter;
+    L.refresh = refresh ? refresh : default_refresh(B->algo, B->prec);
+    L.seed = seed;
+    L.status = status;
+    L.Ntp_max = B->Ntp_max;
+    L.K_max = B->K_max;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
+    e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
+                               : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
+    return check_launch(e, "kz_precode_batched launch");
+}
+
+void kz_batch_destroy(kz_batch* batch) { delete batch; }
+
+kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q, const kz_cf32* X,
+                             const kz_cf32* G_Q, const kz_cf32* G_X, double tol, int32_t max_iter, kz_cf32* lambda,
+                             kz_cf32* y, kz_cf32* grad_H_packed, float* grad_xi, int32_t* iters, double* resid,
+                             int32_t* status, void* stream) {
+    g_err.clear();
+    kz_status rc = check_solve_args("kz_precode_adjoint", plan, nrhs, xi, KZ_VR_OAHK, KZ_SEL_ARGMAX, tol, max_iter, 0, 0);
+    if (rc != KZ_OK) return rc;
+    if (!Q || !X || !lambda || !y || !grad_H_packed || !grad_xi || !iters || !resid || (!G_Q && !G_X)) {
+        kz_set_error("kz_precode_adjoint: Q, X, lambda, y, grad_H_packed, grad_xi, iters, resid and one of G_Q / G_X are required");
+        return KZ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const size_t need = (size_t)plan->K * nrhs;
+    if (plan->scratch_elems < need) {
+        if (plan->d_scratch) cudaFree(plan->d_scratch);
+        plan->d_scratch = nullptr;
+        plan->scratch_elems = 0;
+        cudaError_t e = cudaMalloc((void**)&plan->d_scratch, need * sizeof(float2));
+        if (e != cudaSuccess) {
+            kz_set_error("kz_precode_adjoint: %s", cudaGetErrorString(e));
+            return KZ_ERR_NOMEM;
+        }
+        plan->scratch_elems = need;
+    }
+    KzInst I = plan->inst();
+    I.xi = xi;
+    I.ld = nrhs;
+    cudaError_t e;
+    if (G_X) {
+        e = kz_adjoint_rhs(I, nrhs, reinterpret_cast<const float2*>(G_Q), reinterpret_cast<const float2*>(G_X),
+                           plan->d_scratch, st);
+    } else {
+        e = cudaMemcpyAsync(plan->d_scratch, G_Q, need * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint right-hand side");
+    rc = kz_precode(plan, reinterpret_cast<const kz_cf32*>(plan->d_scratch), nrhs, xi, KZ_VR_OAHK, KZ_SEL_ARGMAX, tol,
+                    max_iter, 0, y, lambda, iters, resid, status, 0, 0, stream);
+    if (rc != KZ_OK) return rc;
+    e = kz_adjoint_contract(I, nrhs, reinterpret_cast<const float2*>(Q), reinterpret_cast<const float2*>(X),
+                            reinterpret_cast<const float2*>(G_X), reinterpret_cast<const float2*>(lambda),
+                            reinterpret_cast<const float2*>(y), plan->d_in_off, reinterpret_cast<float2*>(grad_H_packed),
+                            grad_xi, st);
+    return check_launch(e, "kz_precode_adjoint contraction");
+}
+
+}  // extern "C"

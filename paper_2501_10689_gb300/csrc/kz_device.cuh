@@ -1,0 +1,314 @@
+// Device building blocks of the Kaczmarz sweep over the rows of B = [H, sqrt(xi) I].
+//
+// Shared-memory layouts inside one CTA working on J columns:
+//   m_s[j * Ntp + n]  iterate m (or its correction), antenna-fastest per column;
+//   b_s, q_s, p_s     K x J arrays, element (i, j) at [i * J + j].
+// All reductions run in a fixed order so deterministic methods are bitwise
+// reproducible.
+#pragma once
+
+#include "kz_internal.h"
+
+#define KZ_FULL 0xffffffffu
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(KZ_FULL, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(KZ_FULL, v, o);
+    return v;
+}
+
+// Antenna pair (n, n+1) of a row: {re_n, im_n, re_n+1, im_n+1}.  `off` is the
+// aligned complex offset (even), so the load is 16-byte (C64) / 8-byte (BF16).
+template <bool BF16>
+__device__ __forceinline__ float4 h_pair(const KzInst& I, int off);
+
+template <>
+__device__ __forceinline__ float4 h_pair<false>(const KzInst& I, int off) {
+    return __ldg(reinterpret_cast<const float4*>(I.Hc + off));
+}
+
+template <>
+__device__ __forceinline__ float4 h_pair<true>(const KzInst& I, int off) {
+    const uint2 raw = __ldg(reinterpret_cast<const uint2*>(I.Hb + off));
+    const __nv_bfloat162 a = *reinterpret_cast<const __nv_bfloat162*>(&raw.x);
+    const __nv_bfloat162 b = *reinterpret_cast<const __nv_bfloat162*>(&raw.y);
+    const float2 fa = __bfloat1622float2(a);
+    const float2 fb = __bfloat1622float2(b);
+    return make_float4(fa.x, fa.y, fb.x, fb.y);
+}
+
+// acc[j] = sum_n H[i, n] m[j][n] over row i's aligned interval (warp-wide;
+// every lane holds the result).  Products and sums in FP32.  Four antenna
+// pairs per lane are loaded before they are used, so each lane keeps four
+// independent 16-byte loads in flight.
+template <int J, bool BF16>
+__device__ __forceinline__ void cmac_pair(const float4& h, const float4& mm, float2& acc) {
+    acc.x = fmaf(h.x, mm.x, acc.x);
+    acc.x = fmaf(-h.y, mm.y, acc.x);
+    acc.x = fmaf(h.z, mm.z, acc.x);
+    acc.x = fmaf(-h.w, mm.w, acc.x);
+    acc.y = fmaf(h.x, mm.y, acc.y);
+    acc.y = fmaf(h.y, mm.x, acc.y);
+    acc.y = fmaf(h.z, mm.w, acc.y);
+    acc.y = fmaf(h.w, mm.z, acc.y);
+}
+
+template <int J, bool BF16>
+__device__ __forceinline__ void row_dot(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
+                                        float2 (&acc)[J]) {
+    const int lane = threadIdx.x & 31;
+    const int4 rd = I.rows[i];
+    const int base = I.rptr[i];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
+    int p = 2 * lane;
+    for (; p + 192 < rd.y; p += 256) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = h_pair<BF16>(I, base + p + 64 * u);
+        const int n = rd.x + p;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n + 64 * u);
+                cmac_pair<J, BF16>(h[u], mm, acc[j]);
+            }
+        }
+    }
+    for (; p < rd.y; p += 64) {
+        const float4 h = h_pair<BF16>(I, base + p);
+        const int n = rd.x + p;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n);
+            cmac_pair<J, BF16>(h, mm, acc[j]);
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        acc[j].x = warp_sum(acc[j].x);
+        acc[j].y = warp_sum(acc[j].y);
+    }
+}
+
+// FP64-accumulated variant for true residuals (complex64 H).
+template <int J>
+__device__ __forceinline__ void row_dot_d(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
+                                          double (&ar)[J], double (&ai)[J]) {
+    const int lane = threadIdx.x & 31;
+    const int4 rd = I.rows[i];
+    const int base = I.rptr[i];
+#pragma unroll
+    for (int j = 0; j < J; ++j) ar[j] = ai[j] = 0.0;
+    for (int p = 2 * lane; p < rd.y; p += 64) {
+        const float4 h = h_pair<false>(I, base + p);
+        const int n = rd.x + p;
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n);
+            float pr = h.x * mm.x;
+            pr = fmaf(-h.y, mm.y, pr);
+            float pr2 = h.z * mm.z;
+            pr2 = fmaf(-h.w, mm.w, pr2);
+            float pi = h.x * mm.y;
+            pi = fmaf(h.y, mm.x, pi);
+            float pi2 = h.z * mm.w;
+            pi2 = fmaf(h.w, mm.z, pi2);
+            ar[j] += (double)pr + (double)pr2;
+            ai[j] += (double)pi + (double)pi2;
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        ar[j] = warp_sum_d(ar[j]);
+        ai[j] = warp_sum_d(ai[j]);
+    }
+}
+
+// m[j][n] += g[j] * conj(H[i, n]) on row i's true VR [o, e) (warp-wide).
+// Restricting to the true VR keeps rows of the orthogonal set, whose aligned
+// intervals may share an edge pair, from writing the same element.
+template <int J, bool BF16>
+__device__ __forceinline__ void row_axpy(const KzInst& I, int i, float2* __restrict__ m_s, int Ntp,
+                                         const float2 (&g)[J], int lane, int nlanes) {
+    const int4 rd = I.rows[i];
+    const int base = I.rptr[i];
+    for (int p = 2 * lane; p < rd.y; p += 2 * nlanes) {
+        const float4 h = h_pair<BF16>(I, base + p);
+        const int n = rd.x + p;
+        const bool in0 = (n >= rd.z) && (n < rd.w);
+        const bool in1 = (n + 1 >= rd.z) && (n + 1 < rd.w);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            float2* mp = m_s + j * Ntp + n;
+            if (in0) {
+                float2 v = mp[0];
+                v.x = fmaf(h.x, g[j].x, fmaf(h.y, g[j].y, v.x));
+                v.y = fmaf(h.x, g[j].y, fmaf(-h.y, g[j].x, v.y));
+                mp[0] = v;
+            }
+            if (in1) {
+                float2 v = mp[1];
+                v.x = fmaf(h.z, g[j].x, fmaf(h.w, g[j].y, v.x));
+                v.y = fmaf(h.z, g[j].y, fmaf(-h.w, g[j].x, v.y));
+                mp[1] = v;
+            }
+        }
+    }
+}
+
+// u[j] at antennas (n, n+1), n = 64 * tile + 2 * lane:
+//   u_n = sum_{k in [k0, k1)} conj(H[i_k, n]) * coef[i_k][j]
+// over the covering-row list entries k0..k1 of the tile (antenna-major, no
+// scatter).  trow4[k] = {row, rptr - a, a, a + len2}.  Four rows are fetched
+// before they are used (independent loads in flight).
+template <int J>
+__device__ __forceinline__ void cmac_conj(const float4& h, const float2& c, float2& u0, float2& u1) {
+    u0.x = fmaf(h.x, c.x, fmaf(h.y, c.y, u0.x));
+    u0.y = fmaf(h.x, c.y, fmaf(-h.y, c.x, u0.y));
+    u1.x = fmaf(h.z, c.x, fmaf(h.w, c.y, u1.x));
+    u1.y = fmaf(h.z, c.y, fmaf(-h.w, c.x, u1.y));
+}
+
+template <int J, bool BF16>
+__device__ __forceinline__ void tile_accum(const KzInst& I, const int4* __restrict__ trow4, int tile, int k0,
+                                           int k1, const float2* __restrict__ coef, float2 (&u0)[J],
+                                           float2 (&u1)[J]) {
+    const int lane = threadIdx.x & 31;
+    const int n = tile * KZ_TILE + 2 * lane;
+#pragma unroll
+    for (int j = 0; j < J; ++j) u0[j] = u1[j] = make_float2(0.f, 0.f);
+    int k = k0;
+    for (; k + 3 < k1; k += 4) {
+        int4 e[4];
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) e[u] = __ldg(trow4 + k + u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool in = (n >= e[u].z) && (n < e[u].w);
+            h[u] = in ? h_pair<BF16>(I, e[u].y + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+#pragma unroll
+            for (int j = 0; j < J; ++j) cmac_conj<J>(h[u], coef[e[u].x * J + j], u0[j], u1[j]);
+        }
+    }
+    for (; k < k1; ++k) {
+        const int4 e = __ldg(trow4 + k);
+        if (n >= e.z && n < e.w) {
+            const float4 h = h_pair<BF16>(I, e.y + n);
+#pragma unroll
+            for (int j = 0; j < J; ++j) cmac_conj<J>(h, coef[e.x * J + j], u0[j], u1[j]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): counter-based uniform draws keyed by
+// (seed, instance, column, iteration).
+#define KZ_GOLDEN 0x9E3779B97F4A7C15ull
+
+__device__ __forceinline__ unsigned long long kz_mix64(unsigned long long z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double kz_uniform(unsigned long long seed, int inst, int col, int t) {
+    const unsigned long long ctr = ((unsigned long long)(unsigned)inst << 32) + (unsigned long long)(unsigned)col + 1ull;
+    const unsigned long long key = kz_mix64(seed + ctr * KZ_GOLDEN);
+    const unsigned long long z = kz_mix64(key + (unsigned long long)(t + 1) * KZ_GOLDEN);
+    return (double)(z >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// Warp-wide inverse-CDF draw: the smallest i with (running sum of w up to i)
+// > u * total, weights given per row by `wfun(i)` (FP64).  Each lane owns a
+// contiguous block of rows.  Returns -1 when every weight is zero.
+template <class WF>
+__device__ __forceinline__ int warp_pick(int K, double u, WF wfun) {
+    const int lane = threadIdx.x & 31;
+    const int C = (K + 31) / 32;
+    const int lo = min(lane * C, K), hi = min(lo + C, K);
+    double local = 0.0;
+    int lastpos = -1;
+    for (int i = lo; i < hi; ++i) {
+        const double w = wfun(i);
+        local += w;
+        if (w > 0.0) lastpos = i;
+    }
+    // inclusive scan over lanes
+    double incl = local;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const double y = __shfl_up_sync(KZ_FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const double total = __shfl_sync(KZ_FULL, incl, 31);
+    const double target = u * total;
+    int cand = K;
+    if (total > 0.0 && incl > target) {
+        double cum = incl - local;
+        for (int i = lo; i < hi; ++i) {
+            cum += wfun(i);
+            if (cum > target) {
+                cand = i;
+                break;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cand = min(cand, __shfl_xor_sync(KZ_FULL, cand, o));
+    if (cand == K) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) lastpos = max(lastpos, __shfl_xor_sync(KZ_FULL, lastpos, o));
+        cand = lastpos;
+    }
+    return cand;
+}
+
+// Warp-wide argmax of ratio(i) with the lowest index on ties.
+template <class RF>
+__device__ __forceinline__ int warp_argmax(int K, RF rfun, double* best_out) {
+    const int lane = threadIdx.x & 31;
+    double best = -1.0;
+    int bi = K;
+    for (int i = lane; i < K; i += 32) {
+        const double v = rfun(i);
+        if (v > best) {
+            best = v;
+            bi = i;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(KZ_FULL, best, o);
+        const int oi = __shfl_xor_sync(KZ_FULL, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+            best = ob;
+            bi = oi;
+        }
+    }
+    if (best_out) *best_out = best;
+    return bi < K ? bi : -1;
+}
+
+__device__ __forceinline__ void kz_flag(int* status, int bit) {
+    if (status) atomicOr(status, bit);
+}
+
+// Copy an instance descriptor into shared memory (block-wide; caller syncs).
+__device__ __forceinline__ void load_inst(KzInst& dst, const KzInst* src) {
+    const int nwords = (int)(sizeof(KzInst) / 4);
+    const int* s = reinterpret_cast<const int*>(src);
+    int* d = reinterpret_cast<int*>(&dst);
+    for (int w = threadIdx.x; w < nwords; w += blockDim.x) d[w] = s[w];
+}

@@ -1,0 +1,88 @@
+// Internal definitions shared by the libkzprecode translation units.
+//
+// Device layout of one channel (a "plan"):
+//   * Row k's VR [o_k, e_k) (e_k = o_k + vr_len[k]) is stored over the
+//     aligned interval [a_k, b_k) with a_k = o_k rounded down to even and
+//     b_k = e_k rounded up to even, zero-filled outside [o_k, e_k).  Row k
+//     starts at complex offset rptr[k] (even), so every pair of antennas
+//     (2p, 2p+1) of a row is one 16-byte load, aligned with the same pair of
+//     the iterate m.  Padding entries are exact zeros and contribute nothing
+//     to any product.
+//   * The antenna axis is cut into tiles of KZ_TILE = 64 antennas; tile t
+//     lists the rows whose aligned interval meets it (V rows first, then F
+//     rows), so H^H phi is formed antenna-major with no scatter (each
+//     thread owns one antenna pair and loops over the covering rows).
+//   * Ntp = Nt + 1 rounded up to a whole tile: the length of each iterate
+//     column in shared memory (b_k <= Nt + 1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "../../include/kzprecode.h"
+
+#define KZ_TILE 64
+
+struct KzInst {
+    // --- channel (fixed at plan creation) ---
+    int K, Nt, Ntp, ntiles, nF;
+    int inst;                  // instance number: keys the random streams
+    const int4* rows;          // {a, len2, o, e} per row
+    const int* rptr;           // aligned complex offset of each row
+    const float* nrm;          // ||h_k||^2 (rounded from an FP64 sum)
+    const int* order;          // F rows (ascending) then V rows (ascending)
+    const int* xptr;           // CSR of X_k (k included)
+    const int* xidx;
+    const int* tptr;           // CSR of covering rows per tile
+    const int* tnv;            // number of V rows at the head of each tile list
+    const int4* trow4;         // per entry {row, rptr - a, a, a + len2}
+    const float2* Hc;          // aligned complex64 rows
+    const __nv_bfloat162* Hb;  // aligned BF16 (re, im) rows, or nullptr
+    double sum_nrm;            // sum_k ||h_k||^2 (FP64)
+    // --- call ---
+    float xi;
+    int ld;                    // number of columns of s / x / v
+    const float2* s;
+    float2* x;
+    float2* v;
+    int* iters;
+    double* resid;
+};
+
+struct KzLaunch {
+    const KzInst* insts;  // batched: device table; nullptr: use `single`
+    KzInst single;
+    const int2* items;    // batched: {instance, first column}; nullptr: item k = columns [kJ, kJ+J)
+    int n_items;
+    int* queue;           // work-queue counter (zeroed before the launch), or nullptr
+    int algo, sel, prec;
+    double tol;
+    int max_iter;
+    int refresh;
+    unsigned long long seed;
+    int* status;
+    int Ntp_max, K_max;
+};
+
+// Host-side launchers (kz_ahk.cu / kz_kacz.cu).
+cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
+cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
+size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
+size_t kz_smem_kacz(int J, int Ntp, int K);
+int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
+int kz_occupancy_kacz(int J, int nw, size_t smem);
+
+// Auxiliary kernels (kz_aux.cu).
+cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows, const int* rptr, int K,
+                         int64_t total2, float2* Hc, __nv_bfloat162* Hb, cudaStream_t st);
+cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d,
+                         float* out_f, cudaStream_t st);
+cudaError_t kz_adjoint_rhs(const KzInst& I, int nrhs, const float2* G_Q, const float2* G_X, float2* Gt,
+                           cudaStream_t st);
+cudaError_t kz_adjoint_contract(const KzInst& I, int nrhs, const float2* Q, const float2* X,
+                                const float2* G_X, const float2* Lam, const float2* Y,
+                                const int* in_off, float2* grad_H, float* grad_xi, cudaStream_t st);
+
+// Thread-local last-error text (kz_api.cu).
+void kz_set_error(const char* fmt, ...);

@@ -1,0 +1,258 @@
+"""ctypes binding of libkzprecode (argument marshalling only).
+
+Every function named like a C entry point takes the same arguments, with
+torch CUDA tensors in place of device pointers and NumPy int32 arrays in place
+of host arrays, and returns what the C call returns (raising ``KzError`` on a
+non-OK status).  All arithmetic runs in the CUDA library; when the shared
+library is missing this module raises instead of falling back to anything.
+
+Layouts: a K x nrhs column-major matrix is a contiguous torch tensor of shape
+(nrhs, K) (one row per right-hand side); likewise x is (nrhs, Nt).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+from . import _build
+
+# enums of include/kzprecode.h
+KZ_OK, KZ_NOT_CONVERGED, KZ_ERR_INVALID_ARG, KZ_ERR_NUMERIC, KZ_ERR_CUDA, KZ_ERR_NOMEM, KZ_ERR_UNSUPPORTED = range(7)
+KZ_STATUS_BIT_NOT_CONVERGED, KZ_STATUS_BIT_NUMERIC = 1, 2
+ALGOS = {"rk_energy": 0, "rk_uniform": 1, "grk": 2, "ahk": 3, "vr_ogrk": 4, "vr_oahk": 5}
+SELECT = {"paper": 0, "baiwu": 1, "argmax": 2}
+PREC = {"c64": 0, "bf16": 1}
+
+_lib = None
+
+
+class KzError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libkzprecode status {code}: {msg}")
+        self.code = code
+
+
+class KzBatchItem(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("s", ctypes.c_void_p), ("x", ctypes.c_void_p),
+                ("v", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p),
+                ("xi", ctypes.c_float)]
+
+
+EXPORTS = ("kz_plan_create", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_batch_prepare",
+           "kz_precode_batched", "kz_batch_destroy", "kz_precode_adjoint", "kz_last_error", "kz_version")
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load():
+    """Load the shared library (built by ``_build.build``); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I32, I64, F32, F64, U64 = (ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_float,
+                                  ctypes.c_double, ctypes.c_uint64)
+    lib.kz_plan_create.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
+    lib.kz_plan_create.restype = I32
+    lib.kz_plan_destroy.argtypes = [P]
+    lib.kz_plan_destroy.restype = None
+    lib.kz_plan_query.argtypes = [P, P, P, P, P, P, P, P]
+    lib.kz_plan_query.restype = I32
+    lib.kz_precode.argtypes = [P, P, I32, F32, I32, I32, F64, I32, U64, P, P, P, P, P, I32, I32, P]
+    lib.kz_precode.restype = I32
+    lib.kz_batch_prepare.argtypes = [ctypes.POINTER(P), P, I32, I32, I32, I32, I32, P]
+    lib.kz_batch_prepare.restype = I32
+    lib.kz_precode_batched.argtypes = [P, I32, F64, I32, U64, I32, P, P]
+    lib.kz_precode_batched.restype = I32
+    lib.kz_batch_destroy.argtypes = [P]
+    lib.kz_batch_destroy.restype = None
+    lib.kz_precode_adjoint.argtypes = [P, I32, F32, P, P, P, P, F64, I32, P, P, P, P, P, P, P, P]
+    lib.kz_precode_adjoint.restype = I32
+    lib.kz_last_error.argtypes = []
+    lib.kz_last_error.restype = ctypes.c_char_p
+    lib.kz_version.argtypes = []
+    lib.kz_version.restype = I32
+    _lib = lib
+    return lib
+
+
+def _check(code):
+    if code not in (KZ_OK,):
+        raise KzError(code, load().kz_last_error().decode())
+    return code
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _check_c64(t, shape, name):
+    if t.dtype != torch.complex64 or tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name}: expected complex64 tensor of shape {tuple(shape)}, got {t.dtype} {tuple(t.shape)}")
+
+
+class Plan:
+    """Owner of a ``kz_plan*``."""
+
+    def __init__(self, handle, K, Nt, sum_len, prec):
+        self.handle = handle
+        self.K, self.Nt, self.sum_len, self.prec = K, Nt, sum_len, prec
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kz_plan_destroy(self.handle)
+            self.handle = None
+
+
+def kz_plan_create(K, Nt, vr_offset, vr_len, H_packed, prec="c64", stream=None) -> Plan:
+    lib = load()
+    off = np.ascontiguousarray(vr_offset, dtype=np.int32)
+    ln = np.ascontiguousarray(vr_len, dtype=np.int32)
+    if off.shape != (K,) or ln.shape != (K,):
+        raise ValueError("vr_offset and vr_len must have K entries")
+    _check_c64(H_packed, (int(ln.sum()),), "H_packed")
+    h = ctypes.c_void_p()
+    _check(lib.kz_plan_create(ctypes.byref(h), K, Nt, off.ctypes.data_as(ctypes.c_void_p),
+                              ln.ctypes.data_as(ctypes.c_void_p), _ptr(H_packed), PREC[prec], _stream(stream)))
+    return Plan(h, K, Nt, int(ln.sum()), prec)
+
+
+def kz_plan_query(plan: Plan):
+    lib = load()
+    K = plan.K
+    nF = ctypes.c_int32()
+    F = np.zeros(K, dtype=np.int32)
+    xptr = np.zeros(K + 1, dtype=np.int32)
+    xidx = np.zeros(K * K, dtype=np.int32)
+    _check(lib.kz_plan_query(plan.handle, None, None, None, ctypes.byref(nF), F.ctypes.data_as(ctypes.c_void_p),
+                             xptr.ctypes.data_as(ctypes.c_void_p), xidx.ctypes.data_as(ctypes.c_void_p)))
+    return F[:nF.value].copy(), xptr, xidx[:xptr[-1]].copy()
+
+
+def kz_precode(plan: Plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status=None,
+               rhs_per_cta=0, refresh=0, stream=None):
+    lib = load()
+    _check_c64(s, (nrhs, plan.K), "s")
+    _check_c64(x, (nrhs, plan.Nt), "x")
+    if v is not None:
+        _check_c64(v, (nrhs, plan.K), "v")
+    if iters.dtype != torch.int32 or resid.dtype != torch.float64:
+        raise ValueError("iters must be int32 and resid float64")
+    return _check(lib.kz_precode(plan.handle, _ptr(s), nrhs, float(xi), ALGOS[algo] if isinstance(algo, str) else algo,
+                                 SELECT[sel] if isinstance(sel, str) else sel, float(tol), int(max_iter),
+                                 int(seed), _ptr(x), _ptr(v), _ptr(iters), _ptr(resid), _ptr(status),
+                                 int(rhs_per_cta), int(refresh), _stream(stream)))
+
+
+class Batch:
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep  # the plans and tensors the device table points at
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.kz_batch_destroy(self.handle)
+            self.handle = None
+
+
+def kz_batch_prepare(items, nrhs, algo, prec="c64", rhs_per_cta=0, stream=None) -> Batch:
+    """``items``: list of dicts with plan, s, x, v (or None), iters, resid, xi."""
+    lib = load()
+    arr = (KzBatchItem * len(items))()
+    keep = []
+    for k, it in enumerate(items):
+        p = it["plan"]
+        _check_c64(it["s"], (nrhs, p.K), "s")
+        _check_c64(it["x"], (nrhs, p.Nt), "x")
+        arr[k] = KzBatchItem(p.handle.value, it["s"].data_ptr(), it["x"].data_ptr(),
+                             it["v"].data_ptr() if it.get("v") is not None else None, it["iters"].data_ptr(),
+                             it["resid"].data_ptr(), float(it["xi"]))
+        keep.append(it)
+    h = ctypes.c_void_p()
+    _check(lib.kz_batch_prepare(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(items), nrhs,
+                                ALGOS[algo] if isinstance(algo, str) else algo, PREC[prec], int(rhs_per_cta),
+                                _stream(stream)))
+    return Batch(h, keep)
+
+
+def kz_precode_batched(batch: Batch, sel, tol, max_iter, seed, refresh=0, status=None, stream=None):
+    lib = load()
+    return _check(lib.kz_precode_batched(batch.handle, SELECT[sel] if isinstance(sel, str) else sel, float(tol),
+                                         int(max_iter), int(seed), int(refresh), _ptr(status), _stream(stream)))
+
+
+def kz_precode_adjoint(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam, y, grad_H_packed, grad_xi, iters,
+                       resid, status=None, stream=None):
+    lib = load()
+    return _check(lib.kz_precode_adjoint(plan.handle, nrhs, float(xi), _ptr(Q), _ptr(X), _ptr(G_Q), _ptr(G_X),
+                                         float(tol), int(max_iter), _ptr(lam), _ptr(y), _ptr(grad_H_packed),
+                                         _ptr(grad_xi), _ptr(iters), _ptr(resid), _ptr(status), _stream(stream)))
+
+
+def kz_version() -> int:
+    return load().kz_version()
+
+
+def exported_symbols():
+    """Names of EXPORTS that the loaded library resolves."""
+    lib = load()
+    return [n for n in EXPORTS if hasattr(lib, n)]
+
+
+# ----------------------------------------------------------------- convenience
+def precode(plan: Plan, S, xi, algo="vr_oahk", sel="paper", tol=1e-6, max_iter=1000, seed=0, rhs_per_cta=0,
+            refresh=0, want_v=True, sync=True):
+    """Allocate outputs, run ``kz_precode`` and (by default) wait for it.
+
+    ``S`` is a torch CUDA complex64 tensor of shape (nrhs, K).  Returns a dict
+    with x (nrhs, Nt), v (nrhs, K), iters, resid and the status word.
+    """
+    nrhs = S.shape[0]
+    dev = S.device
+    x = torch.empty((nrhs, plan.Nt), dtype=torch.complex64, device=dev)
+    v = torch.empty((nrhs, plan.K), dtype=torch.complex64, device=dev) if want_v else None
+    iters = torch.empty(nrhs, dtype=torch.int32, device=dev)
+    resid = torch.empty(nrhs, dtype=torch.float64, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    kz_precode(plan, S, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status, rhs_per_cta, refresh)
+    out = {"x": x, "v": v, "iters": iters, "resid": resid, "status": status}
+    if sync:
+        torch.cuda.synchronize(dev)
+        st = int(status.item())
+        if st & KZ_STATUS_BIT_NUMERIC:
+            raise KzError(KZ_ERR_NUMERIC, "NaN or Inf in a residual")
+        out["converged"] = not (st & KZ_STATUS_BIT_NOT_CONVERGED)
+    return out
+
+
+def plan_from_instance(inst, prec="c64", device="cuda"):
+    """Upload a ``kzgen.Instance``'s packed channel and build its plan."""
+    Hp = torch.from_numpy(np.ascontiguousarray(inst.H_packed)).to(device)
+    return kz_plan_create(inst.K, inst.Nt, inst.vr_offset, inst.vr_len, Hp, prec=prec)
+
+
+def rhs_tensor(S_np, device="cuda"):
+    """A K x nrhs NumPy matrix as the (nrhs, K) column-major device layout."""
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(S_np, dtype=np.complex64).T)).to(device)

@@ -1,0 +1,163 @@
+"""Batching, BF16-mixed precision and the adjoint against the FP64 oracle (GB300)."""
+import numpy as np
+import pytest
+
+import kzgen
+from oracle import adjoint as oadj
+from oracle import rzf as orz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kp():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_10689_gb300 import kzprecode
+    return kzprecode
+
+
+def make_items(kp, insts, nrhs, prec="c64"):
+    items = []
+    for inst in insts:
+        p = kp.plan_from_instance(inst, prec=prec)
+        items.append(dict(plan=p, s=kp.rhs_tensor(inst.S), x=torch.empty((nrhs, inst.Nt), dtype=torch.complex64,
+                                                                           device="cuda"),
+                          v=torch.empty((nrhs, inst.K), dtype=torch.complex64, device="cuda"),
+                          iters=torch.empty(nrhs, dtype=torch.int32, device="cuda"),
+                          resid=torch.empty(nrhs, dtype=torch.float64, device="cuda"), xi=inst.xi))
+    return items
+
+
+def uneven(n, nrhs, seed0=100):
+    out = []
+    rng = np.random.default_rng(seed0)
+    for i in range(n):
+        Nt = int(rng.choice([96, 257, 640]))
+        K = int(rng.integers(3, 40))
+        out.append(kzgen.make_instance(seed0 + i, K, Nt, vr_frac_range=(0.1, 0.4), nrhs=nrhs))
+    return out
+
+
+@pytest.mark.parametrize("algo", ["vr_oahk", "ahk", "grk", "vr_ogrk", "rk_energy"])
+def test_batched_matches_oracle_and_single(kp, algo):
+    insts = uneven(9, 5)
+    items = make_items(kp, insts, 5)
+    b = kp.kz_batch_prepare(items, 5, algo, rhs_per_cta=2)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_batched(b, "argmax", 1e-7, 200000, 3, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    for inst, it in zip(insts, items):
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        x = it["x"].cpu().numpy().T
+        assert np.all(orz.rel_err(x, X) <= TOL_X)
+        single = kp.precode(it["plan"], kp.rhs_tensor(inst.S), inst.xi, algo=algo, sel="argmax", tol=1e-7,
+                            max_iter=200000, rhs_per_cta=2)
+        np.testing.assert_array_equal(single["iters"].cpu().numpy(), it["iters"].cpu().numpy())
+
+
+def test_batched_graph_replay(kp):
+    """The batched call is capturable: replaying the graph reproduces the result."""
+    insts = uneven(5, 3, seed0=300)
+    items = make_items(kp, insts, 3)
+    b = kp.kz_batch_prepare(items, 3, "vr_oahk")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        kp.kz_precode_batched(b, "paper", 1e-7, 2000, 0, status=st)
+    torch.cuda.synchronize()
+    first = [it["x"].clone() for it in items]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        kp.kz_precode_batched(b, "paper", 1e-7, 2000, 0, status=st)
+    for it in items:
+        it["x"].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    for a, it in zip(first, items):
+        assert torch.equal(a, it["x"])
+
+
+def test_full_size_batch_sampled(kp):
+    """The 512-instance, 16-column batch the benchmark times, in the same launch
+    configuration; a sample of instances is checked against the FP64 RZF."""
+    import bench
+    insts = kzgen.config3(512)
+    items = make_items(kp, insts, 16)
+    b = kp.kz_batch_prepare(items, 16, "vr_oahk")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_batched(b, "paper", bench.TOL, bench.MAX_ITER, 0, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    resid = np.concatenate([it["resid"].cpu().numpy() for it in items])
+    assert np.all(resid <= bench.TOL * (1 + 1e-6))
+    for k in range(0, 512, 37):
+        inst = insts[k]
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        assert np.all(orz.rel_err(items[k]["x"].cpu().numpy().T, X) <= TOL_X), k
+
+
+@pytest.mark.parametrize("algo", ["vr_oahk", "ahk"])
+def test_bf16_mixed_refines_to_fp32_accuracy(kp, algo):
+    """BF16 H in the iteration, complex64 / FP64 true residual in the refresh:
+    the result still meets 1e-5 against the FP64 RZF."""
+    inst = kzgen.make_instance(77, 40, 700, vr_len_range=(60, 260), nrhs=6, snr_db=10.0)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    plan = kp.plan_from_instance(inst, prec="bf16")
+    out = kp.precode(plan, kp.rhs_tensor(inst.S), inst.xi, algo=algo, tol=1e-7, max_iter=3000)
+    assert out["converged"]
+    err = orz.rel_err(out["x"].cpu().numpy().T, X)
+    assert np.all(err <= TOL_X), err
+    assert np.all(out["resid"].cpu().numpy() <= 1e-7 * (1 + 1e-6))
+
+
+def test_bf16_mixed_large_elaa(kp):
+    """Large-array shape: Nt = 16384, K = 512, VR 1024-4096, 64 columns."""
+    inst = kzgen.config4()
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    plan = kp.plan_from_instance(inst, prec="bf16")
+    out = kp.precode(plan, kp.rhs_tensor(inst.S), inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000)
+    assert out["converged"]
+    err = orz.rel_err(out["x"].cpu().numpy().T, X)
+    assert np.max(err) <= TOL_X, np.max(err)
+
+
+def _gpu_gradient(kp, inst, tol=1e-7):
+    from paper_2501_10689_gb300 import autograd as kad
+    Hp = torch.tensor(inst.H_packed, device="cuda", requires_grad=True)
+    xi = torch.tensor(inst.xi, dtype=torch.float32, device="cuda", requires_grad=True)
+    S = kp.rhs_tensor(inst.S)
+    X, V = kad.precode(Hp, xi, S, inst.vr_offset, inst.vr_len, inst.Nt, tol=tol)
+    Hd = kad.dense_from_packed(Hp, inst.vr_offset, inst.vr_len, inst.Nt)
+    L = kad.sum_rate_loss(Hd, X, 10.0 ** (inst.snr_db / 10.0))
+    L.backward()
+    return float(L.item()), Hp.grad.cpu().numpy().astype(np.complex128), float(xi.grad.item())
+
+
+def test_adjoint_gradient_small_vs_fd_and_dense(kp):
+    inst = kzgen.make_instance(5, 8, 96, vr_len_range=(12, 40), nrhs=8, rhs="identity", snr_db=10.0)
+    L_ref, gH_ref, gxi_ref = oadj.reference_gradient(inst)
+    L, gH, gxi = _gpu_gradient(kp, inst)
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert abs(gxi - gxi_ref) <= 1e-3 * abs(gxi_ref)
+    assert np.linalg.norm(gH - gH_ref) <= 1e-3 * np.linalg.norm(gH_ref)
+    picks = [0, 17, 55, int(inst.H_packed.size) - 1]
+    fd = oadj.central_difference(inst, [("xi",)] + [("re", p) for p in picks] + [("im", p) for p in picks], h=1e-4)
+    got = np.array([gxi] + [gH[p].real for p in picks] + [gH[p].imag for p in picks])
+    assert np.max(np.abs(got - fd)) <= 1e-3 * np.max(np.abs(fd))
+
+
+def test_adjoint_gradient_full_channel(kp):
+    """One channel of the gradient batch: Nt = 2048, K = 128, VR 256-1024, identity symbols."""
+    inst = kzgen.config5_instance(0)
+    L_ref, gH_ref, gxi_ref = oadj.reference_gradient(inst)
+    L, gH, gxi = _gpu_gradient(kp, inst)
+    assert abs(L - L_ref) <= 1e-5 * abs(L_ref)
+    assert abs(gxi - gxi_ref) <= 1e-4 * abs(gxi_ref)
+    assert np.linalg.norm(gH - gH_ref) <= 1e-4 * np.linalg.norm(gH_ref)
