@@ -183,6 +183,31 @@ kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf3
                              float* grad_xi, int32_t* iters, double* resid, int32_t* status,
                              void* stream);
 
+/* The adjoint above without any device allocation.  The paper has no
+ * counterpart; this entry exists for callers that cannot allocate device memory
+ * when they differentiate: a backward pass recorded into a CUDA graph (a device
+ * allocation is not a stream operation, so a replay would not repeat it), a
+ * real-time loop that must not block in the driver's allocator, or a process
+ * whose device memory is reserved up front by another allocator.
+ * kz_precode_adjoint keeps its right-hand side G~ (K x nrhs) in plan-owned
+ * memory that it allocates on first use; this variant keeps G~ in one
+ * file-scope device array of 262144 complex entries (2 MiB), which every GPU
+ * that loads the library holds until the process exits.
+ *   Arguments, outputs and errors are those of kz_precode_adjoint (the plan
+ *   itself is created beforehand with kz_plan_create).  K * nrhs above 262144
+ *   returns KZ_ERR_INVALID_ARG with a message; nothing is enqueued then.
+ *   The first call on a device looks up the array's device address (with that
+ *   device current) and caches it; make that first call before any stream
+ *   capture.  All calls share the one array, which keeps the last call's
+ *   contents: calls that overlap on the GPU (different streams or devices
+ *   sharing nothing but the library) race on it, so serialise them.  Every
+ *   entry of G~ the solve reads is written first, so nothing needs clearing. */
+kz_status kz_precode_adjoint_noalloc(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q,
+                                     const kz_cf32* X, const kz_cf32* G_Q, const kz_cf32* G_X,
+                                     double tol, int32_t max_iter, kz_cf32* lambda, kz_cf32* y,
+                                     kz_cf32* grad_H_packed, float* grad_xi, int32_t* iters,
+                                     double* resid, int32_t* status, void* stream);
+
 /* One-line description of the last error on this thread ("" if none). */
 const char* kz_last_error(void);
 

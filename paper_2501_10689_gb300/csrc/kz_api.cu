@@ -619,3 +619,87 @@ kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf3
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint.  Some callers cannot allocate device memory at the
+// time they differentiate: a backward pass recorded into a CUDA graph (a
+// device allocation is not a stream operation and would not be replayed), a
+// real-time loop that must not block in the driver's allocator, or a process
+// whose device memory is reserved up front by another allocator.  For them
+// the right-hand side G~ = G_Q + H G_X, the only scratch of the adjoint, lives
+// in this file-scope device array instead of plan-owned memory.
+namespace {
+
+constexpr int64_t kNoAllocMaxElems = 262144;  // K * nrhs complex entries (2 MiB)
+static __device__ __align__(256) float2 g_kz_adjoint_scratch[kNoAllocMaxElems];
+
+constexpr int kNoAllocMaxDevices = 64;
+float2* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+
+// Host code cannot use the array's name as a device address; fetch the
+// address once per device, with that device current.
+kz_status noalloc_scratch(float2** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint_noalloc cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) {
+        kz_set_error("kz_precode_adjoint_noalloc: device %d is beyond the supported %d", dev, kNoAllocMaxDevices);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_kz_adjoint_scratch);
+        if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint_noalloc cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = static_cast<float2*>(p);
+    }
+    *out = g_noalloc_ptr[dev];
+    return KZ_OK;
+}
+
+}  // namespace
+
+extern "C" kz_status kz_precode_adjoint_noalloc(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q,
+                                                const kz_cf32* X, const kz_cf32* G_Q, const kz_cf32* G_X,
+                                                double tol, int32_t max_iter, kz_cf32* lambda, kz_cf32* y,
+                                                kz_cf32* grad_H_packed, float* grad_xi, int32_t* iters,
+                                                double* resid, int32_t* status, void* stream) {
+    g_err.clear();
+    kz_status rc = check_solve_args("kz_precode_adjoint_noalloc", plan, nrhs, xi, KZ_VR_OAHK, KZ_SEL_ARGMAX, tol,
+                                    max_iter, 0, 0);
+    if (rc != KZ_OK) return rc;
+    if (!Q || !X || !lambda || !y || !grad_H_packed || !grad_xi || !iters || !resid || (!G_Q && !G_X)) {
+        kz_set_error("kz_precode_adjoint_noalloc: Q, X, lambda, y, grad_H_packed, grad_xi, iters, resid and one of "
+                     "G_Q / G_X are required");
+        return KZ_ERR_INVALID_ARG;
+    }
+    const int64_t need = (int64_t)plan->K * nrhs;
+    if (need > kNoAllocMaxElems) {
+        kz_set_error("kz_precode_adjoint_noalloc: K * nrhs = %lld exceeds the static scratch of %lld entries",
+                     (long long)need, (long long)kNoAllocMaxElems);
+        return KZ_ERR_INVALID_ARG;
+    }
+    float2* scratch = nullptr;
+    rc = noalloc_scratch(&scratch);
+    if (rc != KZ_OK) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    KzInst I = plan->inst();
+    I.xi = xi;
+    I.ld = nrhs;
+    // every entry of G~ that the solve reads is written first, so nothing is cleared
+    cudaError_t e;
+    if (G_X) {
+        e = kz_adjoint_rhs(I, nrhs, reinterpret_cast<const float2*>(G_Q), reinterpret_cast<const float2*>(G_X),
+                           scratch, st);
+    } else {
+        e = cudaMemcpyAsync(scratch, G_Q, (size_t)need * sizeof(float2), cudaMemcpyDeviceToDevice, st);
+    }
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint_noalloc right-hand side");
+    rc = kz_precode(plan, reinterpret_cast<const kz_cf32*>(scratch), nrhs, xi, KZ_VR_OAHK, KZ_SEL_ARGMAX, tol,
+                    max_iter, 0, y, lambda, iters, resid, status, 0, 0, stream);
+    if (rc != KZ_OK) return rc;
+    e = kz_adjoint_contract(I, nrhs, reinterpret_cast<const float2*>(Q), reinterpret_cast<const float2*>(X),
+                            reinterpret_cast<const float2*>(G_X), reinterpret_cast<const float2*>(lambda),
+                            reinterpret_cast<const float2*>(y), plan->d_in_off,
+                            reinterpret_cast<float2*>(grad_H_packed), grad_xi, st);
+    return check_launch(e, "kz_precode_adjoint_noalloc contraction");
+}

@@ -42,7 +42,8 @@ class KzBatchItem(ctypes.Structure):
 
 
 EXPORTS = ("kz_plan_create", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_batch_prepare",
-           "kz_precode_batched", "kz_batch_destroy", "kz_precode_adjoint", "kz_last_error", "kz_version")
+           "kz_precode_batched", "kz_batch_destroy", "kz_precode_adjoint", "kz_precode_adjoint_noalloc",
+           "kz_last_error", "kz_version")
 
 
 def library_path() -> str:
@@ -76,6 +77,8 @@ def load():
     lib.kz_batch_destroy.restype = None
     lib.kz_precode_adjoint.argtypes = [P, I32, F32, P, P, P, P, F64, I32, P, P, P, P, P, P, P, P]
     lib.kz_precode_adjoint.restype = I32
+    lib.kz_precode_adjoint_noalloc.argtypes = [P, I32, F32, P, P, P, P, F64, I32, P, P, P, P, P, P, P, P]
+    lib.kz_precode_adjoint_noalloc.restype = I32
     lib.kz_last_error.argtypes = []
     lib.kz_last_error.restype = ctypes.c_char_p
     lib.kz_version.argtypes = []
@@ -209,6 +212,18 @@ def kz_precode_adjoint(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam,
     return _check(lib.kz_precode_adjoint(plan.handle, nrhs, float(xi), _ptr(Q), _ptr(X), _ptr(G_Q), _ptr(G_X),
                                          float(tol), int(max_iter), _ptr(lam), _ptr(y), _ptr(grad_H_packed),
                                          _ptr(grad_xi), _ptr(iters), _ptr(resid), _ptr(status), _stream(stream)))
+
+
+def kz_precode_adjoint_noalloc(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam, y, grad_H_packed, grad_xi,
+                               iters, resid, status=None, stream=None):
+    """The adjoint without device allocation (for callers that cannot allocate
+    when they differentiate, e.g. inside a captured CUDA graph); its scratch is a
+    fixed 2 MiB device array shared by all calls, so K * nrhs <= 262144."""
+    lib = load()
+    return _check(lib.kz_precode_adjoint_noalloc(plan.handle, nrhs, float(xi), _ptr(Q), _ptr(X), _ptr(G_Q),
+                                                 _ptr(G_X), float(tol), int(max_iter), _ptr(lam), _ptr(y),
+                                                 _ptr(grad_H_packed), _ptr(grad_xi), _ptr(iters), _ptr(resid),
+                                                 _ptr(status), _stream(stream)))
 
 
 def kz_version() -> int:
