@@ -193,6 +193,10 @@ def run_ours(args):
     batch = kp.kz_batch_prepare(items, NRHS, "vr_oahk", rhs_per_cta=args.rhs_per_cta)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
+    tuned = None
+    if args.rhs_per_cta == 0:
+        with torch.cuda.stream(stream):
+            tuned = kp.kz_batch_tune(batch, "paper", TOL, MAX_ITER, 0)
 
     def launch():
         kp.kz_precode_batched(batch, "paper", TOL, MAX_ITER, 0, status=status)
@@ -328,7 +332,10 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": {"workload": workload_desc(), "instances_per_gpu": args.instances, "nrhs": NRHS,
-                           "tol": TOL, "max_iter": MAX_ITER, "rhs_per_cta": batch and args.rhs_per_cta,
+                           "tol": TOL, "max_iter": MAX_ITER,
+                           "launch": ({"kernel": tuned[0], "rhs_per_cta": tuned[1], "threads": tuned[2],
+                                       "chosen_by": "kz_batch_tune"}
+                                      if tuned else {"rhs_per_cta": args.rhs_per_cta}),
                            "l2": "inputs larger than L2 (packed H of the batch is %.0f MB)" % (float(sumL.sum()) * 8 / 1e6),
                            "graph": "CUDA graph replay of queue reset + persistent kernel"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,

@@ -89,6 +89,16 @@ typedef enum { KZ_SEL_PAPER = 0, KZ_SEL_BAIWU = 1, KZ_SEL_ARGMAX = 2 } kz_select
  * refresh period; that recomputation drives the stopping test. */
 typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
 
+/* Which kernel runs AHK / VR_OAHK.  RESIDENT keeps the iterate m of J
+ * columns in shared memory and streams H per column group (every method,
+ * both precisions).  DUAL (AHK / VR_OAHK, C64) keeps only q and the residual
+ * r = s - B B^H q of 8 or 16 columns, updates r by r -= gamma (H H^H phi + xi phi)
+ * (the same iterates as eq. (update4)), stages each 64-antenna tile of H in
+ * shared memory once per pass for all its columns, and recomputes the true
+ * residual to confirm stops.  AUTO: RESIDENT for kz_precode; the batch
+ * default is RESIDENT until kz_batch_tune or kz_batch_set_launch chooses. */
+typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_DUAL = 2 } kz_kernel;
+
 typedef struct kz_plan kz_plan;
 typedef struct kz_batch kz_batch;
 
@@ -136,6 +146,14 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
                      kz_cf32* v, int32_t* iters, double* resid, int32_t* status, int32_t rhs_per_cta,
                      int32_t refresh, void* stream);
 
+/* kz_precode with an explicit kernel (see kz_kernel).  With KZ_KERNEL_DUAL,
+ * rhs_per_cta must be 0, 8 or 16 (0: 16 when nrhs >= 16 and it fits, else 8)
+ * and algo AHK or VR_OAHK on a C64 plan (else KZ_ERR_UNSUPPORTED). */
+kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
+                        kz_select sel, double tol, int32_t max_iter, uint64_t seed, kz_cf32* x,
+                        kz_cf32* v, int32_t* iters, double* resid, int32_t* status, kz_kernel kernel,
+                        int32_t rhs_per_cta, int32_t refresh, void* stream);
+
 /* One item of a batch: a plan with its own right-hand sides and outputs
  * (layouts as in kz_precode, all device pointers, nrhs columns each). */
 typedef struct {
@@ -164,6 +182,24 @@ kz_status kz_precode_batched(kz_batch* batch, kz_select sel, double tol, int32_t
                              uint64_t seed, int32_t refresh, int32_t* status, void* stream);
 
 void kz_batch_destroy(kz_batch* batch);
+
+/* Autotune a prepared batch (step A8's launch shape): time every feasible
+ * launch on the batch itself -- the RESIDENT kernel with columns-per-CTA in
+ * {1, 2, 4, 8} and 256 or 512 threads, and for AHK / VR_OAHK on C64 the DUAL
+ * kernel with 8 columns (256 or 512 threads) or 16 columns (512 threads) --
+ * three runs each, the last two timed with CUDA events on `stream`; keep the
+ * fastest and write it to chosen (host int32[3]: kernel, columns per CTA,
+ * threads; may be NULL).  It solves the batch repeatedly, so the batch's
+ * outputs hold a valid result afterwards.  Synchronous. */
+kz_status kz_batch_tune(kz_batch* batch, kz_select sel, double tol, int32_t max_iter, uint64_t seed,
+                        int32_t* chosen, void* stream);
+
+/* Fix a batch's launch: kernel (RESIDENT or DUAL), columns per CTA (RESIDENT:
+ * 1, 2, 4, 8; DUAL: 8, 16) and threads (256 or 512; DUAL with 16 columns:
+ * 512).  Rebuilds the work list; synchronous.  KZ_ERR_UNSUPPORTED if the
+ * combination does not fit shared memory or the batch's method. */
+kz_status kz_batch_set_launch(kz_batch* batch, kz_kernel kernel, int32_t rhs_per_cta, int32_t threads,
+                              void* stream);
 
 /* Adjoint (implicit differentiation) of Q = (H H^H + xi I)^-1 S, X = H^H Q for
  * a real loss L.  Given the gradients G_Q (K x nrhs) and G_X (Nt x nrhs) of L

@@ -28,7 +28,7 @@ namespace {
 constexpr int ALGO_OAHK = KZ_VR_OAHK;
 
 template <int J, int NW, bool BF16>
-__global__ void __launch_bounds__(NW * 32) kz_ahk_kernel(const __grid_constant__ KzLaunch L) {
+__global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32))) kz_ahk_kernel(const __grid_constant__ KzLaunch L) {
     extern __shared__ __align__(16) unsigned char kz_smem[];
     __shared__ KzInst sI;
     __shared__ float s_part[NW][3 * J];
@@ -141,23 +141,31 @@ __global__ void __launch_bounds__(NW * 32) kz_ahk_kernel(const __grid_constant__
             float pr[J], pn[J], pp[J];
 #pragma unroll
             for (int j = 0; j < J; ++j) pr[j] = pn[j] = pp[j] = 0.f;
-            for (int v = warp; v < vcount; v += NW) {
-                const int i = I.order[v0 + v];
-                float2 acc[J];
-                row_dot<J, BF16>(I, i, m_s, Ntp, acc);
-                const float di = d_s[i];
+            // rows v and v + NW go to the same warp together (two loads streams)
+            for (int v = warp; v < vcount; v += 2 * NW) {
+                const int i0 = I.order[v0 + v];
+                const int i1 = (v + NW < vcount) ? I.order[v0 + v + NW] : -1;
+                float2 acc0[J], acc1[J];
+                row_dot2<J, BF16>(I, i0, i1, m_s, Ntp, acc0, acc1);
 #pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
-                    const float rx = bv.x - acc[j].x - xi * qv.x;
-                    const float ry = bv.y - acc[j].y - xi * qv.y;
-                    const float r2 = rx * rx + ry * ry;
-                    const bool on = (act >> j) & 1;
-                    const float2 ph = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
-                    pr[j] += r2;
-                    pn[j] += on ? r2 / di : 0.f;
-                    pp[j] += ph.x * ph.x + ph.y * ph.y;
-                    if (lane == 0) p_s[i * J + j] = ph;
+                for (int rr = 0; rr < 2; ++rr) {
+                    const int i = rr ? i1 : i0;
+                    if (i < 0) continue;
+                    const float di = d_s[i];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float2 a = rr ? acc1[j] : acc0[j];
+                        const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                        const float rx = bv.x - a.x - xi * qv.x;
+                        const float ry = bv.y - a.y - xi * qv.y;
+                        const float r2 = rx * rx + ry * ry;
+                        const bool on = (act >> j) & 1;
+                        const float2 ph = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                        pr[j] += r2;
+                        pn[j] += on ? r2 / di : 0.f;
+                        pp[j] += ph.x * ph.x + ph.y * ph.y;
+                        if (lane == 0) p_s[i * J + j] = ph;
+                    }
                 }
             }
             if (lane == 0) {

@@ -15,7 +15,9 @@ namespace {
 
 thread_local std::string g_err;
 
-constexpr size_t kSmemLimit = 227 * 1024 - 2048;  // dynamic shared memory budget per CTA
+// Dynamic shared memory budget per CTA: the 227 KiB opt-in maximum less room
+// for the kernels' static shared memory (at most 6 KiB).
+constexpr size_t kSmemLimit = 227 * 1024 - 8 * 1024;
 
 template <class T>
 cudaError_t upload(T** dst, const std::vector<T>& v, cudaStream_t st) {
@@ -49,6 +51,7 @@ void kz_set_error(const char* fmt, ...) {
 
 struct kz_plan {
     int K = 0, Nt = 0, Ntp = 0, ntiles = 0, nF = 0;
+    int cmax = 0;  // largest number of rows covering one tile
     int64_t sumL = 0, total2 = 0;
     kz_prec prec = KZ_C64;
     double sum_nrm = 0.0;
@@ -104,6 +107,8 @@ struct kz_plan {
 
 struct kz_batch {
     int n = 0, nrhs = 0, J = 1, nw = 16, grid = 1, n_items = 0, Ntp_max = 0, K_max = 0;
+    int kernel = KZ_KERNEL_RESIDENT, cs = 0, cmax = 0;
+    std::vector<double> cost;  // per-instance work estimate (aligned entries + 4 Nt)
     size_t smem = 0;
     kz_algo algo = KZ_VR_OAHK;
     kz_prec prec = KZ_C64;
@@ -149,6 +154,53 @@ int choose_J(kz_algo a, int nrhs_total_items_base, int Ntp, int K, kz_prec p, in
 }
 
 int choose_nw(int Ntp) { return (Ntp / KZ_TILE) >= 16 ? 16 : 8; }
+
+// Dual kernel: staged rows per chunk (all rows of the most-covered tile when
+// they fit, else as many as fit, at least 32).  Returns 0 if nothing fits.
+int dual_cs(int J, int nw, int K, int cmax) {
+    if (!((J == 8 && (nw == 8 || nw == 16)) || (J == 16 && nw == 16))) return 0;
+    const size_t base = kz_smem_dual(J, nw, 0, K);
+    if (base + 32 * ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int)) > kSmemLimit) return 0;
+    const int fit = (int)((kSmemLimit - base) / ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int)));
+    return std::max(32, std::min(fit, std::max(cmax, 1)));
+}
+
+// Work items of a batch for J columns per CTA and nw warps: {instance, first
+// column} ordered by estimated cost, largest first; grid = resident CTAs.
+cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cudaStream_t st);
+cudaError_t batch_layout(kz_batch* B, int J, int nw, int sms, cudaStream_t st) {
+    return batch_layout_k(B, KZ_KERNEL_RESIDENT, J, nw, sms, st);
+}
+cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cudaStream_t st) {
+    std::vector<std::pair<double, int2>> work;
+    for (int b = 0; b < B->n; ++b)
+        for (int c = 0; c < B->nrhs; c += J) work.push_back({B->cost[b], make_int2(b, c)});
+    std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+    std::vector<int2> witems(work.size());
+    for (size_t w = 0; w < work.size(); ++w) witems[w] = work[w].second;
+    if (B->d_items) cudaFree(B->d_items);
+    B->d_items = nullptr;
+    cudaError_t e = upload(&B->d_items, witems, st);
+    if (e != cudaSuccess) return e;
+    B->J = J;
+    B->nw = nw;
+    B->kernel = kernel;
+    B->n_items = (int)witems.size();
+    int occ = 1;
+    if (kernel == KZ_KERNEL_DUAL) {
+        B->cs = dual_cs(J, nw, B->K_max, B->cmax);
+        B->smem = kz_smem_dual(J, nw, B->cs, B->K_max);
+        occ = std::max(1, kz_occupancy_dual(J, nw, B->smem));
+    } else {
+        B->cs = 0;
+        B->smem = smem_for(B->algo, J, B->Ntp_max, B->K_max, B->prec);
+        occ = std::max(1, occupancy_for(B->algo, J, nw, B->smem, B->prec));
+    }
+    B->grid = std::min(B->n_items, sms * occ);
+    return cudaSuccess;
+}
+
+bool dual_ok(kz_algo a, kz_prec p) { return is_ahk_family(a) && p == KZ_C64; }
 
 kz_status check_launch(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
@@ -294,6 +346,7 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     std::vector<int4> trow4;
     for (int t = 0; t < P->ntiles; ++t) {
         tnv[t] = (int)tv[t].size();
+        P->cmax = std::max(P->cmax, (int)(tv[t].size() + tf[t].size()));
         for (int pass = 0; pass < 2; ++pass)
             for (int k : (pass == 0 ? tv[t] : tf[t])) trow4.push_back(make_int4(k, rptr[k] - rows[k].x, rows[k].x, rows[k].x + rows[k].y));
         tptr[t + 1] = (int)trow4.size();
@@ -394,8 +447,26 @@ static kz_status check_solve_args(const char* fn, const kz_plan* plan, int nrhs,
 kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
                      double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
                      double* resid, int32_t* status, int32_t rhs_per_cta, int32_t refresh, void* stream) {
+    return kz_precode_ex(plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status,
+                         KZ_KERNEL_AUTO, rhs_per_cta, refresh, stream);
+}
+
+kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
+                        double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
+                        double* resid, int32_t* status, kz_kernel kernel, int32_t rhs_per_cta, int32_t refresh,
+                        void* stream) {
     g_err.clear();
-    kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter, rhs_per_cta, refresh);
+    if (kernel == KZ_KERNEL_DUAL) {
+        if (rhs_per_cta != 0 && rhs_per_cta != 8 && rhs_per_cta != 16) {
+            kz_set_error("kz_precode_ex: the dual kernel takes 0, 8 or 16 columns per CTA");
+            return KZ_ERR_INVALID_ARG;
+        }
+    } else if (kernel != KZ_KERNEL_AUTO && kernel != KZ_KERNEL_RESIDENT) {
+        kz_set_error("kz_precode_ex: unknown kernel %d", (int)kernel);
+        return KZ_ERR_INVALID_ARG;
+    }
+    kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
+                                    kernel == KZ_KERNEL_DUAL ? 0 : rhs_per_cta, refresh);
     if (rc != KZ_OK) return rc;
     if (!s || !x || !iters || !resid) {
         kz_set_error("kz_precode: s, x, iters and resid are required");
@@ -411,9 +482,26 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
         kz_set_error("kz_precode: BF16_MIXED is provided for AHK and VR_OAHK only");
         return KZ_ERR_UNSUPPORTED;
     }
-    const int J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
-    const int nw = choose_nw(plan->Ntp);
-    const size_t smem = smem_for(algo, J, plan->Ntp, plan->K, prec);
+    if (kernel == KZ_KERNEL_DUAL && !dual_ok(algo, prec)) {
+        kz_set_error("kz_precode_ex: the dual kernel runs AHK / VR_OAHK on C64 plans");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    int J, nw, cs = 0;
+    size_t smem;
+    if (kernel == KZ_KERNEL_DUAL) {
+        J = rhs_per_cta ? rhs_per_cta : (nrhs >= 16 && dual_cs(16, 16, plan->K, plan->cmax) ? 16 : 8);
+        nw = (J == 16) ? 16 : 8;
+        cs = dual_cs(J, nw, plan->K, plan->cmax);
+        if (cs == 0) {
+            kz_set_error("kz_precode_ex: K = %d does not fit the dual kernel's shared memory", plan->K);
+            return KZ_ERR_UNSUPPORTED;
+        }
+        smem = kz_smem_dual(J, nw, cs, plan->K);
+    } else {
+        J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
+        nw = choose_nw(plan->Ntp);
+        smem = smem_for(algo, J, plan->Ntp, plan->K, prec);
+    }
     if (smem > kSmemLimit) {
         kz_set_error("kz_precode: channel needs %zu bytes of shared memory per CTA (limit %zu); use fewer columns per CTA",
                      smem, kSmemLimit);
@@ -443,10 +531,17 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
     L.status = status;
     L.Ntp_max = plan->Ntp;
     L.K_max = plan->K;
-    const int occ = std::max(1, occupancy_for(algo, J, nw, smem, prec));
-    const int grid = std::min(L.n_items, plan->sms * occ);
+    L.cs = cs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = is_ahk_family(algo) ? kz_launch_ahk(L, J, nw, grid, smem, st) : kz_launch_kacz(L, J, nw, grid, smem, st);
+    cudaError_t e;
+    if (kernel == KZ_KERNEL_DUAL) {
+        const int occ = std::max(1, kz_occupancy_dual(J, nw, smem));
+        e = kz_launch_dual(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
+    } else {
+        const int occ = std::max(1, occupancy_for(algo, J, nw, smem, prec));
+        const int grid = std::min(L.n_items, plan->sms * occ);
+        e = is_ahk_family(algo) ? kz_launch_ahk(L, J, nw, grid, smem, st) : kz_launch_kacz(L, J, nw, grid, smem, st);
+    }
     return check_launch(e, "kz_precode launch");
 }
 
@@ -470,7 +565,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         kz_set_error("kz_batch_prepare: rhs_per_cta must be 0, 1, 2, 4 or 8");
         return KZ_ERR_INVALID_ARG;
     }
-    int Ntp_max = 0, K_max = 0, sms = sm_count();
+    int Ntp_max = 0, K_max = 0, cmax = 0, sms = sm_count();
     for (int b = 0; b < n; ++b) {
         const kz_batch_item& it = items[b];
         if (!it.plan || !it.s || !it.x || !it.iters || !it.resid || !(it.xi > 0.f)) {
@@ -483,6 +578,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         }
         Ntp_max = std::max(Ntp_max, it.plan->Ntp);
         K_max = std::max(K_max, it.plan->K);
+        cmax = std::max(cmax, it.plan->cmax);
     }
     kz_batch* B = new kz_batch();
     B->n = n;
@@ -491,6 +587,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
     B->prec = prec;
     B->Ntp_max = Ntp_max;
     B->K_max = K_max;
+    B->cmax = cmax;
     B->J = rhs_per_cta ? rhs_per_cta : choose_J(algo, n, Ntp_max, K_max, prec, sms, nrhs);
     B->nw = choose_nw(Ntp_max);
     B->smem = smem_for(algo, B->J, Ntp_max, K_max, prec);
@@ -500,7 +597,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         return KZ_ERR_UNSUPPORTED;
     }
     std::vector<KzInst> insts(n);
-    std::vector<std::pair<double, int2>> work;
+    B->cost.resize(n);
     for (int b = 0; b < n; ++b) {
         const kz_batch_item& it = items[b];
         KzInst I = it.plan->inst();
@@ -513,25 +610,18 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         I.iters = it.iters;
         I.resid = it.resid;
         insts[b] = I;
-        const double cost = (double)it.plan->total2 + 4.0 * it.plan->Ntp;
-        for (int c = 0; c < nrhs; c += B->J) work.push_back({cost, make_int2(b, c)});
+        B->cost[b] = (double)it.plan->total2 + 4.0 * it.plan->Ntp;
     }
-    std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-    std::vector<int2> witems(work.size());
-    for (size_t w = 0; w < work.size(); ++w) witems[w] = work[w].second;
-    B->n_items = (int)witems.size();
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(&B->d_insts, insts, st);
-    if (e == cudaSuccess) e = upload(&B->d_items, witems, st);
     if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = batch_layout(B, B->J, B->nw, sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
         delete B;
         kz_set_error("kz_batch_prepare: %s", cudaGetErrorString(e));
         return e == cudaErrorMemoryAllocation ? KZ_ERR_NOMEM : KZ_ERR_CUDA;
     }
-    const int occ = std::max(1, occupancy_for(algo, B->J, B->nw, B->smem, prec));
-    B->grid = std::min(B->n_items, sms * occ);
     *out = B;
     return KZ_OK;
 }
@@ -563,15 +653,131 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.status = status;
     L.Ntp_max = B->Ntp_max;
     L.K_max = B->K_max;
+    L.cs = B->cs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
-    e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
-                               : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
+    if (B->kernel == KZ_KERNEL_DUAL)
+        e = kz_launch_dual(L, B->J, B->nw, B->grid, B->smem, st);
+    else
+        e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
+                                   : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
     return check_launch(e, "kz_precode_batched launch");
 }
 
 void kz_batch_destroy(kz_batch* batch) { delete batch; }
+
+kz_status kz_batch_tune(kz_batch* B, kz_select sel, double tol, int32_t max_iter, uint64_t seed, int32_t* chosen,
+                        void* stream) {
+    g_err.clear();
+    if (!B) {
+        kz_set_error("kz_batch_tune: batch is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int sms = sm_count();
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        kz_set_error("kz_batch_tune: cudaEventCreate failed");
+        return KZ_ERR_CUDA;
+    }
+    float best_ms = 1e30f;
+    int best_J = B->J, best_nw = B->nw;
+    kz_status rc = KZ_OK;
+    int best_kernel = B->kernel;
+    struct Cand {
+        int kernel, J, nw;
+    };
+    std::vector<Cand> cands;
+    for (int J : {1, 2, 4, 8}) {
+        if (J > B->nrhs) continue;
+        if (smem_for(B->algo, J, B->Ntp_max, B->K_max, B->prec) > kSmemLimit) continue;
+        for (int nw : {8, 16}) cands.push_back({KZ_KERNEL_RESIDENT, J, nw});
+    }
+    if (dual_ok(B->algo, B->prec)) {
+        for (Cand c : {Cand{KZ_KERNEL_DUAL, 8, 8}, Cand{KZ_KERNEL_DUAL, 8, 16}, Cand{KZ_KERNEL_DUAL, 16, 16}})
+            if (dual_cs(c.J, c.nw, B->K_max, B->cmax) > 0) cands.push_back(c);
+    }
+    for (const Cand& cd : cands) {
+        const int J = cd.J, nw = cd.nw;
+        {
+            cudaError_t e = batch_layout_k(B, cd.kernel, J, nw, sms, st);
+            if (e != cudaSuccess) {
+                rc = check_launch(e, "kz_batch_tune layout");
+                break;
+            }
+            float ms = 0.f;
+            bool skip = false;
+            for (int rep = 0; rep < 3 && rc == KZ_OK; ++rep) {
+                if (rep == 1) cudaEventRecord(e0, st);
+                rc = kz_precode_batched(B, sel, tol, max_iter, seed, 0, nullptr, stream);
+                if (rc == KZ_ERR_CUDA) {  // a launch this device rejects: not a candidate
+                    (void)cudaGetLastError();
+                    rc = KZ_OK;
+                    skip = true;
+                    break;
+                }
+            }
+            if (rc != KZ_OK) break;
+            if (skip) continue;
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+                rc = KZ_ERR_CUDA;
+                kz_set_error("kz_batch_tune: timing failed");
+                break;
+            }
+            if (ms < best_ms) {
+                best_ms = ms;
+                best_J = J;
+                best_nw = nw;
+                best_kernel = cd.kernel;
+            }
+        }
+        if (rc != KZ_OK) break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != KZ_OK) return rc;
+    cudaError_t e = batch_layout_k(B, best_kernel, best_J, best_nw, sms, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return check_launch(e, "kz_batch_tune");
+    if (chosen) {
+        chosen[0] = best_kernel;
+        chosen[1] = best_J;
+        chosen[2] = best_nw * 32;
+    }
+    return KZ_OK;
+}
+
+kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta, int32_t threads, void* stream) {
+    g_err.clear();
+    if (!B || (threads != 256 && threads != 512)) {
+        kz_set_error("kz_batch_set_launch: need a batch and threads of 256 or 512");
+        return KZ_ERR_INVALID_ARG;
+    }
+    const int nw = threads / 32;
+    if (kernel == KZ_KERNEL_DUAL) {
+        if (!dual_ok(B->algo, B->prec) || dual_cs(rhs_per_cta, nw, B->K_max, B->cmax) == 0) {
+            kz_set_error("kz_batch_set_launch: the dual kernel needs AHK / VR_OAHK on C64 with 8 or 16 columns "
+                         "that fit shared memory");
+            return KZ_ERR_UNSUPPORTED;
+        }
+    } else if (kernel == KZ_KERNEL_RESIDENT || kernel == KZ_KERNEL_AUTO) {
+        if ((rhs_per_cta != 1 && rhs_per_cta != 2 && rhs_per_cta != 4 && rhs_per_cta != 8) ||
+            smem_for(B->algo, rhs_per_cta, B->Ntp_max, B->K_max, B->prec) > kSmemLimit) {
+            kz_set_error("kz_batch_set_launch: resident kernel needs 1, 2, 4 or 8 columns that fit shared memory");
+            return KZ_ERR_UNSUPPORTED;
+        }
+        kernel = KZ_KERNEL_RESIDENT;
+    } else {
+        kz_set_error("kz_batch_set_launch: unknown kernel %d", (int)kernel);
+        return KZ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = batch_layout_k(B, kernel, rhs_per_cta, nw, sm_count(), st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    return check_launch(e, "kz_batch_set_launch");
+}
 
 kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q, const kz_cf32* X,
                              const kz_cf32* G_Q, const kz_cf32* G_X, double tol, int32_t max_iter, kz_cf32* lambda,

@@ -98,37 +98,92 @@ __device__ __forceinline__ void row_dot(const KzInst& I, int i, const float2* __
     }
 }
 
-// FP64-accumulated variant for true residuals (complex64 H).
-template <int J>
-__device__ __forceinline__ void row_dot_d(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
-                                          double (&ar)[J], double (&ai)[J]) {
+// Two rows per warp at once: acc0[j] = h_{i0} . m_j and acc1[j] = h_{i1} . m_j
+// (i1 < 0: only i0).  Both rows' loads are in flight together, four antenna
+// pairs per row per lane, which doubles the independent loads of a warp.
+template <int J, bool BF16>
+__device__ __forceinline__ void row_dot2(const KzInst& I, int i0, int i1, const float2* __restrict__ m_s, int Ntp,
+                                         float2 (&acc0)[J], float2 (&acc1)[J]) {
     const int lane = threadIdx.x & 31;
-    const int4 rd = I.rows[i];
-    const int base = I.rptr[i];
+    const int4 r0 = I.rows[i0];
+    const int b0 = I.rptr[i0];
+    int4 r1 = make_int4(0, 0, 0, 0);
+    int b1 = 0;
+    if (i1 >= 0) {
+        r1 = I.rows[i1];
+        b1 = I.rptr[i1];
+    }
 #pragma unroll
-    for (int j = 0; j < J; ++j) ar[j] = ai[j] = 0.0;
-    for (int p = 2 * lane; p < rd.y; p += 64) {
-        const float4 h = h_pair<false>(I, base + p);
-        const int n = rd.x + p;
+    for (int j = 0; j < J; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
+    const int len = max(r0.y, r1.y);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int p = 2 * lane; p < len; p += 256) {
+        float4 h0[4], h1[4];
 #pragma unroll
-        for (int j = 0; j < J; ++j) {
-            const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n);
-            float pr = h.x * mm.x;
-            pr = fmaf(-h.y, mm.y, pr);
-            float pr2 = h.z * mm.z;
-            pr2 = fmaf(-h.w, mm.w, pr2);
-            float pi = h.x * mm.y;
-            pi = fmaf(h.y, mm.x, pi);
-            float pi2 = h.z * mm.w;
-            pi2 = fmaf(h.w, mm.z, pi2);
-            ar[j] += (double)pr + (double)pr2;
-            ai[j] += (double)pi + (double)pi2;
+        for (int u = 0; u < 4; ++u) {
+            const int q = p + 64 * u;
+            h0[u] = (q < r0.y) ? h_pair<BF16>(I, b0 + q) : z4;
+            h1[u] = (q < r1.y) ? h_pair<BF16>(I, b1 + q) : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = p + 64 * u;
+            if (q < r0.y) {
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    cmac_pair<J, BF16>(h0[u], *reinterpret_cast<const float4*>(m_s + j * Ntp + r0.x + q), acc0[j]);
+            }
+            if (q < r1.y) {
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    cmac_pair<J, BF16>(h1[u], *reinterpret_cast<const float4*>(m_s + j * Ntp + r1.x + q), acc1[j]);
+            }
         }
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        ar[j] = warp_sum_d(ar[j]);
-        ai[j] = warp_sum_d(ai[j]);
+        acc0[j].x = warp_sum(acc0[j].x);
+        acc0[j].y = warp_sum(acc0[j].y);
+        acc1[j].x = warp_sum(acc1[j].x);
+        acc1[j].y = warp_sum(acc1[j].y);
+    }
+}
+
+// True-residual variant (complex64 H): each lane sums its share of the row in
+// FP32 (the VR is split over 32 lanes, so a lane adds at most a few dozen
+// products), and the 32 lane sums are combined in FP64.  FP64 arithmetic is
+// kept out of the inner loop, where it would run at the GPU's far lower
+// double-precision rate.
+template <int J>
+__device__ __forceinline__ void row_dot_d(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
+                                          double (&ar)[J], double (&ai)[J]) {
+    float2 acc[J];
+    const int lane = threadIdx.x & 31;
+    const int4 rd = I.rows[i];
+    const int base = I.rptr[i];
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
+    int p = 2 * lane;
+    for (; p + 192 < rd.y; p += 256) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = h_pair<false>(I, base + p + 64 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int j = 0; j < J; ++j)
+                cmac_pair<J, false>(h[u], *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p + 64 * u), acc[j]);
+    }
+    for (; p < rd.y; p += 64) {
+        const float4 h = h_pair<false>(I, base + p);
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+            cmac_pair<J, false>(h, *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p), acc[j]);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        ar[j] = warp_sum_d((double)acc[j].x);
+        ai[j] = warp_sum_d((double)acc[j].y);
     }
 }
 
@@ -185,29 +240,29 @@ __device__ __forceinline__ void tile_accum(const KzInst& I, const int4* __restri
     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
     for (int j = 0; j < J; ++j) u0[j] = u1[j] = make_float2(0.f, 0.f);
-    int k = k0;
-    for (; k + 3 < k1; k += 4) {
+    const int4 none = make_int4(0, 0, 0, 0);  // empty interval: never matches
+    int4 en[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) en[u] = (k0 + u < k1) ? __ldg(trow4 + k0 + u) : none;
+    for (int k = k0; k < k1; k += 4) {
         int4 e[4];
         float4 h[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) e[u] = __ldg(trow4 + k + u);
+        for (int u = 0; u < 4; ++u) e[u] = en[u];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const bool in = (n >= e[u].z) && (n < e[u].w);
             h[u] = in ? h_pair<BF16>(I, e[u].y + n) : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+        // descriptors of the next batch, in flight while this batch is used
+#pragma unroll
+        for (int u = 0; u < 4; ++u) en[u] = (k + 4 + u < k1) ? __ldg(trow4 + k + 4 + u) : none;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            if (k + u < k1) {
 #pragma unroll
-            for (int j = 0; j < J; ++j) cmac_conj<J>(h[u], coef[e[u].x * J + j], u0[j], u1[j]);
-        }
-    }
-    for (; k < k1; ++k) {
-        const int4 e = __ldg(trow4 + k);
-        if (n >= e.z && n < e.w) {
-            const float4 h = h_pair<BF16>(I, e.y + n);
-#pragma unroll
-            for (int j = 0; j < J; ++j) cmac_conj<J>(h, coef[e.x * J + j], u0[j], u1[j]);
+                for (int j = 0; j < J; ++j) cmac_conj<J>(h[u], coef[e[u].x * J + j], u0[j], u1[j]);
+            }
         }
     }
 }

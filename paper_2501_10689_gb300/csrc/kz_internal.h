@@ -63,6 +63,7 @@ struct KzLaunch {
     unsigned long long seed;
     int* status;
     int Ntp_max, K_max;
+    int cs;               // dual kernel: staged rows per chunk
 };
 
 // Host-side launchers (kz_ahk.cu / kz_kacz.cu).
@@ -72,6 +73,9 @@ size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
 int kz_occupancy_kacz(int J, int nw, size_t smem);
+cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
+size_t kz_smem_dual(int J, int nw, int CS, int K);
+int kz_occupancy_dual(int J, int nw, size_t smem);
 
 // Auxiliary kernels (kz_aux.cu).
 cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows, const int* rptr, int K,

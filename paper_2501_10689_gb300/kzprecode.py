@@ -41,9 +41,10 @@ class KzBatchItem(ctypes.Structure):
                 ("xi", ctypes.c_float)]
 
 
-EXPORTS = ("kz_plan_create", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_batch_prepare",
-           "kz_precode_batched", "kz_batch_destroy", "kz_precode_adjoint", "kz_precode_adjoint_noalloc",
-           "kz_last_error", "kz_version")
+EXPORTS = ("kz_plan_create", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
+           "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
+           "kz_precode_adjoint", "kz_precode_adjoint_noalloc", "kz_last_error", "kz_version")
+KERNELS = {"auto": 0, "resident": 1, "dual": 2}
 
 
 def library_path() -> str:
@@ -69,12 +70,18 @@ def load():
     lib.kz_plan_query.restype = I32
     lib.kz_precode.argtypes = [P, P, I32, F32, I32, I32, F64, I32, U64, P, P, P, P, P, I32, I32, P]
     lib.kz_precode.restype = I32
+    lib.kz_precode_ex.argtypes = [P, P, I32, F32, I32, I32, F64, I32, U64, P, P, P, P, P, I32, I32, I32, P]
+    lib.kz_precode_ex.restype = I32
+    lib.kz_batch_set_launch.argtypes = [P, I32, I32, I32, P]
+    lib.kz_batch_set_launch.restype = I32
     lib.kz_batch_prepare.argtypes = [ctypes.POINTER(P), P, I32, I32, I32, I32, I32, P]
     lib.kz_batch_prepare.restype = I32
     lib.kz_precode_batched.argtypes = [P, I32, F64, I32, U64, I32, P, P]
     lib.kz_precode_batched.restype = I32
     lib.kz_batch_destroy.argtypes = [P]
     lib.kz_batch_destroy.restype = None
+    lib.kz_batch_tune.argtypes = [P, I32, F64, I32, U64, P, P]
+    lib.kz_batch_tune.restype = I32
     lib.kz_precode_adjoint.argtypes = [P, I32, F32, P, P, P, P, F64, I32, P, P, P, P, P, P, P, P]
     lib.kz_precode_adjoint.restype = I32
     lib.kz_precode_adjoint_noalloc.argtypes = [P, I32, F32, P, P, P, P, F64, I32, P, P, P, P, P, P, P, P]
@@ -169,6 +176,23 @@ def kz_precode(plan: Plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, it
                                  int(rhs_per_cta), int(refresh), _stream(stream)))
 
 
+def kz_precode_ex(plan: Plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status=None,
+                  kernel="auto", rhs_per_cta=0, refresh=0, stream=None):
+    lib = load()
+    _check_c64(s, (nrhs, plan.K), "s")
+    _check_c64(x, (nrhs, plan.Nt), "x")
+    if v is not None:
+        _check_c64(v, (nrhs, plan.K), "v")
+    if iters.dtype != torch.int32 or resid.dtype != torch.float64:
+        raise ValueError("iters must be int32 and resid float64")
+    return _check(lib.kz_precode_ex(plan.handle, _ptr(s), nrhs, float(xi),
+                                    ALGOS[algo] if isinstance(algo, str) else algo,
+                                    SELECT[sel] if isinstance(sel, str) else sel, float(tol), int(max_iter),
+                                    int(seed), _ptr(x), _ptr(v), _ptr(iters), _ptr(resid), _ptr(status),
+                                    KERNELS[kernel] if isinstance(kernel, str) else kernel, int(rhs_per_cta),
+                                    int(refresh), _stream(stream)))
+
+
 class Batch:
     def __init__(self, handle, keep):
         self.handle = handle
@@ -206,6 +230,23 @@ def kz_precode_batched(batch: Batch, sel, tol, max_iter, seed, refresh=0, status
                                          int(max_iter), int(seed), int(refresh), _ptr(status), _stream(stream)))
 
 
+def kz_batch_tune(batch: Batch, sel, tol, max_iter, seed, stream=None):
+    """Time the feasible launches on the batch; keep the fastest.
+    Returns (kernel name, columns per CTA, threads)."""
+    lib = load()
+    chosen = np.zeros(3, dtype=np.int32)
+    _check(lib.kz_batch_tune(batch.handle, SELECT[sel] if isinstance(sel, str) else sel, float(tol), int(max_iter),
+                             int(seed), chosen.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
+    names = {v: k for k, v in KERNELS.items()}
+    return names[int(chosen[0])], int(chosen[1]), int(chosen[2])
+
+
+def kz_batch_set_launch(batch: Batch, kernel, rhs_per_cta, threads, stream=None):
+    lib = load()
+    return _check(lib.kz_batch_set_launch(batch.handle, KERNELS[kernel] if isinstance(kernel, str) else kernel,
+                                          int(rhs_per_cta), int(threads), _stream(stream)))
+
+
 def kz_precode_adjoint(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam, y, grad_H_packed, grad_xi, iters,
                        resid, status=None, stream=None):
     lib = load()
@@ -238,7 +279,7 @@ def exported_symbols():
 
 # ----------------------------------------------------------------- convenience
 def precode(plan: Plan, S, xi, algo="vr_oahk", sel="paper", tol=1e-6, max_iter=1000, seed=0, rhs_per_cta=0,
-            refresh=0, want_v=True, sync=True):
+            refresh=0, want_v=True, sync=True, kernel="auto"):
     """Allocate outputs, run ``kz_precode`` and (by default) wait for it.
 
     ``S`` is a torch CUDA complex64 tensor of shape (nrhs, K).  Returns a dict
@@ -251,7 +292,8 @@ def precode(plan: Plan, S, xi, algo="vr_oahk", sel="paper", tol=1e-6, max_iter=1
     iters = torch.empty(nrhs, dtype=torch.int32, device=dev)
     resid = torch.empty(nrhs, dtype=torch.float64, device=dev)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
-    kz_precode(plan, S, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status, rhs_per_cta, refresh)
+    kz_precode_ex(plan, S, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status, kernel, rhs_per_cta,
+                  refresh)
     out = {"x": x, "v": v, "iters": iters, "resid": resid, "status": status}
     if sync:
         torch.cuda.synchronize(dev)
