@@ -49,9 +49,14 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--instances", type=int, default=N_INST)
     ap.add_argument("--verify", type=int, default=48, help="instances checked against the oracle")
-    ap.add_argument("--rhs-per-cta", type=int, default=0)
+    ap.add_argument("--rhs-per-cta", type=int, default=0, help="fix the launch instead of autotuning")
+    ap.add_argument("--kernel", default="resident", choices=["resident", "dual"],
+                    help="kernel used with --rhs-per-cta")
+    ap.add_argument("--threads", type=int, default=512, help="threads per CTA used with --rhs-per-cta")
     ap.add_argument("--no-grk", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--configs", action="store_true",
+                    help="measure the other workloads (configs 1, 2, 4, 5) instead of the benchmark line")
     return ap.parse_args()
 
 
@@ -197,6 +202,8 @@ def run_ours(args):
     if args.rhs_per_cta == 0:
         with torch.cuda.stream(stream):
             tuned = kp.kz_batch_tune(batch, "paper", TOL, MAX_ITER, 0)
+    else:
+        kp.kz_batch_set_launch(batch, args.kernel, args.rhs_per_cta, args.threads)
 
     def launch():
         kp.kz_precode_batched(batch, "paper", TOL, MAX_ITER, 0, status=status)
@@ -335,7 +342,8 @@ def run_ours(args):
                            "tol": TOL, "max_iter": MAX_ITER,
                            "launch": ({"kernel": tuned[0], "rhs_per_cta": tuned[1], "threads": tuned[2],
                                        "chosen_by": "kz_batch_tune"}
-                                      if tuned else {"rhs_per_cta": args.rhs_per_cta}),
+                                      if tuned else {"kernel": args.kernel, "rhs_per_cta": args.rhs_per_cta,
+                                                     "threads": args.threads, "chosen_by": "command line"}),
                            "l2": "inputs larger than L2 (packed H of the batch is %.0f MB)" % (float(sumL.sum()) * 8 / 1e6),
                            "graph": "CUDA graph replay of queue reset + persistent kernel"},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
@@ -350,8 +358,128 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# ----------------------------------------------------------------------------- other workloads
+def _time_ms(fn, reps=5):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        ts.append(a.elapsed_time(b))
+    return float(np.median(ts))
+
+
+def run_configs(args):
+    """One JSON line per (workload, method): time per solve, throughput and the
+    error against the FP64 oracle.  Not the benchmark line."""
+    import torch
+
+    import __graft_entry__
+    import kzgen
+    import oracle
+    from paper_2501_10689_gb300 import kzprecode as kp
+    __graft_entry__.build()
+    dev = torch.device("cuda", 0)
+
+    def emit(d):
+        print(json.dumps(d), flush=True)
+
+    def solve(plan, S, xi, algo, tol, max_iter, kernel="auto", sel="paper"):
+        return kp.precode(plan, S, xi, algo=algo, sel=sel, tol=tol, max_iter=max_iter, kernel=kernel, sync=False)
+
+    # config 1: single column, latency
+    inst = kzgen.config1()
+    V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
+    plan = kp.plan_from_instance(inst, device=dev)
+    S = kp.rhs_tensor(inst.S, device=dev)
+    for algo in ("grk", "vr_ogrk", "ahk", "vr_oahk"):
+        out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=4000)
+        err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])
+        ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, 4000))
+        emit({"workload": "config1 Nt=256 K=16 1 column SNR 10 dB", "algo": algo, "tol": 1e-6,
+              "us_per_solve": 1000 * ms, "iters": int(out["iters"][0].item()), "rel_err": err})
+
+    # config 2: 256 columns sharing one channel, every method, three SNRs
+    for snr in (0.0, 10.0, 20.0):
+        inst = kzgen.config2(snr)
+        V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
+        plan = kp.plan_from_instance(inst, device=dev)
+        S = kp.rhs_tensor(inst.S, device=dev)
+        for algo, kernel in (("rk_energy", "auto"), ("grk", "auto"), ("vr_ogrk", "auto"), ("ahk", "auto"),
+                             ("vr_oahk", "resident"), ("vr_oahk", "dual")):
+            max_iter = 400000 if algo.startswith("rk") else (40000 if "grk" in algo else 4000)
+            for tol in (1e-5, 3e-6, 1e-6):
+                out = kp.precode(plan, S, inst.xi, algo=algo, tol=tol, max_iter=max_iter, kernel=kernel)
+                err = float(np.max(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)))
+                if err <= ERR_BAR:
+                    break
+            ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, tol, max_iter, kernel), reps=3)
+            emit({"workload": f"config2 Nt=1024 K=64 256 columns SNR {snr:g} dB", "algo": algo, "kernel": kernel,
+                  "tol": tol, "ms_per_solve": ms, "precoders_per_s": 256 / (ms / 1000.0),
+                  "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err": err})
+
+    # config 4: large array, BF16-mixed vs complex64
+    inst = kzgen.config4()
+    V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
+    S = kp.rhs_tensor(inst.S, device=dev)
+    for prec in ("bf16", "c64"):
+        plan = kp.plan_from_instance(inst, prec=prec, device=dev)
+        out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000)
+        err = float(np.max(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)))
+        ms = _time_ms(lambda: solve(plan, S, inst.xi, "vr_oahk", 1e-6, 3000), reps=3)
+        emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
+              "tol": 1e-6, "ms_per_solve": ms, "precoders_per_s": 64 / (ms / 1000.0),
+              "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err_vs_fp64": err})
+
+    # config 5: forward + adjoint of the sum-rate loss over 64 channels
+    from oracle import adjoint as oadj
+    from paper_2501_10689_gb300 import autograd as kad
+    chans = [kzgen.config5_instance(i) for i in range(64)]
+    snr_lin = 10.0
+    Hps = [torch.tensor(c.H_packed, device=dev) for c in chans]
+    Ss = [kp.rhs_tensor(c.S, device=dev) for c in chans]
+
+    def grad_all():
+        total = 0.0
+        for c, Hp0, S0 in zip(chans, Hps, Ss):
+            Hp = Hp0.clone().requires_grad_(True)
+            xi = torch.tensor(c.xi, dtype=torch.float32, device=dev, requires_grad=True)
+            X5, V5 = kad.precode(Hp, xi, S0, c.vr_offset, c.vr_len, c.Nt, tol=1e-6)
+            L = kad.sum_rate_loss(kad.dense_from_packed(Hp, c.vr_offset, c.vr_len, c.Nt), X5, snr_lin)
+            L.backward()
+            total += float(L.item())
+        return total
+
+    grad_all()
+    t0 = time.perf_counter()
+    grad_all()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    c = chans[0]
+    L_ref, gH_ref, gxi_ref = oadj.reference_gradient(c, snr_lin)
+    Hp = Hps[0].clone().requires_grad_(True)
+    xi = torch.tensor(c.xi, dtype=torch.float32, device=dev, requires_grad=True)
+    X5, V5 = kad.precode(Hp, xi, Ss[0], c.vr_offset, c.vr_len, c.Nt, tol=1e-6)
+    kad.sum_rate_loss(kad.dense_from_packed(Hp, c.vr_offset, c.vr_len, c.Nt), X5, snr_lin).backward()
+    gH = Hp.grad.cpu().numpy().astype(np.complex128)
+    emit({"workload": "config5 64 channels Nt=2048 K=128 VR 256-1024 identity symbols, forward + adjoint",
+          "grad_evals_per_s": 64 / dt, "seconds_per_batch": dt,
+          "grad_H_rel_err_vs_fp64_autograd": float(np.linalg.norm(gH - gH_ref) / np.linalg.norm(gH_ref)),
+          "grad_xi_rel_err": float(abs(xi.grad.item() - gxi_ref) / abs(gxi_ref)),
+          "note": "per-channel autograd calls (plan set-up, forward solve, adjoint solve, loss in torch) timed "
+                  "end to end on the host clock"})
+
+
 def main():
     args = parse()
+    if args.configs:
+        run_configs(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -43,11 +43,27 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NT = NW * 32;
-    float2* m_s = reinterpret_cast<float2*>(kz_smem);
-    float2* b_s = m_s + (size_t)J * L.Ntp_max;
-    float2* q_s = b_s + (size_t)L.K_max * J;
-    float2* p_s = q_s + (size_t)L.K_max * J;
-    float* d_s = reinterpret_cast<float*>(p_s + (size_t)L.K_max * J);
+    // shared-memory carve-up: every array starts at a 16-byte aligned offset
+    // (the int4 descriptors and the float4 iterate loads need it)
+    size_t off = 0;
+    auto carve = [&](size_t bytes) {
+        unsigned char* p = kz_smem + off;
+        off += (bytes + 15) & ~(size_t)15;
+        return p;
+    };
+    float2* m_s = reinterpret_cast<float2*>(carve((size_t)J * L.Ntp_max * sizeof(float2)));
+    float2* b_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
+    float2* q_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
+    float2* p_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
+    float* d_s = reinterpret_cast<float*>(carve((size_t)L.K_max * sizeof(float)));
+    // per-channel descriptors staged once per item (no dependent global loads
+    // in front of every row): row intervals, offsets, solve order, 1 / d
+    int4* rows_s = reinterpret_cast<int4*>(carve((size_t)L.K_max * sizeof(int4)));
+    int* rptr_s = reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int)));
+    int* order_s = reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int)));
+    float* dinv_s = reinterpret_cast<float*>(carve((size_t)L.K_max * sizeof(float)));
+    int* tptr_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE + 1) * sizeof(int)));
+    int* tnv_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE) * sizeof(int)));
     const float tol2 = (float)(L.tol * L.tol);
     const bool oahk = (L.algo == ALGO_OAHK);
 
@@ -81,7 +97,18 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             q_s[e] = make_float2(0.f, 0.f);
             p_s[e] = make_float2(0.f, 0.f);
         }
-        for (int i = tid; i < K; i += NT) d_s[i] = I.nrm[i] + xi;
+        for (int i = tid; i < K; i += NT) {
+            const float d = I.nrm[i] + xi;
+            d_s[i] = d;
+            dinv_s[i] = 1.f / d;
+            rows_s[i] = I.rows[i];
+            rptr_s[i] = I.rptr[i];
+            order_s[i] = I.order[i];
+        }
+        for (int t2 = tid; t2 <= I.ntiles; t2 += NT) {
+            tptr_s[t2] = I.tptr[t2];
+            if (t2 < I.ntiles) tnv_s[t2] = I.tnv[t2];
+        }
         __syncthreads();
         if (warp < J) {
             double a = 0.0;
@@ -112,9 +139,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             if (oahk) {
                 ++t;
                 for (int f = warp; f < nF; f += NW) {
-                    const int i = I.order[f];
+                    const int i = order_s[f];
                     float2 acc[J];
-                    row_dot<J, BF16>(I, i, m_s, Ntp, acc);
+                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, Ntp, acc);
                     float2 g[J];
                     const float di = d_s[i];
 #pragma unroll
@@ -125,7 +152,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const bool on = (act >> j) & 1;
                         g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
                     }
-                    row_axpy<J, BF16>(I, i, m_s, Ntp, g, lane, 32);
+                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, Ntp, g, lane, 32);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -143,15 +170,15 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             for (int j = 0; j < J; ++j) pr[j] = pn[j] = pp[j] = 0.f;
             // rows v and v + NW go to the same warp together (two loads streams)
             for (int v = warp; v < vcount; v += 2 * NW) {
-                const int i0 = I.order[v0 + v];
-                const int i1 = (v + NW < vcount) ? I.order[v0 + v + NW] : -1;
+                const int i0 = order_s[v0 + v];
+                const int i1 = (v + NW < vcount) ? order_s[v0 + v + NW] : -1;
                 float2 acc0[J], acc1[J];
-                row_dot2<J, BF16>(I, i0, i1, m_s, Ntp, acc0, acc1);
+                row_dot2<J, BF16>(I, rows_s, rptr_s, i0, i1, m_s, Ntp, acc0, acc1);
 #pragma unroll
                 for (int rr = 0; rr < 2; ++rr) {
                     const int i = rr ? i1 : i0;
                     if (i < 0) continue;
-                    const float di = d_s[i];
+                    const float di = dinv_s[i];
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float2 a = rr ? acc1[j] : acc0[j];
@@ -160,9 +187,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const float ry = bv.y - a.y - xi * qv.y;
                         const float r2 = rx * rx + ry * ry;
                         const bool on = (act >> j) & 1;
-                        const float2 ph = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                        const float2 ph = on ? make_float2(rx * di, ry * di) : make_float2(0.f, 0.f);
                         pr[j] += r2;
-                        pn[j] += on ? r2 / di : 0.f;
+                        pn[j] += on ? r2 * di : 0.f;
                         pp[j] += ph.x * ph.x + ph.y * ph.y;
                         if (lane == 0) p_s[i * J + j] = ph;
                     }
@@ -213,7 +240,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 since_refresh = 0;
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     float2 u0[J], u1[J];
-                    tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+                    tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
@@ -227,7 +254,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 for (int j = 0; j < J; ++j) rp[j] = 0.0;
                 for (int i = warp; i < K; i += NW) {
                     double ar[J], ai[J];
-                    row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+                    row_dot_d<J>(I, rows_s, rptr_s, i, m_s, Ntp, ar, ai);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -279,8 +306,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 #pragma unroll
                 for (int j = 0; j < J; ++j) uu[j] = 0.f;
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
-                    const int k0 = I.tptr[tile];
-                    const int k1 = oahk ? k0 + I.tnv[tile] : I.tptr[tile + 1];
+                    const int k0 = tptr_s[tile];
+                    const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                     if (k0 == k1) continue;
                     float2 u0[J], u1[J];
                     tile_accum<J, BF16>(I, trow4, tile, k0, k1, p_s, u0, u1);
@@ -313,8 +340,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 __syncthreads();
                 // ---------------- m += gamma u ; q_V += gamma phi_V
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
-                    const int k0 = I.tptr[tile];
-                    const int k1 = oahk ? k0 + I.tnv[tile] : I.tptr[tile + 1];
+                    const int k0 = tptr_s[tile];
+                    const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                     if (k0 == k1) continue;
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
@@ -337,7 +364,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     }
                 }
                 for (int e = tid; e < vcount * J; e += NT) {
-                    const int i = I.order[v0 + e / J], j = e % J;
+                    const int i = order_s[v0 + e / J], j = e % J;
                     const float g = s_gamma[j];
                     const float2 ph = p_s[i * J + j];
                     q_s[i * J + j].x = fmaf(g, ph.x, q_s[i * J + j].x);
@@ -352,7 +379,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 since_refresh = 0;
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     float2 u0[J], u1[J];
-                    tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+                    tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
@@ -376,7 +403,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         // ---- finalise: x = m = H^H q (complex64), true residual with FP64 accumulation
         for (int tile = warp; tile < I.ntiles; tile += NW) {
             float2 u0[J], u1[J];
-            tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
+            tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
             const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
@@ -391,7 +418,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             for (int j = 0; j < J; ++j) rp[j] = 0.0;
             for (int i = warp; i < K; i += NW) {
                 double ar[J], ai[J];
-                row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+                row_dot_d<J>(I, rows_s, rptr_s, i, m_s, Ntp, ar, ai);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -471,7 +498,10 @@ int occ_j(int J, size_t smem) {
 
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
     (void)prec;
-    return (size_t)J * Ntp * sizeof(float2) + 3 * (size_t)K * J * sizeof(float2) + (size_t)K * sizeof(float) + 16;
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    return r16((size_t)J * Ntp * sizeof(float2)) + 3 * r16((size_t)K * J * sizeof(float2)) +
+           r16((size_t)K * sizeof(float)) + r16((size_t)K * sizeof(int4)) + 3 * r16((size_t)K * sizeof(int)) +
+           r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int));
 }
 
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {

@@ -101,6 +101,7 @@ struct kz_plan {
         I.Hc = d_Hc;
         I.Hb = d_Hb;
         I.sum_nrm = sum_nrm;
+        I.cmax = cmax;
         return I;
     }
 };
@@ -160,8 +161,9 @@ int choose_nw(int Ntp) { return (Ntp / KZ_TILE) >= 16 ? 16 : 8; }
 int dual_cs(int J, int nw, int K, int cmax) {
     if (!((J == 8 && (nw == 8 || nw == 16)) || (J == 16 && nw == 16))) return 0;
     const size_t base = kz_smem_dual(J, nw, 0, K);
-    if (base + 32 * ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int)) > kSmemLimit) return 0;
-    const int fit = (int)((kSmemLimit - base) / ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int)));
+    const size_t per_row = 2 * ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int));  // two staging buffers
+    if (base + 32 * per_row > kSmemLimit) return 0;
+    const int fit = (int)((kSmemLimit - base) / per_row);
     return std::max(32, std::min(fit, std::max(cmax, 1)));
 }
 

@@ -60,11 +60,11 @@ __device__ __forceinline__ void cmac_pair(const float4& h, const float4& mm, flo
 }
 
 template <int J, bool BF16>
-__device__ __forceinline__ void row_dot(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
-                                        float2 (&acc)[J]) {
+__device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                        const float2* __restrict__ m_s, int Ntp, float2 (&acc)[J]) {
     const int lane = threadIdx.x & 31;
-    const int4 rd = I.rows[i];
-    const int base = I.rptr[i];
+    const int4 rd = rows[i];
+    const int base = rptr[i];
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
     int p = 2 * lane;
@@ -102,16 +102,17 @@ __device__ __forceinline__ void row_dot(const KzInst& I, int i, const float2* __
 // (i1 < 0: only i0).  Both rows' loads are in flight together, four antenna
 // pairs per row per lane, which doubles the independent loads of a warp.
 template <int J, bool BF16>
-__device__ __forceinline__ void row_dot2(const KzInst& I, int i0, int i1, const float2* __restrict__ m_s, int Ntp,
-                                         float2 (&acc0)[J], float2 (&acc1)[J]) {
+__device__ __forceinline__ void row_dot2(const KzInst& I, const int4* rows, const int* rptr, int i0, int i1,
+                                         const float2* __restrict__ m_s, int Ntp, float2 (&acc0)[J],
+                                         float2 (&acc1)[J]) {
     const int lane = threadIdx.x & 31;
-    const int4 r0 = I.rows[i0];
-    const int b0 = I.rptr[i0];
+    const int4 r0 = rows[i0];
+    const int b0 = rptr[i0];
     int4 r1 = make_int4(0, 0, 0, 0);
     int b1 = 0;
     if (i1 >= 0) {
-        r1 = I.rows[i1];
-        b1 = I.rptr[i1];
+        r1 = rows[i1];
+        b1 = rptr[i1];
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) acc0[j] = acc1[j] = make_float2(0.f, 0.f);
@@ -155,12 +156,12 @@ __device__ __forceinline__ void row_dot2(const KzInst& I, int i0, int i1, const 
 // kept out of the inner loop, where it would run at the GPU's far lower
 // double-precision rate.
 template <int J>
-__device__ __forceinline__ void row_dot_d(const KzInst& I, int i, const float2* __restrict__ m_s, int Ntp,
-                                          double (&ar)[J], double (&ai)[J]) {
+__device__ __forceinline__ void row_dot_d(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                          const float2* __restrict__ m_s, int Ntp, double (&ar)[J], double (&ai)[J]) {
     float2 acc[J];
     const int lane = threadIdx.x & 31;
-    const int4 rd = I.rows[i];
-    const int base = I.rptr[i];
+    const int4 rd = rows[i];
+    const int base = rptr[i];
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
     int p = 2 * lane;
@@ -191,10 +192,11 @@ __device__ __forceinline__ void row_dot_d(const KzInst& I, int i, const float2* 
 // Restricting to the true VR keeps rows of the orthogonal set, whose aligned
 // intervals may share an edge pair, from writing the same element.
 template <int J, bool BF16>
-__device__ __forceinline__ void row_axpy(const KzInst& I, int i, float2* __restrict__ m_s, int Ntp,
-                                         const float2 (&g)[J], int lane, int nlanes) {
-    const int4 rd = I.rows[i];
-    const int base = I.rptr[i];
+__device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                         float2* __restrict__ m_s, int Ntp, const float2 (&g)[J], int lane,
+                                         int nlanes) {
+    const int4 rd = rows[i];
+    const int base = rptr[i];
     for (int p = 2 * lane; p < rd.y; p += 2 * nlanes) {
         const float4 h = h_pair<BF16>(I, base + p);
         const int n = rd.x + p;

@@ -26,7 +26,8 @@
 namespace {
 
 constexpr int HSTR = KZ_TILE + 1;  // staged row stride (complex): odd, so row-wise reads spread over banks
-constexpr int JT = 4;              // columns per thread in the tile products
+constexpr int JT = 4;              // columns per thread in the u product
+constexpr int JZ = 2;              // columns per thread in the z product (more tasks: every warp busy)
 
 enum PassKind { PASS_F = 0, PASS_V = 1, PASS_ALL = 2 };
 
@@ -50,14 +51,46 @@ struct DualSmem {
     float2* hs;     // [CS][HSTR] staged rows of one tile (chunk)
     int* hrow;      // [CS] row index of each staged slot, -1 if empty
     int* huse;      // [CS] 1 if the slot's row contributes to u in this pass
-    float2* up;     // [RG][KZ_TILE][J] partial u per row group
-    float2* us;     // [KZ_TILE][J] u of the tile
+    float2* up;     // [RG][J][KZ_TILE] partial u per row group (antenna fastest: conflict-free stores)
+    float2* us;     // [J][KZ_TILE] u of the tile
     float2* r_s;    // [K][J]
     float2* q_s;    // [K][J]
     float2* p_s;    // [K][J] phi
     float2* z_s;    // [K][J] H u accumulators of the pass
     float* d_s;     // [K]
 };
+
+// 8-byte asynchronous global -> shared copy; `valid == false` writes zeros
+// (source size 0) without reading the source.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool valid) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    const int nbytes = valid ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(nbytes) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Asynchronous version of stage_rows: the copies complete at the next
+// cp_async_wait; hrow / huse are plain stores (visible after the barrier).
+template <int NW>
+__device__ __forceinline__ void stage_rows_async(const KzInst& I, const int4* __restrict__ trow4, int tile, int k0,
+                                                 int n, int ku0, int ku1, float2* hs, int* hrow, int* huse) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nb = tile * KZ_TILE + 2 * lane;
+    for (int sl = warp; sl < n; sl += NW) {
+        const int4 e = __ldg(trow4 + k0 + sl);
+        const bool in = (nb >= e.z && nb < e.w);
+        const float2* src = in ? (I.Hc + e.y + nb) : I.Hc;
+        float2* dst = hs + sl * HSTR + 2 * lane;
+        cp_async8(dst, src, in);
+        cp_async8(dst + 1, src + 1, in);
+        if (lane == 0) {
+            hrow[sl] = e.x;
+            huse[sl] = (k0 + sl >= ku0 && k0 + sl < ku1) ? 1 : 0;
+        }
+    }
+}
 
 // Stage the covering-row entries [k0, k0 + n) of `tile` into slots 0..n-1.
 template <int NW>
@@ -79,13 +112,182 @@ __device__ __forceinline__ void stage_rows(const KzInst& I, const int4* __restri
     }
 }
 
+// z[row] += H_tile[row, :] u_tile for the n staged rows: one thread per
+// (staged row, JZ columns), rows over lanes (padded stride: conflict-free),
+// u_tile read as broadcasts.
+template <int J, int NW>
+__device__ __forceinline__ void z_tile(const DualSmem<J, NW>& S, const float2* hs, const int* hrow, int n) {
+    constexpr int CZ = J / JZ;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ntask = ((n + 31) / 32) * CZ;
+    for (int task = warp; task < ntask; task += NW) {
+        const int sl = (task / CZ) * 32 + lane;
+        const int g = task % CZ;
+        if (sl < n) {
+            float2 acc[JZ];
+#pragma unroll
+            for (int t = 0; t < JZ; ++t) acc[t] = make_float2(0.f, 0.f);
+            const float2* hp = hs + sl * HSTR;
+#pragma unroll 8
+            for (int nn = 0; nn < KZ_TILE; ++nn) {
+                const float2 h = hp[nn];
+                const float2* up = S.us + (g * JZ) * KZ_TILE + nn;
+#pragma unroll
+                for (int t = 0; t < JZ; ++t) {
+                    const float2 u = up[t * KZ_TILE];
+                    acc[t].x = fmaf(h.x, u.x, fmaf(-h.y, u.y, acc[t].x));
+                    acc[t].y = fmaf(h.x, u.y, fmaf(h.y, u.x, acc[t].y));
+                }
+            }
+            float2* zp = S.z_s + hrow[sl] * J + g * JZ;
+#pragma unroll
+            for (int t = 0; t < JZ; ++t) {
+                zp[t].x += acc[t].x;
+                zp[t].y += acc[t].y;
+            }
+        }
+    }
+}
+
 // One pass: z = H (H^H coef) restricted as `kind` says, ||u||^2 per column.
 // kind PASS_V: u from V rows (list head), PASS_F: from F rows (list tail),
 // PASS_ALL: from every row.  If xout != nullptr, u is also written to
 // x (columns col0.., leading dimension Nt).  z_s must be zero on entry.
+// u-phase contribution of n staged rows (rows of this warp's row group that
+// are flagged for u), per thread 2 antennas x JT columns.
+template <int J, int NW>
+__device__ __forceinline__ void u_rows(const float2* hs, const int* hrow, const int* huse, int n, const float2* coef,
+                                       float2 (&a0)[JT], float2 (&a1)[JT]) {
+    constexpr int CG = J / JT, RG = NW / CG;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cg = warp % CG, rg = warp / CG;
+    for (int sl = rg; sl < n; sl += RG) {
+        if (!huse[sl]) continue;
+        const float2* hp = hs + sl * HSTR + 2 * lane;
+        const float2 h0 = hp[0], h1 = hp[1];
+        const float2* cp = coef + hrow[sl] * J + cg * JT;
+#pragma unroll
+        for (int t = 0; t < JT; ++t) {
+            const float2 cv = cp[t];
+            a0[t].x = fmaf(h0.x, cv.x, fmaf(h0.y, cv.y, a0[t].x));
+            a0[t].y = fmaf(h0.x, cv.y, fmaf(-h0.y, cv.x, a0[t].y));
+            a1[t].x = fmaf(h1.x, cv.x, fmaf(h1.y, cv.y, a1[t].x));
+            a1[t].y = fmaf(h1.x, cv.y, fmaf(-h1.y, cv.x, a1[t].y));
+        }
+    }
+}
+
+// Combine the row groups' partial u of one tile into us, add ||u||^2 of
+// column tid / 32 to uacc and optionally write u to x.  Ends with us ready.
+template <int J, int NW>
+__device__ __forceinline__ void finish_u(const DualSmem<J, NW>& S, int tile, int Nt, const float2 (&a0)[JT],
+                                         const float2 (&a1)[JT], float& uacc, float2* xout, int col0, int ncols) {
+    constexpr int CG = J / JT, RG = NW / CG;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int cg = warp % CG, rg = warp / CG;
+    float2* upp = S.up + (size_t)rg * KZ_TILE * J;
+#pragma unroll
+    for (int t = 0; t < JT; ++t) {
+        upp[(cg * JT + t) * KZ_TILE + 2 * lane] = a0[t];
+        upp[(cg * JT + t) * KZ_TILE + 2 * lane + 1] = a1[t];
+    }
+    __syncthreads();
+    for (int e = tid; e < KZ_TILE * J; e += NW * 32) {
+        float2 u = make_float2(0.f, 0.f);
+        for (int g = 0; g < RG; ++g) {
+            const float2 v = S.up[(size_t)g * KZ_TILE * J + e];
+            u.x += v.x;
+            u.y += v.y;
+        }
+        S.us[e] = u;
+    }
+    __syncthreads();
+    if (tid < 32 * J) {
+        const int j = tid / 32, l = tid % 32;
+        const float2 u0 = S.us[j * KZ_TILE + 2 * l], u1 = S.us[j * KZ_TILE + 2 * l + 1];
+        uacc += u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y;
+        if (xout && j < ncols) {
+            const int nn = tile * KZ_TILE + 2 * l;
+            float2* xc = xout + (size_t)(col0 + j) * Nt;
+            if (nn < Nt) xc[nn] = u0;
+            if (nn + 1 < Nt) xc[nn + 1] = u1;
+        }
+    }
+}
+
+// Pass with the next tile's rows copied (cp.async) into the other staging
+// buffer while the current tile computes; every tile's rows fit one buffer.
+template <int J, int NW>
+__device__ float dual_pass_pipe(const KzInst& I, const DualSmem<J, NW>& S, int CS, int kind, const float2* coef,
+                                float2* xout, int col0, int ncols) {
+    const int tid = threadIdx.x;
+    const int4* trow4 = I.trow4;
+    const int Nt = I.Nt;
+    float uacc = 0.f;
+    auto has_u = [&](int tile, int& k0, int& k1, int& ku0, int& ku1) {
+        k0 = I.tptr[tile];
+        k1 = I.tptr[tile + 1];
+        const int nv = I.tnv[tile];
+        ku0 = k0;
+        ku1 = k1;
+        if (kind == PASS_V) ku1 = k0 + nv;
+        if (kind == PASS_F) ku0 = k0 + nv;
+        return ku0 < ku1;
+    };
+    auto next_tile = [&](int t) {
+        for (int tt = t + 1; tt < I.ntiles; ++tt) {
+            int k0, k1, ku0, ku1;
+            if (has_u(tt, k0, k1, ku0, ku1)) return tt;
+            if (xout && tid < 32 * J && tid / 32 < ncols) {  // u = 0 on an uncovered tile
+                const int nn = tt * KZ_TILE + 2 * (tid % 32);
+                float2* xc = xout + (size_t)(col0 + tid / 32) * Nt;
+                if (nn < Nt) xc[nn] = make_float2(0.f, 0.f);
+                if (nn + 1 < Nt) xc[nn + 1] = make_float2(0.f, 0.f);
+            }
+        }
+        return -1;
+    };
+    int t = next_tile(-1), b = 0;
+    if (t >= 0) {
+        int k0, k1, ku0, ku1;
+        has_u(t, k0, k1, ku0, ku1);
+        stage_rows_async<NW>(I, trow4, t, k0, k1 - k0, ku0, ku1, S.hs, S.hrow, S.huse);
+    }
+    cp_async_commit();
+    while (t >= 0) {
+        const int tn = next_tile(t);
+        if (tn >= 0) {
+            int k0, k1, ku0, ku1;
+            has_u(tn, k0, k1, ku0, ku1);
+            stage_rows_async<NW>(I, trow4, tn, k0, k1 - k0, ku0, ku1, S.hs + (b ^ 1) * CS * HSTR,
+                                 S.hrow + (b ^ 1) * CS, S.huse + (b ^ 1) * CS);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // this tile's copies are done (the prefetch may still fly)
+        __syncthreads();
+        const int n = I.tptr[t + 1] - I.tptr[t];
+        const float2* hs = S.hs + b * CS * HSTR;
+        const int* hrow = S.hrow + b * CS;
+        const int* huse = S.huse + b * CS;
+        float2 a0[JT], a1[JT];
+#pragma unroll
+        for (int q = 0; q < JT; ++q) a0[q] = a1[q] = make_float2(0.f, 0.f);
+        u_rows<J, NW>(hs, hrow, huse, n, coef, a0, a1);
+        finish_u<J, NW>(S, t, Nt, a0, a1, uacc, xout, col0, ncols);
+        z_tile<J, NW>(S, hs, hrow, n);
+        __syncthreads();  // buffers of this tile free before they are refilled
+        t = tn;
+        b ^= 1;
+    }
+    cp_async_wait<0>();
+    __syncthreads();
+    return uacc;
+}
+
 template <int J, int NW>
 __device__ float dual_pass(const KzInst& I, const DualSmem<J, NW>& S, int CS, int kind, const float2* coef,
                            float2* xout, int col0, int ncols) {
+    if (I.cmax <= CS) return dual_pass_pipe<J, NW>(I, S, CS, kind, coef, xout, col0, ncols);
     constexpr int CG = J / JT;        // column groups
     constexpr int RG = NW / CG;       // row groups in the u phase
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -139,8 +341,8 @@ __device__ float dual_pass(const KzInst& I, const DualSmem<J, NW>& S, int CS, in
             float2* upp = S.up + (size_t)rg * KZ_TILE * J;
 #pragma unroll
             for (int t = 0; t < JT; ++t) {
-                upp[(2 * lane) * J + cg * JT + t] = a0[t];
-                upp[(2 * lane + 1) * J + cg * JT + t] = a1[t];
+                upp[(cg * JT + t) * KZ_TILE + 2 * lane] = a0[t];
+                upp[(cg * JT + t) * KZ_TILE + 2 * lane + 1] = a1[t];
             }
         }
         __syncthreads();
@@ -157,7 +359,7 @@ __device__ float dual_pass(const KzInst& I, const DualSmem<J, NW>& S, int CS, in
         // ||u||^2 and the optional x output (thread per antenna pair x column)
         if (tid < 32 * J) {
             const int j = tid / 32, l = tid % 32;
-            const float2 u0 = S.us[(2 * l) * J + j], u1 = S.us[(2 * l + 1) * J + j];
+            const float2 u0 = S.us[j * KZ_TILE + 2 * l], u1 = S.us[j * KZ_TILE + 2 * l + 1];
             const float p = u0.x * u0.x + u0.y * u0.y + u1.x * u1.x + u1.y * u1.y;
             uacc += p;
             if (xout && j < ncols) {
@@ -175,34 +377,7 @@ __device__ float dual_pass(const KzInst& I, const DualSmem<J, NW>& S, int CS, in
                 stage_rows<NW>(I, trow4, tile, kc, n, ku0, ku1, S.hs, S.hrow, S.huse);
                 __syncthreads();
             }
-            const int ntask = ((n + 31) / 32) * CG;
-            for (int task = warp; task < ntask; task += NW) {
-                const int sl = (task / CG) * 32 + lane;
-                const int g = task % CG;
-                if (sl < n) {
-                    float2 acc[JT];
-#pragma unroll
-                    for (int t = 0; t < JT; ++t) acc[t] = make_float2(0.f, 0.f);
-                    const float2* hp = S.hs + sl * HSTR;
-#pragma unroll 8
-                    for (int nn = 0; nn < KZ_TILE; ++nn) {
-                        const float2 h = hp[nn];
-                        const float2* up = S.us + nn * J + g * JT;
-#pragma unroll
-                        for (int t = 0; t < JT; ++t) {
-                            const float2 u = up[t];
-                            acc[t].x = fmaf(h.x, u.x, fmaf(-h.y, u.y, acc[t].x));
-                            acc[t].y = fmaf(h.x, u.y, fmaf(h.y, u.x, acc[t].y));
-                        }
-                    }
-                    float2* zp = S.z_s + S.hrow[sl] * J + g * JT;
-#pragma unroll
-                    for (int t = 0; t < JT; ++t) {
-                        zp[t].x += acc[t].x;
-                        zp[t].y += acc[t].y;
-                    }
-                }
-            }
+            z_tile<J, NW>(S, S.hs, S.hrow, n);
         }
         __syncthreads();  // z and us settled before the next tile reuses the buffers
     }
@@ -231,7 +406,7 @@ __global__ void __launch_bounds__(NW * 32, 1) kz_dual_kernel(const __grid_consta
     {
         unsigned char* p = kz_smem;
         S.hs = reinterpret_cast<float2*>(p);
-        p += (size_t)CS * HSTR * sizeof(float2);
+        p += 2 * (size_t)CS * HSTR * sizeof(float2);
         S.up = reinterpret_cast<float2*>(p);
         p += (size_t)RG * KZ_TILE * J * sizeof(float2);
         S.us = reinterpret_cast<float2*>(p);
@@ -247,7 +422,7 @@ __global__ void __launch_bounds__(NW * 32, 1) kz_dual_kernel(const __grid_consta
         S.d_s = reinterpret_cast<float*>(p);
         p += (size_t)L.K_max * sizeof(float);
         S.hrow = reinterpret_cast<int*>(p);
-        p += (size_t)CS * sizeof(int);
+        p += 2 * (size_t)CS * sizeof(int);
         S.huse = reinterpret_cast<int*>(p);
     }
     const float tol2 = (float)(L.tol * L.tol);
@@ -538,9 +713,9 @@ int occ_t(size_t smem) {
 // Shared memory of the dual kernel with CS staged rows per chunk.
 size_t kz_smem_dual(int J, int nw, int CS, int K) {
     const int CG = J / JT, RG = nw / CG;
-    return (size_t)CS * HSTR * sizeof(float2) + (size_t)RG * KZ_TILE * J * sizeof(float2) +
+    return 2 * (size_t)CS * HSTR * sizeof(float2) + (size_t)RG * KZ_TILE * J * sizeof(float2) +
            (size_t)KZ_TILE * J * sizeof(float2) + 4 * (size_t)K * J * sizeof(float2) + (size_t)K * sizeof(float) +
-           2 * (size_t)CS * sizeof(int) + 16;
+           4 * (size_t)CS * sizeof(int) + 16;
 }
 
 cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {

@@ -40,6 +40,7 @@ struct KzInst {
     const float2* Hc;          // aligned complex64 rows
     const __nv_bfloat162* Hb;  // aligned BF16 (re, im) rows, or nullptr
     double sum_nrm;            // sum_k ||h_k||^2 (FP64)
+    int cmax;                  // most rows covering one tile
     // --- call ---
     float xi;
     int ld;                    // number of columns of s / x / v

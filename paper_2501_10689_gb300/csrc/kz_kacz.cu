@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             if (full) {
                 for (int i = warp; i < K; i += NW) {
                     float2 acc[J];
-                    row_dot<J, false>(I, i, m_s, Ntp, acc);
+                    row_dot<J, false>(I, I.rows, I.rptr, i, m_s, Ntp, acc);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                 for (int i = warp; i < K; i += NW) {
                     if (stamp[i] != t) continue;
                     float2 acc[J];
-                    row_dot<J, false>(I, i, m_s, Ntp, acc);
+                    row_dot<J, false>(I, I.rows, I.rptr, i, m_s, Ntp, acc);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                 __syncthreads();
                 for (int i = warp; i < K; i += NW) {
                     double ar[J], ai[J];
-                    row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+                    row_dot_d<J>(I, I.rows, I.rptr, i, m_s, Ntp, ar, ai);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                 const int sel = s_sel[j];
                 if (sel < 0) continue;
                 const float2 g1[1] = {s_gam[j]};
-                row_axpy<1, false>(I, sel, m_s + j * Ntp, Ntp, g1, tid, NT);
+                row_axpy<1, false>(I, I.rows, I.rptr, sel, m_s + j * Ntp, Ntp, g1, tid, NT);
             }
             ++t;
             ++since_refresh;
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             for (int j = 0; j < J; ++j) rp[j] = 0.0;
             for (int i = warp; i < K; i += NW) {
                 double ar[J], ai[J];
-                row_dot_d<J>(I, i, m_s, Ntp, ar, ai);
+                row_dot_d<J>(I, I.rows, I.rptr, i, m_s, Ntp, ar, ai);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const float2 sv = b_s[i * J + j];
