@@ -35,6 +35,22 @@ MAX_ITER = 1000
 GRK_MAX_ITER = 100000
 ERR_BAR = 1e-5
 
+# DRAM traffic of one resident-kernel launch on this workload (ncu, one pass:
+# dram__bytes_read.sum + dram__bytes_write.sum; profiles/kz_ahk_batched_512x16.md),
+# valid only for the kernel sources it was measured on (their SHA-256 prefix).
+TRAFFIC = {"sources_sha256": "ca6a2ebf809ffb4c", "bytes_per_launch": 7.59e9 + 2.00e9,
+           "launch": ("resident", 2, 512)}
+KERNEL_SOURCES = ("paper_2501_10689_gb300/csrc/kz_ahk.cu", "paper_2501_10689_gb300/csrc/kz_device.cuh",
+                  "paper_2501_10689_gb300/csrc/kz_internal.h")
+
+
+def kernel_sources_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, f), "rb").read())
+    return h.hexdigest()[:16]
+
 
 def workload_desc():
     return ("batched VR-OAHK, one persistent launch: 512 near-field channels, Nt in {1024,2048,4096}, "
@@ -275,8 +291,15 @@ def run_ours(args):
     achieved_tflops = alg_flops / (ms_per_step / 1000.0) / 1e12
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x clock under load
+    launch_now = (tuned if tuned else (args.kernel, args.rhs_per_cta, args.threads))
+    traffic = None
+    if kernel_sources_sha() == TRAFFIC["sources_sha256"] and tuple(launch_now) == TRAFFIC["launch"] \
+            and args.instances == N_INST:
+        traffic = TRAFFIC["bytes_per_launch"]
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None,
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic,
+                "traffic_note": "DRAM bytes per launch from ncu (one pass) on this workload and kernel build; "
+                                "null when the kernel sources or launch differ",
                 "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
                 "kernel": "kz_ahk_kernel (batched VR-OAHK)",
                 "alu_view": {"achieved_tflops": achieved_tflops, "fp32_fma_peak_tflops": alu_peak,
