@@ -119,6 +119,14 @@ typedef struct kz_batch kz_batch;
 kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset,
                          const int32_t* vr_len, const kz_cf32* H_packed, kz_prec prec, void* stream);
 
+/* Replace the channel of an existing plan (same K, Nt and VRs): re-pack
+ * H_packed (device, layout as in kz_plan_create, 8-byte aligned) into the
+ * plan's aligned copy (and BF16 copy) and recompute the row norms, as kernels
+ * on `stream`; nothing else of the plan changes and no host synchronisation
+ * happens, so prepared batches that name the plan stay valid.  Calls that use
+ * the plan must be ordered after this one on the stream. */
+kz_status kz_plan_update(kz_plan* plan, const kz_cf32* H_packed, void* stream);
+
 /* Release a plan (NULL is ignored).  Not stream-ordered: the caller makes
  * sure no call using the plan is still running. */
 void kz_plan_destroy(kz_plan* plan);
@@ -174,6 +182,14 @@ typedef struct {
  * items must stay valid while the batch is used.  Synchronous. */
 kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n, int32_t nrhs,
                            kz_algo algo, kz_prec prec, int32_t rhs_per_cta, void* stream);
+
+/* Point every item of a prepared batch at new buffers and a new xi (the
+ * plans and nrhs stay those of kz_batch_prepare; items[b].plan must be the
+ * plan item b was prepared with).  The instance table is copied on `stream`,
+ * ordered after earlier launches of the batch on that stream; a CUDA graph
+ * captured earlier replays with the new buffers.  items: host array of
+ * batch->n entries, free to reuse on return. */
+kz_status kz_batch_rebind(kz_batch* batch, const kz_batch_item* items, void* stream);
 
 /* Run a prepared batch: one kernel launch after a 4-byte memset of the
  * queue counter, no host synchronisation, so it can be captured in a CUDA
@@ -243,6 +259,28 @@ kz_status kz_precode_adjoint_noalloc(kz_plan* plan, int32_t nrhs, float xi, cons
                                      double tol, int32_t max_iter, kz_cf32* lambda, kz_cf32* y,
                                      kz_cf32* grad_H_packed, float* grad_xi, int32_t* iters,
                                      double* resid, int32_t* status, void* stream);
+
+/* One channel of a batched adjoint (device pointers; layouts as in
+ * kz_precode_adjoint). */
+typedef struct {
+    const kz_cf32* Q;        /* K x nrhs: the forward's v */
+    const kz_cf32* X;        /* Nt x nrhs: the forward's x */
+    const kz_cf32* G_Q;      /* K x nrhs gradient of the loss w.r.t. Q, or NULL */
+    const kz_cf32* G_X;      /* Nt x nrhs gradient w.r.t. X, or NULL (not both) */
+    kz_cf32* grad_H_packed;  /* sum vr_len: gradient w.r.t. the packed H */
+    float* grad_xi;          /* one float: gradient w.r.t. xi */
+} kz_adjoint_item;
+
+/* kz_precode_adjoint for every channel of a batch at once (step A10 over
+ * step A8): `batch` is prepared with algo VR_OAHK and C64, and its items'
+ * s / x / v buffers receive G~ = G_Q + H G_X (written here), y = H^H Lambda
+ * and Lambda; its xi are the forward's.  One kernel forms all right-hand
+ * sides, one persistent launch solves all adjoint systems, two kernels form
+ * all gradients.  items: host array of batch->n entries (copied on the
+ * stream before return).  The first call allocates a small device table
+ * owned by the batch. */
+kz_status kz_precode_adjoint_batched(kz_batch* batch, const kz_adjoint_item* items, double tol,
+                                     int32_t max_iter, int32_t* status, void* stream);
 
 /* One-line description of the last error on this thread ("" if none). */
 const char* kz_last_error(void);

@@ -57,6 +57,162 @@ class KzPrecodeFn(torch.autograd.Function):
         return gH, grad_xi, lam, None, None, None, None, None
 
 
+class BatchedPrecoder:
+    """Differentiable RZF precoders of n channels solved in one persistent launch.
+
+    The VR layout of every channel (vr_offset, vr_len, Nt) and the number of
+    columns are fixed at construction; the plans (packed-row layout, X sets,
+    tile covering lists) are built once and each call only re-packs the new
+    channel into them (kz_plan_update).  Forward: one kz_precode_batched over
+    all channels (VR-OAHK, step A8).  Backward: one kz_precode_adjoint_batched
+    (step A10 over A8): right-hand sides, adjoint solves and gradient
+    contractions for all channels in four launches.
+
+    Tensors are concatenations over channels in construction order:
+    H_cat (sum over channels of sum vr_len,) complex64; xi (n,) float32;
+    S_cat (sum nrhs K,) complex64 (channel c's block is its (nrhs, K)
+    right-hand-side layout); outputs X_cat (sum nrhs Nt,) and V_cat (sum nrhs K,).
+    ``split`` views them per channel.
+    """
+
+    def __init__(self, layouts, nrhs, tol=1e-6, max_iter=2000, device="cuda"):
+        self.layouts = [(np.asarray(o, np.int32), np.asarray(l, np.int32), int(nt)) for o, l, nt in layouts]
+        self.n = len(self.layouts)
+        self.nrhs = int(nrhs)
+        self.tol, self.max_iter = float(tol), int(max_iter)
+        self.device = torch.device(device)
+        self.K = [len(l) for _, l, _ in self.layouts]
+        self.Nt = [nt for _, _, nt in self.layouts]
+        self.L = [int(l.sum()) for _, l, _ in self.layouts]
+        self.h_off = np.concatenate([[0], np.cumsum(self.L)]).astype(np.int64)
+        self.s_off = np.concatenate([[0], np.cumsum([self.nrhs * k for k in self.K])]).astype(np.int64)
+        self.x_off = np.concatenate([[0], np.cumsum([self.nrhs * t for t in self.Nt])]).astype(np.int64)
+        dev = self.device
+        self.plans = [kp.kz_plan_create(K, Nt, o, l, torch.zeros(L, dtype=torch.complex64, device=dev))
+                      for (o, l, Nt), K, L in zip(self.layouts, self.K, self.L)]
+        self.version = 0   # bumped whenever the plans are loaded with another channel
+        self._loaded = None  # (id, version) of the tensor the plans hold
+        # scratch owned by the adjoint batch: G~ = G_Q + H G_X and y = H^H Lambda
+        self._gt = torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev)
+        self._y = torch.zeros(int(self.x_off[-1]), dtype=torch.complex64, device=dev)
+        self._fwd = self._prepare(torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev),
+                                  torch.zeros(int(self.x_off[-1]), dtype=torch.complex64, device=dev),
+                                  torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev))
+        self._adj = self._prepare(self._gt, self._y, torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev))
+        self._dense_idx = None
+
+    def split(self, cat, which):
+        """Per-channel (nrhs, K) or (nrhs, Nt) views of an S/V ('s') or X ('x') concatenation."""
+        off, w = (self.s_off, self.K) if which == "s" else (self.x_off, self.Nt)
+        return [cat[int(off[c]):int(off[c + 1])].view(self.nrhs, w[c]) for c in range(self.n)]
+
+    def _items(self, S_cat, X_cat, V_cat, xi, iters=None, resid=None):
+        dev = self.device
+        iters = torch.empty((self.n, self.nrhs), dtype=torch.int32, device=dev) if iters is None else iters
+        resid = torch.empty((self.n, self.nrhs), dtype=torch.float64, device=dev) if resid is None else resid
+        S, X, V = self.split(S_cat, "s"), self.split(X_cat, "x"), self.split(V_cat, "s")
+        return [dict(plan=self.plans[c], s=S[c], x=X[c], v=V[c], iters=iters[c], resid=resid[c], xi=xi[c])
+                for c in range(self.n)], iters, resid
+
+    def _prepare(self, S_cat, X_cat, V_cat):
+        items, _, _ = self._items(S_cat, X_cat, V_cat, [1.0] * self.n)
+        return kp.kz_batch_prepare(items, self.nrhs, "vr_oahk")
+
+    def load(self, H_cat):
+        """Re-pack H_cat into the plans (asynchronous, on the current stream)."""
+        H_cat = H_cat.detach().reshape(-1).contiguous()
+        for c in range(self.n):
+            kp.kz_plan_update(self.plans[c], H_cat[int(self.h_off[c]):int(self.h_off[c + 1])])
+        self.version += 1
+        return self.version
+
+    def _run(self, batch, items, status, adjoint_items=None):
+        kp.kz_batch_rebind(batch, items)
+        if adjoint_items is None:
+            kp.kz_precode_batched(batch, "paper", self.tol, self.max_iter, 0, status=status)
+        else:
+            kp.kz_precode_adjoint_batched(batch, adjoint_items, self.tol, self.max_iter, status=status)
+        st = int(status.item())
+        if st & kp.KZ_STATUS_BIT_NUMERIC:
+            raise kp.KzError(kp.KZ_ERR_NUMERIC, "NaN or Inf in a residual")
+        if st & kp.KZ_STATUS_BIT_NOT_CONVERGED:
+            raise kp.KzError(kp.KZ_NOT_CONVERGED, "batched solve did not converge")
+
+    def forward(self, H_cat, xi, S_cat):
+        return _BatchedFn.apply(self, H_cat, xi, S_cat)
+
+    __call__ = forward
+
+    def dense(self, H_cat):
+        """(n, K, Nt) zero-padded dense channels from H_cat (differentiable); equal K and Nt only."""
+        if len(set(self.K)) != 1 or len(set(self.Nt)) != 1:
+            raise ValueError("dense: channels differ in K or Nt")
+        K, Nt = self.K[0], self.Nt[0]
+        if self._dense_idx is None:
+            idx = []
+            for c, (o, l, _) in enumerate(self.layouts):
+                rows = np.repeat(np.arange(K, dtype=np.int64), l)
+                cols = np.repeat(o.astype(np.int64), l) + (np.arange(int(l.sum())) - np.repeat(np.cumsum(l) - l, l))
+                idx.append(c * K * Nt + rows * Nt + cols)
+            self._dense_idx = torch.from_numpy(np.concatenate(idx)).to(self.device)
+        flat = torch.zeros(self.n * K * Nt, dtype=H_cat.dtype, device=H_cat.device)
+        return flat.index_put((self._dense_idx,), H_cat).view(self.n, K, Nt)
+
+
+class _BatchedFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pre, H_cat, xi, S_cat):
+        xi_l = [float(v) for v in (xi.detach().cpu().tolist() if isinstance(xi, torch.Tensor) else xi)]
+        ver = pre.load(H_cat)
+        dev = pre.device
+        X = torch.empty(int(pre.x_off[-1]), dtype=torch.complex64, device=dev)
+        V = torch.empty(int(pre.s_off[-1]), dtype=torch.complex64, device=dev)
+        items, _, _ = pre._items(S_cat.detach().reshape(-1).contiguous(), X, V, xi_l)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        pre._run(pre._fwd, items, status)
+        ctx.pre, ctx.version, ctx.xi = pre, ver, xi_l
+        ctx.shapes = (H_cat.shape, S_cat.shape)
+        ctx.xi_is_tensor = isinstance(xi, torch.Tensor)
+        ctx.save_for_backward(H_cat.detach(), X, V)
+        return X, V
+
+    @staticmethod
+    def backward(ctx, gX, gV):
+        pre = ctx.pre
+        H_cat, X, V = ctx.saved_tensors
+        if gX is None and gV is None:
+            return None, None, None, None
+        if pre.version != ctx.version:  # another forward reloaded the plans since
+            ctx.version = pre.load(H_cat)
+        dev = pre.device
+        lam = torch.empty_like(V)
+        gH = torch.empty(int(pre.h_off[-1]), dtype=torch.complex64, device=dev)
+        gxi = torch.empty(pre.n, dtype=torch.float32, device=dev)
+        gX = gX.contiguous() if gX is not None else None
+        gV = gV.contiguous() if gV is not None else None
+        items, _, _ = pre._items(pre._gt, pre._y, lam, ctx.xi)
+        Qs, Xs = pre.split(V, "s"), pre.split(X, "x")
+        GQ = pre.split(gV, "s") if gV is not None else [None] * pre.n
+        GX = pre.split(gX, "x") if gX is not None else [None] * pre.n
+        adj = [dict(Q=Qs[c], X=Xs[c], G_Q=GQ[c], G_X=GX[c],
+                    grad_H=gH[int(pre.h_off[c]):int(pre.h_off[c + 1])], grad_xi=gxi[c:c + 1])
+               for c in range(pre.n)]
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        pre._run(pre._adj, items, status, adjoint_items=adj)
+        hs, ss = ctx.shapes
+        return None, gH.view(hs), (gxi if ctx.xi_is_tensor else None), lam.view(ss)
+
+
+def sum_rate_loss_batched(H_dense, X, snr_lin):
+    """Sum over channels of sum_rate_loss: H_dense (n, K, Nt), X (n, K, Nt)."""
+    F = X.transpose(1, 2) / torch.linalg.norm(X.reshape(X.shape[0], -1), dim=1)[:, None, None]
+    G = H_dense @ F
+    sig = torch.abs(torch.diagonal(G, dim1=1, dim2=2)) ** 2
+    tot = torch.sum(torch.abs(G) ** 2, dim=2)
+    sinr = sig / (tot - sig + 1.0 / snr_lin)
+    return -torch.sum(torch.log2(1.0 + sinr))
+
+
 def precode(H_packed, xi, S, vr_offset, vr_len, Nt, tol=1e-7, max_iter=2000):
     """Differentiable (X, V) = (H^H V, (H H^H + xi I)^-1 S)."""
     return KzPrecodeFn.apply(H_packed, xi, S, np.asarray(vr_offset, np.int32), np.asarray(vr_len, np.int32),
@@ -75,13 +231,12 @@ def sum_rate_loss(H_dense, X, snr_lin):
 
 
 def dense_from_packed(H_packed, vr_offset, vr_len, Nt):
-    """K x Nt matrix from the packed rows (differentiable gather; tensor ops only)."""
-    K = len(vr_len)
-    idx_rows, idx_cols = [], []
-    for k in range(K):
-        idx_rows += [k] * int(vr_len[k])
-        idx_cols += list(range(int(vr_offset[k]), int(vr_offset[k]) + int(vr_len[k])))
-    H = torch.zeros((K, Nt), dtype=H_packed.dtype, device=H_packed.device)
-    r = torch.tensor(idx_rows, device=H_packed.device)
-    c = torch.tensor(idx_cols, device=H_packed.device)
-    return H.index_put((r, c), H_packed)
+    """K x Nt matrix from the packed rows (differentiable scatter; tensor ops only)."""
+    off = np.asarray(vr_offset, np.int64)
+    ln = np.asarray(vr_len, np.int64)
+    K = len(ln)
+    rows = np.repeat(np.arange(K, dtype=np.int64), ln)
+    cols = np.repeat(off, ln) + (np.arange(int(ln.sum())) - np.repeat(np.cumsum(ln) - ln, ln))
+    idx = torch.from_numpy(rows * Nt + cols).to(H_packed.device)
+    flat = torch.zeros(K * Nt, dtype=H_packed.dtype, device=H_packed.device)
+    return flat.index_put((idx,), H_packed).view(K, Nt)

@@ -54,7 +54,6 @@ struct kz_plan {
     int cmax = 0;  // largest number of rows covering one tile
     int64_t sumL = 0, total2 = 0;
     kz_prec prec = KZ_C64;
-    double sum_nrm = 0.0;
     std::vector<int> F, xptr, xidx;
     // device
     int4* d_rows = nullptr;
@@ -100,7 +99,8 @@ struct kz_plan {
         I.trow4 = d_trow4;
         I.Hc = d_Hc;
         I.Hb = d_Hb;
-        I.sum_nrm = sum_nrm;
+        I.nrmd = d_nrmd;
+        I.in_off = d_in_off;
         I.cmax = cmax;
         return I;
     }
@@ -116,7 +116,12 @@ struct kz_batch {
     KzInst* d_insts = nullptr;
     int2* d_items = nullptr;
     int* d_queue = nullptr;
+    KzAdjItem* d_adj = nullptr;  // adjoint item table (allocated on first use)
+    bool all_v = true;           // every item has a v buffer
+    std::vector<const kz_plan*> plans;  // the items' plans, fixed at preparation
+    std::vector<KzInst> h_insts;        // host copy of the instance table
     ~kz_batch() {
+        if (d_adj) cudaFree(d_adj);
         if (d_insts) cudaFree(d_insts);
         if (d_items) cudaFree(d_items);
         if (d_queue) cudaFree(d_queue);
@@ -380,14 +385,23 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     KZ_TRY(kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, K, acc, P->d_Hc,
                         P->d_Hb, st));
     KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, st));
-    std::vector<double> nrm(K);
-    KZ_TRY(cudaMemcpyAsync(nrm.data(), P->d_nrmd, K * sizeof(double), cudaMemcpyDeviceToHost, st));
     KZ_TRY(cudaStreamSynchronize(st));
 #undef KZ_TRY
-    P->sum_nrm = 0.0;
-    for (double v : nrm) P->sum_nrm += v;
     *out = P;
     return KZ_OK;
+}
+
+kz_status kz_plan_update(kz_plan* P, const kz_cf32* H_packed, void* stream) {
+    g_err.clear();
+    if (!P || !H_packed || !aligned(H_packed, 8)) {
+        kz_set_error("kz_plan_update: need a plan and an 8-byte aligned H_packed");
+        return KZ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, P->K,
+                                 P->total2, P->d_Hc, P->d_Hb, st);
+    if (e == cudaSuccess) e = kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, P->K, P->d_nrmd, P->d_nrm, st);
+    return check_launch(e, "kz_plan_update");
 }
 
 void kz_plan_destroy(kz_plan* plan) { delete plan; }
@@ -612,8 +626,11 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         I.iters = it.iters;
         I.resid = it.resid;
         insts[b] = I;
+        if (!it.v) B->all_v = false;
         B->cost[b] = (double)it.plan->total2 + 4.0 * it.plan->Ntp;
+        B->plans.push_back(it.plan);
     }
+    B->h_insts = insts;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(&B->d_insts, insts, st);
     if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, sizeof(int));
@@ -625,6 +642,42 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         return e == cudaErrorMemoryAllocation ? KZ_ERR_NOMEM : KZ_ERR_CUDA;
     }
     *out = B;
+    return KZ_OK;
+}
+
+kz_status kz_batch_rebind(kz_batch* B, const kz_batch_item* items, void* stream) {
+    g_err.clear();
+    if (!B || !items) {
+        kz_set_error("kz_batch_rebind: need a batch and its items");
+        return KZ_ERR_INVALID_ARG;
+    }
+    std::vector<KzInst> insts = B->h_insts;
+    bool all_v = true;
+    for (int b = 0; b < B->n; ++b) {
+        const kz_batch_item& it = items[b];
+        if (it.plan != B->plans[b]) {
+            kz_set_error("kz_batch_rebind: item %d names another plan than at preparation", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        if (!it.s || !it.x || !it.iters || !it.resid || !(it.xi > 0.f)) {
+            kz_set_error("kz_batch_rebind: item %d is missing a buffer or positive xi", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        KzInst& I = insts[b];
+        I.xi = it.xi;
+        I.s = reinterpret_cast<const float2*>(it.s);
+        I.x = reinterpret_cast<float2*>(it.x);
+        I.v = reinterpret_cast<float2*>(it.v);
+        I.iters = it.iters;
+        I.resid = it.resid;
+        if (!it.v) all_v = false;
+    }
+    // pageable source: staged before return, so the host vector may go away
+    cudaError_t e = cudaMemcpyAsync(B->d_insts, insts.data(), insts.size() * sizeof(KzInst), cudaMemcpyHostToDevice,
+                                    static_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return check_launch(e, "kz_batch_rebind");
+    B->h_insts.swap(insts);
+    B->all_v = all_v;
     return KZ_OK;
 }
 
@@ -779,6 +832,49 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
     cudaError_t e = batch_layout_k(B, kernel, rhs_per_cta, nw, sm_count(), st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     return check_launch(e, "kz_batch_set_launch");
+}
+
+kz_status kz_precode_adjoint_batched(kz_batch* B, const kz_adjoint_item* items, double tol, int32_t max_iter,
+                                     int32_t* status, void* stream) {
+    g_err.clear();
+    if (!B || !items) {
+        kz_set_error("kz_precode_adjoint_batched: need a batch and its items");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (B->algo != KZ_VR_OAHK || B->prec != KZ_C64 || !B->all_v) {
+        kz_set_error("kz_precode_adjoint_batched: the batch must run VR_OAHK on C64 plans with a v buffer per item");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (!(tol >= 0.0) || max_iter < 1) {
+        kz_set_error("kz_precode_adjoint_batched: need tol >= 0 and max_iter >= 1");
+        return KZ_ERR_INVALID_ARG;
+    }
+    std::vector<KzAdjItem> adj(B->n);
+    for (int b = 0; b < B->n; ++b) {
+        const kz_adjoint_item& it = items[b];
+        if (!it.Q || !it.X || !it.grad_H_packed || !it.grad_xi || (!it.G_Q && !it.G_X)) {
+            kz_set_error("kz_precode_adjoint_batched: item %d needs Q, X, grad_H_packed, grad_xi and G_Q or G_X", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        adj[b] = KzAdjItem{reinterpret_cast<const float2*>(it.Q), reinterpret_cast<const float2*>(it.X),
+                           reinterpret_cast<const float2*>(it.G_Q), reinterpret_cast<const float2*>(it.G_X),
+                           reinterpret_cast<float2*>(it.grad_H_packed), it.grad_xi};
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!B->d_adj) e = cudaMalloc((void**)&B->d_adj, (size_t)B->n * sizeof(KzAdjItem));
+    if (e != cudaSuccess) {
+        kz_set_error("kz_precode_adjoint_batched: %s", cudaGetErrorString(e));
+        return KZ_ERR_NOMEM;
+    }
+    // staged copy from pageable memory: the host table may be reused on return
+    e = cudaMemcpyAsync(B->d_adj, adj.data(), (size_t)B->n * sizeof(KzAdjItem), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = kz_adjoint_rhs_batched(B->d_insts, B->d_adj, B->n, B->K_max, B->nrhs, st);
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint_batched right-hand side");
+    kz_status rc = kz_precode_batched(B, KZ_SEL_ARGMAX, tol, max_iter, 0, 0, status, stream);
+    if (rc != KZ_OK) return rc;
+    e = kz_adjoint_contract_batched(B->d_insts, B->d_adj, B->n, B->K_max, B->nrhs, st);
+    return check_launch(e, "kz_precode_adjoint_batched contraction");
 }
 
 kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q, const kz_cf32* X,

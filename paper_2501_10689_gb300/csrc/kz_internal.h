@@ -39,7 +39,8 @@ struct KzInst {
     const int4* trow4;         // per entry {row, rptr - a, a, a + len2}
     const float2* Hc;          // aligned complex64 rows
     const __nv_bfloat162* Hb;  // aligned BF16 (re, im) rows, or nullptr
-    double sum_nrm;            // sum_k ||h_k||^2 (FP64)
+    const double* nrmd;        // ||h_k||^2 in FP64
+    const int* in_off;         // row k's offset in the caller's packed layout
     int cmax;                  // most rows covering one tile
     // --- call ---
     float xi;
@@ -88,6 +89,22 @@ cudaError_t kz_adjoint_rhs(const KzInst& I, int nrhs, const float2* G_Q, const f
 cudaError_t kz_adjoint_contract(const KzInst& I, int nrhs, const float2* Q, const float2* X,
                                 const float2* G_X, const float2* Lam, const float2* Y,
                                 const int* in_off, float2* grad_H, float* grad_xi, cudaStream_t st);
+
+// Batched adjoint pieces: item b's channel is insts[b] (its s / x / v are the
+// adjoint right-hand side G~, y = H^H Lambda and Lambda), its gradients and
+// forward outputs are in adj[b].
+struct KzAdjItem {
+    const float2* Q;
+    const float2* X;
+    const float2* G_Q;
+    const float2* G_X;
+    float2* grad_H;
+    float* grad_xi;
+};
+cudaError_t kz_adjoint_rhs_batched(const KzInst* insts, const KzAdjItem* adj, int n, int K_max, int nrhs,
+                                   cudaStream_t st);
+cudaError_t kz_adjoint_contract_batched(const KzInst* insts, const KzAdjItem* adj, int n, int K_max, int nrhs,
+                                        cudaStream_t st);
 
 // Thread-local last-error text (kz_api.cu).
 void kz_set_error(const char* fmt, ...);

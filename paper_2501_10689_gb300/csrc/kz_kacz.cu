@@ -90,7 +90,12 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             a = warp_sum_d(a);
             if (lane == 0) s_sn2[warp] = a;
         }
-        if (tid == 0) s_sumd = I.sum_nrm + (double)K * xi;  // ||B||_F^2
+        if (warp == NW - 1) {  // ||B||_F^2 = sum_k ||h_k||^2 + K xi, in FP64
+            double a = 0.0;
+            for (int i = lane; i < K; i += 32) a += I.nrmd[i];
+            a = warp_sum_d(a);
+            if (lane == 0) s_sumd = a + (double)K * xi;
+        }
         __syncthreads();
         if (tid == 0) {
             int act = 0;

@@ -35,15 +35,21 @@ class KzError(RuntimeError):
         self.code = code
 
 
+class KzAdjointItem(ctypes.Structure):
+    _fields_ = [("Q", ctypes.c_void_p), ("X", ctypes.c_void_p), ("G_Q", ctypes.c_void_p), ("G_X", ctypes.c_void_p),
+                ("grad_H_packed", ctypes.c_void_p), ("grad_xi", ctypes.c_void_p)]
+
+
 class KzBatchItem(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("s", ctypes.c_void_p), ("x", ctypes.c_void_p),
                 ("v", ctypes.c_void_p), ("iters", ctypes.c_void_p), ("resid", ctypes.c_void_p),
                 ("xi", ctypes.c_float)]
 
 
-EXPORTS = ("kz_plan_create", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
+EXPORTS = ("kz_plan_create", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
-           "kz_precode_adjoint", "kz_precode_adjoint_noalloc", "kz_last_error", "kz_version")
+           "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
+           "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "dual": 2}
 
 
@@ -64,6 +70,12 @@ def load():
                                   ctypes.c_double, ctypes.c_uint64)
     lib.kz_plan_create.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_create.restype = I32
+    lib.kz_batch_rebind.argtypes = [P, P, P]
+    lib.kz_batch_rebind.restype = I32
+    lib.kz_plan_update.argtypes = [P, P, P]
+    lib.kz_plan_update.restype = I32
+    lib.kz_precode_adjoint_batched.argtypes = [P, P, F64, I32, P, P]
+    lib.kz_precode_adjoint_batched.restype = I32
     lib.kz_plan_destroy.argtypes = [P]
     lib.kz_plan_destroy.restype = None
     lib.kz_plan_query.argtypes = [P, P, P, P, P, P, P, P]
@@ -149,6 +161,12 @@ def kz_plan_create(K, Nt, vr_offset, vr_len, H_packed, prec="c64", stream=None) 
     return Plan(h, K, Nt, int(ln.sum()), prec)
 
 
+def kz_plan_update(plan: Plan, H_packed, stream=None):
+    lib = load()
+    _check_c64(H_packed, (plan.sum_len,), "H_packed")
+    return _check(lib.kz_plan_update(plan.handle, _ptr(H_packed), _stream(stream)))
+
+
 def kz_plan_query(plan: Plan):
     lib = load()
     K = plan.K
@@ -196,7 +214,8 @@ def kz_precode_ex(plan: Plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v,
 class Batch:
     def __init__(self, handle, keep):
         self.handle = handle
-        self._keep = keep  # the plans and tensors the device table points at
+        self.keep = keep  # the plans and tensors the device table points at
+        self.nrhs = 0
 
     def __del__(self):
         if getattr(self, "handle", None) and _lib is not None:
@@ -204,11 +223,8 @@ class Batch:
             self.handle = None
 
 
-def kz_batch_prepare(items, nrhs, algo, prec="c64", rhs_per_cta=0, stream=None) -> Batch:
-    """``items``: list of dicts with plan, s, x, v (or None), iters, resid, xi."""
-    lib = load()
+def _batch_items(items, nrhs):
     arr = (KzBatchItem * len(items))()
-    keep = []
     for k, it in enumerate(items):
         p = it["plan"]
         _check_c64(it["s"], (nrhs, p.K), "s")
@@ -216,12 +232,30 @@ def kz_batch_prepare(items, nrhs, algo, prec="c64", rhs_per_cta=0, stream=None) 
         arr[k] = KzBatchItem(p.handle.value, it["s"].data_ptr(), it["x"].data_ptr(),
                              it["v"].data_ptr() if it.get("v") is not None else None, it["iters"].data_ptr(),
                              it["resid"].data_ptr(), float(it["xi"]))
-        keep.append(it)
+    return arr
+
+
+def kz_batch_prepare(items, nrhs, algo, prec="c64", rhs_per_cta=0, stream=None) -> Batch:
+    """``items``: list of dicts with plan, s, x, v (or None), iters, resid, xi."""
+    lib = load()
+    arr = _batch_items(items, nrhs)
     h = ctypes.c_void_p()
     _check(lib.kz_batch_prepare(ctypes.byref(h), ctypes.cast(arr, ctypes.c_void_p), len(items), nrhs,
                                 ALGOS[algo] if isinstance(algo, str) else algo, PREC[prec], int(rhs_per_cta),
                                 _stream(stream)))
-    return Batch(h, keep)
+    b = Batch(h, list(items))
+    b.nrhs = nrhs
+    return b
+
+
+def kz_batch_rebind(batch: Batch, items, stream=None):
+    """Point the batch's items at new buffers / xi (same plans, same order)."""
+    lib = load()
+    if len(items) != len(batch.keep):
+        raise ValueError("kz_batch_rebind: the batch has %d items" % len(batch.keep))
+    arr = _batch_items(items, batch.nrhs)
+    _check(lib.kz_batch_rebind(batch.handle, ctypes.cast(arr, ctypes.c_void_p), _stream(stream)))
+    batch.keep = list(items)
 
 
 def kz_precode_batched(batch: Batch, sel, tol, max_iter, seed, refresh=0, status=None, stream=None):
@@ -265,6 +299,19 @@ def kz_precode_adjoint_noalloc(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_it
                                                  _ptr(G_X), float(tol), int(max_iter), _ptr(lam), _ptr(y),
                                                  _ptr(grad_H_packed), _ptr(grad_xi), _ptr(iters), _ptr(resid),
                                                  _ptr(status), _stream(stream)))
+
+
+def kz_precode_adjoint_batched(batch: Batch, items, tol, max_iter, status=None, stream=None):
+    """``items``: list of dicts with Q, X, G_Q (or None), G_X (or None), grad_H, grad_xi."""
+    lib = load()
+    arr = (KzAdjointItem * len(items))()
+    for k, it in enumerate(items):
+        arr[k] = KzAdjointItem(it["Q"].data_ptr(), it["X"].data_ptr(),
+                               it["G_Q"].data_ptr() if it.get("G_Q") is not None else None,
+                               it["G_X"].data_ptr() if it.get("G_X") is not None else None,
+                               it["grad_H"].data_ptr(), it["grad_xi"].data_ptr())
+    return _check(lib.kz_precode_adjoint_batched(batch.handle, ctypes.cast(arr, ctypes.c_void_p), float(tol),
+                                                 int(max_iter), _ptr(status), _stream(stream)))
 
 
 def kz_version() -> int:
