@@ -66,7 +66,7 @@ def parse():
     ap.add_argument("--instances", type=int, default=N_INST)
     ap.add_argument("--verify", type=int, default=48, help="instances checked against the oracle")
     ap.add_argument("--rhs-per-cta", type=int, default=0, help="fix the launch instead of autotuning")
-    ap.add_argument("--kernel", default="resident", choices=["resident", "dual"],
+    ap.add_argument("--kernel", default="resident", choices=["resident", "dual", "tc"],
                     help="kernel used with --rhs-per-cta")
     ap.add_argument("--threads", type=int, default=512, help="threads per CTA used with --rhs-per-cta")
     ap.add_argument("--no-grk", action="store_true")

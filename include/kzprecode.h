@@ -85,8 +85,8 @@ typedef enum { KZ_SEL_PAPER = 0, KZ_SEL_BAIWU = 1, KZ_SEL_ARGMAX = 2 } kz_select
 /* Storage / arithmetic of the iteration.  C64: complex64 H, FP32 arithmetic.
  * BF16_MIXED (AHK / VR_OAHK only): the residual and projection read a BF16
  * copy of H with FP32 accumulation, in correction form against a true
- * residual recomputed from the complex64 H with FP64 accumulation every
- * refresh period; that recomputation drives the stopping test. */
+ * residual recomputed from the complex64 H (FP32 products, compensated
+ * sums) every refresh period; that recomputation drives the stopping test. */
 typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
 
 /* Which kernel runs AHK / VR_OAHK.  RESIDENT keeps the iterate m of J
@@ -95,9 +95,15 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * r = s - B B^H q of 8 or 16 columns, updates r by r -= gamma (H H^H phi + xi phi)
  * (the same iterates as eq. (update4)), stages each 64-antenna tile of H in
  * shared memory once per pass for all its columns, and recomputes the true
- * residual to confirm stops.  AUTO: RESIDENT for kz_precode; the batch
- * default is RESIDENT until kz_batch_tune or kz_batch_set_launch chooses. */
-typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_DUAL = 2 } kz_kernel;
+ * residual to confirm stops.  TC (AHK / VR_OAHK, C64, 4 or 8 columns) is
+ * RESIDENT in correction form with the two contractions of each iteration
+ * (the V-row residuals and H_V^H phi) on the tensor cores in TF32 with FP32
+ * sums; the right-hand side b = s - H m_ref is recomputed from the complex64
+ * H every `refresh` iterations and every stop is confirmed on the true
+ * residual, so results meet the same tolerance as RESIDENT.  AUTO: RESIDENT
+ * for kz_precode; the batch default is RESIDENT until kz_batch_tune or
+ * kz_batch_set_launch chooses. */
+typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_DUAL = 2, KZ_KERNEL_TC = 3 } kz_kernel;
 
 typedef struct kz_plan kz_plan;
 typedef struct kz_batch kz_batch;
@@ -156,7 +162,9 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
 
 /* kz_precode with an explicit kernel (see kz_kernel).  With KZ_KERNEL_DUAL,
  * rhs_per_cta must be 0, 8 or 16 (0: 16 when nrhs >= 16 and it fits, else 8)
- * and algo AHK or VR_OAHK on a C64 plan (else KZ_ERR_UNSUPPORTED). */
+ * and algo AHK or VR_OAHK on a C64 plan (else KZ_ERR_UNSUPPORTED).  With
+ * KZ_KERNEL_TC, rhs_per_cta must be 0, 4 or 8 (0: 8 when nrhs >= 8 and it
+ * fits, else 4), same algorithms and plans. */
 kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
                         kz_select sel, double tol, int32_t max_iter, uint64_t seed, kz_cf32* x,
                         kz_cf32* v, int32_t* iters, double* resid, int32_t* status, kz_kernel kernel,

@@ -18,17 +18,30 @@
 // The right-hand side of the row equations is b (= s for C64).  In BF16_MIXED
 // the iteration reads the BF16 copy of H and works in correction form: at
 // each refresh m_ref = H^H q and b = s - H m_ref are recomputed from the
-// complex64 H with FP64 accumulation, m restarts at 0, so the inner residual
+// complex64 H (compensated FP32 sums), m restarts at 0, so the inner residual
 // b - H_bf16 m - xi q differs from the true one only by (H - H_bf16) times the
 // correction.  The refresh's true residual drives the stopping test.
+//
+// The tensor-core mode (MODE 2) runs the same correction form on the
+// complex64 H, with the two contractions of every iteration on the tensor
+// cores (TF32 products, FP32 sums): the V-row residuals as 8-row blocks
+// (rows sorted by VR centre, so a block's rows share most of their union
+// interval) and the aggregate H_V^H phi per tile.  The F half-step, the
+// refresh and every stopping decision stay in FP32 on the CUDA cores.
 #include "kz_device.cuh"
 
 namespace {
 
 constexpr int ALGO_OAHK = KZ_VR_OAHK;
 
-template <int J, int NW, bool BF16>
+// MODE 0: complex64, FP32 CUDA-core products; 1: BF16_MIXED (correction
+// form on the BF16 copy); 2: tensor-core correction form on complex64.
+template <int J, int NW, int MODE>
 __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32))) kz_ahk_kernel(const __grid_constant__ KzLaunch L) {
+    constexpr bool BF16 = (MODE == 1);
+    constexpr bool TC = (MODE == 2);
+    constexpr bool CORR = (MODE != 0);  // correction form with periodic refresh
+    static_assert(!TC || J == 4 || J == 8, "tensor-core mode takes 4 or 8 columns");
     extern __shared__ __align__(16) unsigned char kz_smem[];
     __shared__ KzInst sI;
     __shared__ float s_part[NW][3 * J];
@@ -51,7 +64,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         off += (bytes + 15) & ~(size_t)15;
         return p;
     };
-    float2* m_s = reinterpret_cast<float2*>(carve((size_t)J * L.Ntp_max * sizeof(float2)));
+    // iterate columns; the tensor-core mode pads each by 4 entries so the 8
+    // columns read by one MMA fragment fall in different banks
+    float2* m_s = reinterpret_cast<float2*>(carve((size_t)J * (L.Ntp_max + (TC ? 4 : 0)) * sizeof(float2)));
     float2* b_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* q_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* p_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
@@ -64,6 +79,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     float* dinv_s = reinterpret_cast<float*>(carve((size_t)L.K_max * sizeof(float)));
     int* tptr_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE + 1) * sizeof(int)));
     int* tnv_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE) * sizeof(int)));
+    int* vs_s = TC ? reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int))) : nullptr;
     const float tol2 = (float)(L.tol * L.tol);
     const bool oahk = (L.algo == ALGO_OAHK);
 
@@ -85,12 +101,13 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         __syncthreads();
         const KzInst& I = sI;
         const int K = I.K, Nt = I.Nt, Ntp = I.Ntp, nF = oahk ? I.nF : 0;
+        const int MS = TC ? Ntp + 4 : Ntp;  // column stride of m_s
         const int col0 = it.y, ncols = min(J, I.ld - col0);
         const float xi = I.xi;
         const int4* trow4 = I.trow4;
 
         // ---- initialise: m = 0, q = 0, b = s, d = ||h||^2 + xi
-        for (int e = tid; e < J * Ntp; e += NT) m_s[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < J * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
         for (int e = tid; e < K * J; e += NT) {
             const int i = e / J, j = e % J;
             b_s[e] = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -108,6 +125,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         for (int t2 = tid; t2 <= I.ntiles; t2 += NT) {
             tptr_s[t2] = I.tptr[t2];
             if (t2 < I.ntiles) tnv_s[t2] = I.tnv[t2];
+        }
+        if (TC) {  // V rows by VR centre (all rows for AHK)
+            const int* src = I.vsort + (oahk ? 0 : K - I.nF);
+            for (int v = tid; v < K - nF; v += NT) vs_s[v] = src[v];
         }
         __syncthreads();
         if (warp < J) {
@@ -134,14 +155,16 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 
         int t = 0, since_refresh = 0;
         while (s_active) {
-            const int act = s_active;
+            // correction form: a column whose residual passed the test waits,
+            // without stepping, for the next refresh to confirm it
+            const int act = CORR ? (s_active & ~s_pending) : s_active;
             // ---------------- F half-step (VR-OAHK only)
             if (oahk) {
                 ++t;
                 for (int f = warp; f < nF; f += NW) {
                     const int i = order_s[f];
                     float2 acc[J];
-                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, Ntp, acc);
+                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, acc);
                     float2 g[J];
                     const float di = d_s[i];
 #pragma unroll
@@ -152,7 +175,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const bool on = (act >> j) & 1;
                         g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
                     }
-                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, Ntp, g, lane, 32);
+                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, g, lane, 32);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -168,12 +191,54 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             float pr[J], pn[J], pp[J];
 #pragma unroll
             for (int j = 0; j < J; ++j) pr[j] = pn[j] = pp[j] = 0.f;
+            if constexpr (TC) {
+                // 8-row blocks on the tensor cores; lane (g, c) finishes column
+                // g of rows 2c and 2c + 1 of each block
+                const int g = lane >> 2, c = lane & 3;
+                float spr = 0.f, spn = 0.f, spp = 0.f;
+                const int nblk = (vcount + 7) >> 3;
+                for (int blk = warp; blk < nblk; blk += NW) {
+                    float d[4];
+                    tc_row_block<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, blk, m_s, MS, d);
+                    if (g < J) {
+                        const bool on = (act >> g) & 1;
+#pragma unroll
+                        for (int rr = 0; rr < 2; ++rr) {
+                            const int k = 8 * blk + 2 * c + rr;
+                            if (k < vcount) {
+                                const int i = vs_s[k];
+                                const float2 bv = b_s[i * J + g], qv = q_s[i * J + g];
+                                const float rx = bv.x - (rr ? d[1] : d[0]) - xi * qv.x;
+                                const float ry = bv.y - (rr ? d[3] : d[2]) - xi * qv.y;
+                                const float r2 = rx * rx + ry * ry;
+                                const float di = dinv_s[i];
+                                const float2 ph = on ? make_float2(rx * di, ry * di) : make_float2(0.f, 0.f);
+                                spr += r2;
+                                spn += on ? r2 * di : 0.f;
+                                spp += ph.x * ph.x + ph.y * ph.y;
+                                p_s[i * J + g] = ph;
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 4; o <<= 1) {
+                    spr += __shfl_xor_sync(KZ_FULL, spr, o);
+                    spn += __shfl_xor_sync(KZ_FULL, spn, o);
+                    spp += __shfl_xor_sync(KZ_FULL, spp, o);
+                }
+                if (c == 0 && g < J) {
+                    s_part[warp][g] = spr;
+                    s_part[warp][J + g] = spn;
+                    s_part[warp][2 * J + g] = spp;
+                }
+            } else {
             // rows v and v + NW go to the same warp together (two loads streams)
             for (int v = warp; v < vcount; v += 2 * NW) {
                 const int i0 = order_s[v0 + v];
                 const int i1 = (v + NW < vcount) ? order_s[v0 + v + NW] : -1;
                 float2 acc0[J], acc1[J];
-                row_dot2<J, BF16>(I, rows_s, rptr_s, i0, i1, m_s, Ntp, acc0, acc1);
+                row_dot2<J, BF16>(I, rows_s, rptr_s, i0, i1, m_s, MS, acc0, acc1);
 #pragma unroll
                 for (int rr = 0; rr < 2; ++rr) {
                     const int i = rr ? i1 : i0;
@@ -202,6 +267,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     s_part[warp][J + j] = pn[j];
                     s_part[warp][2 * J + j] = pp[j];
                 }
+            }
             }
             __syncthreads();
             if (tid < 3 * J) {
@@ -233,10 +299,16 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             }
             __syncthreads();
             // ---------------- confirmation: m = H^H q from the complex64 H, the
-            // true residual s - H m - xi q with FP64 accumulation, and the test
+            // true residual s - H m - xi q with compensated sums, and the test
             // again.  In BF16_MIXED this is also the periodic refresh that sets
             // the correction right-hand side b = s - H m and restarts m at 0.
-            if (s_pending || (BF16 && since_refresh >= L.refresh)) {
+            // the true residual is recomputed (and, in correction form, b with
+            // it): at once for a tentative stop in MODE 0; in correction form
+            // when every active column waits, at the refresh period, or at the
+            // last iteration
+            const bool last = t >= L.max_iter;
+            if ((!CORR && s_pending) ||
+                (CORR && ((s_pending && (s_pending == s_active || last)) || since_refresh >= L.refresh))) {
                 since_refresh = 0;
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     float2 u0[J], u1[J];
@@ -244,25 +316,24 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        m_s[j * Ntp + n] = u0[j];
-                        m_s[j * Ntp + n + 1] = u1[j];
+                        m_s[j * MS + n] = u0[j];
+                        m_s[j * MS + n + 1] = u1[j];
                     }
                 }
                 __syncthreads();
-                double rp[J];
+                float rp[J];
 #pragma unroll
-                for (int j = 0; j < J; ++j) rp[j] = 0.0;
+                for (int j = 0; j < J; ++j) rp[j] = 0.f;
                 for (int i = warp; i < K; i += NW) {
-                    double ar[J], ai[J];
-                    row_dot_d<J>(I, rows_s, rptr_s, i, m_s, Ntp, ar, ai);
+                    float2 hi[J], lo[J];
+                    row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
-                        const double bx = (double)sv.x - ar[j], by = (double)sv.y - ai[j];
-                        const float2 qv = q_s[i * J + j];
-                        const double rx = bx - (double)xi * qv.x, ry = by - (double)xi * qv.y;
-                        rp[j] += rx * rx + ry * ry;
-                        if (BF16 && lane == 0) b_s[i * J + j] = make_float2((float)bx, (float)by);
+                        const float2 r = true_resid(sv, hi[j], lo[j], q_s[i * J + j], xi);
+                        rp[j] += r.x * r.x + r.y * r.y;
+                        if (CORR && lane == 0)
+                            b_s[i * J + j] = make_float2((sv.x - hi[j].x) - lo[j].x, (sv.y - hi[j].y) - lo[j].y);
                     }
                 }
                 if (lane == 0) {
@@ -272,7 +343,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 __syncthreads();
                 if (tid == 0) {
                     int a2 = s_active;
-                    const int tested = BF16 ? a2 : s_pending;
+                    const int tested = CORR ? a2 : s_pending;
                     for (int j = 0; j < ncols; ++j) {
                         if (!((tested >> j) & 1) || !((a2 >> j) & 1)) continue;
                         double rn2 = 0.0;
@@ -292,16 +363,60 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     s_active = a2;
                     s_pending = 0;
                 }
-                if (BF16)
-                    for (int e = tid; e < J * Ntp; e += NT) m_s[e] = make_float2(0.f, 0.f);
+                if (CORR)
+                    for (int e = tid; e < J * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
                 __syncthreads();
             }
             if (!s_active) break;
             // columns that take the aggregate step this iteration (a column whose
             // confirmation failed keeps iterating, so nothing stalls)
-            const int stepmask = (!oahk && t >= L.max_iter) ? 0 : s_active;
+            const int stepmask = (!oahk && t >= L.max_iter) ? 0 : (CORR ? (s_active & ~s_pending) : s_active);
             // ---------------- aggregate u = H_V^H phi_V (antenna-major), ||u||^2
             if (stepmask) {
+                if constexpr (TC) {
+                    constexpr int NB = J / 4;
+                    const int g = lane >> 2, c = lane & 3;
+                    float uu[2 * NB];
+#pragma unroll
+                    for (int j = 0; j < 2 * NB; ++j) uu[j] = 0.f;
+                    for (int tile = warp; tile < I.ntiles; tile += NW) {
+                        const int k0 = tptr_s[tile];
+                        const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
+                        if (k0 == k1) continue;
+                        float acc[8][NB][4];
+                        tc_tile_aggr<J>(I.Hc, trow4, tile, k0, k1, p_s, acc);
+#pragma unroll
+                        for (int ab = 0; ab < 8; ++ab) {
+                            const int n = tile * KZ_TILE + 8 * ab + g;
+#pragma unroll
+                            for (int nb = 0; nb < NB; ++nb) {
+                                float2 u0, u1;
+                                tc_u_combine(acc[ab][nb], u0, u1);
+                                const int j = 4 * nb + 2 * c;
+                                if (c < 2) {
+                                    if (n < Nt) {
+                                        if (j < ncols) I.x[(size_t)(col0 + j) * Nt + n] = u0;
+                                        if (j + 1 < ncols) I.x[(size_t)(col0 + j + 1) * Nt + n] = u1;
+                                    }
+                                    uu[2 * nb] += u0.x * u0.x + u0.y * u0.y;
+                                    uu[2 * nb + 1] += u1.x * u1.x + u1.y * u1.y;
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 2 * NB; ++j) {
+#pragma unroll
+                        for (int o = 4; o < 32; o <<= 1) uu[j] += __shfl_xor_sync(KZ_FULL, uu[j], o);
+                    }
+                    if (g == 0 && c < 2) {
+#pragma unroll
+                        for (int nb = 0; nb < NB; ++nb) {
+                            s_part[warp][4 * nb + 2 * c] = uu[2 * nb];
+                            s_part[warp][4 * nb + 2 * c + 1] = uu[2 * nb + 1];
+                        }
+                    }
+                } else {
                 float uu[J];
 #pragma unroll
                 for (int j = 0; j < J; ++j) uu[j] = 0.f;
@@ -328,6 +443,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 #pragma unroll
                     for (int j = 0; j < J; ++j) s_part[warp][j] = uu[j];
                 }
+                }
                 __syncthreads();
                 if (tid < J) {
                     float a = 0.f;
@@ -349,7 +465,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const float g = s_gamma[j];
                         if (j < ncols && g != 0.f) {
                             const float2* xc = I.x + (size_t)(col0 + j) * Nt;
-                            float2* mp = m_s + j * Ntp + n;
+                            float2* mp = m_s + j * MS + n;
                             if (n < Nt) {
                                 const float2 u = xc[n];
                                 mp[0].x = fmaf(g, u.x, mp[0].x);
@@ -375,7 +491,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             ++since_refresh;
             __syncthreads();
             // ---------------- periodic drift correction m = H^H q (C64)
-            if (!BF16 && L.refresh > 0 && since_refresh >= L.refresh) {
+            if (!CORR && L.refresh > 0 && since_refresh >= L.refresh) {
                 since_refresh = 0;
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     float2 u0[J], u1[J];
@@ -383,8 +499,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
-                        m_s[j * Ntp + n] = u0[j];
-                        m_s[j * Ntp + n + 1] = u1[j];
+                        m_s[j * MS + n] = u0[j];
+                        m_s[j * MS + n + 1] = u1[j];
                     }
                 }
                 __syncthreads();
@@ -400,32 +516,30 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             }
         }
 
-        // ---- finalise: x = m = H^H q (complex64), true residual with FP64 accumulation
+        // ---- finalise: x = m = H^H q (complex64), true residual with compensated sums
         for (int tile = warp; tile < I.ntiles; tile += NW) {
             float2 u0[J], u1[J];
             tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
             const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
-                m_s[j * Ntp + n] = u0[j];
-                m_s[j * Ntp + n + 1] = u1[j];
+                m_s[j * MS + n] = u0[j];
+                m_s[j * MS + n + 1] = u1[j];
             }
         }
         __syncthreads();
         {
-            double rp[J];
+            float rp[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) rp[j] = 0.0;
+            for (int j = 0; j < J; ++j) rp[j] = 0.f;
             for (int i = warp; i < K; i += NW) {
-                double ar[J], ai[J];
-                row_dot_d<J>(I, rows_s, rptr_s, i, m_s, Ntp, ar, ai);
+                float2 hi[J], lo[J];
+                row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
-                    const float2 qv = q_s[i * J + j];
-                    const double rx = (double)sv.x - ar[j] - (double)xi * qv.x;
-                    const double ry = (double)sv.y - ai[j] - (double)xi * qv.y;
-                    rp[j] += rx * rx + ry * ry;
+                    const float2 r = true_resid(sv, hi[j], lo[j], q_s[i * J + j], xi);
+                    rp[j] += r.x * r.x + r.y * r.y;
                 }
             }
             if (lane == 0) {
@@ -435,7 +549,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         }
         for (int j = 0; j < ncols; ++j) {
             float2* xc = I.x + (size_t)(col0 + j) * Nt;
-            for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * Ntp + n];
+            for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * MS + n];
             if (I.v) {
                 float2* vc = I.v + (size_t)(col0 + j) * K;
                 for (int i = tid; i < K; i += NT) vc[i] = q_s[i * J + j];
@@ -454,44 +568,74 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     }
 }
 
-template <int J, int NW, bool BF16>
+template <int J, int NW, int MODE>
 cudaError_t launch_t(const KzLaunch& L, int grid, size_t smem, cudaStream_t st) {
-    auto k = kz_ahk_kernel<J, NW, BF16>;
+    auto k = kz_ahk_kernel<J, NW, MODE>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     k<<<grid, NW * 32, smem, st>>>(L);
     return cudaGetLastError();
 }
 
-template <int J, int NW, bool BF16>
+template <int J, int NW, int MODE>
 int occ_t(size_t smem) {
-    auto k = kz_ahk_kernel<J, NW, BF16>;
+    auto k = kz_ahk_kernel<J, NW, MODE>;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, NW * 32, smem) != cudaSuccess) return 0;
     return n;
 }
 
-template <int NW, bool BF16>
+template <int NW, int MODE>
 cudaError_t launch_j(const KzLaunch& L, int J, int grid, size_t smem, cudaStream_t st) {
-    switch (J) {
-        case 1: return launch_t<1, NW, BF16>(L, grid, smem, st);
-        case 2: return launch_t<2, NW, BF16>(L, grid, smem, st);
-        case 4: return launch_t<4, NW, BF16>(L, grid, smem, st);
-        case 8: return launch_t<8, NW, BF16>(L, grid, smem, st);
-        default: return cudaErrorInvalidValue;
+    if constexpr (MODE == 2) {
+        switch (J) {
+            case 4: return launch_t<4, NW, MODE>(L, grid, smem, st);
+            case 8: return launch_t<8, NW, MODE>(L, grid, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
+    } else {
+        switch (J) {
+            case 1: return launch_t<1, NW, MODE>(L, grid, smem, st);
+            case 2: return launch_t<2, NW, MODE>(L, grid, smem, st);
+            case 4: return launch_t<4, NW, MODE>(L, grid, smem, st);
+            case 8: return launch_t<8, NW, MODE>(L, grid, smem, st);
+            default: return cudaErrorInvalidValue;
+        }
     }
 }
 
-template <int NW, bool BF16>
+template <int NW, int MODE>
 int occ_j(int J, size_t smem) {
-    switch (J) {
-        case 1: return occ_t<1, NW, BF16>(smem);
-        case 2: return occ_t<2, NW, BF16>(smem);
-        case 4: return occ_t<4, NW, BF16>(smem);
-        case 8: return occ_t<8, NW, BF16>(smem);
-        default: return 0;
+    if constexpr (MODE == 2) {
+        switch (J) {
+            case 4: return occ_t<4, NW, MODE>(smem);
+            case 8: return occ_t<8, NW, MODE>(smem);
+            default: return 0;
+        }
+    } else {
+        switch (J) {
+            case 1: return occ_t<1, NW, MODE>(smem);
+            case 2: return occ_t<2, NW, MODE>(smem);
+            case 4: return occ_t<4, NW, MODE>(smem);
+            case 8: return occ_t<8, NW, MODE>(smem);
+            default: return 0;
+        }
     }
+}
+
+template <int MODE>
+cudaError_t launch_nw(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {
+    if (nw == 8) return launch_j<8, MODE>(L, J, grid, smem, st);
+    if (nw == 16) return launch_j<16, MODE>(L, J, grid, smem, st);
+    return cudaErrorInvalidValue;
+}
+
+template <int MODE>
+int occ_nw(int J, int nw, size_t smem) {
+    if (nw == 8) return occ_j<8, MODE>(J, smem);
+    if (nw == 16) return occ_j<16, MODE>(J, smem);
+    return 0;
 }
 
 }  // namespace
@@ -504,16 +648,19 @@ size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
            r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int));
 }
 
+size_t kz_smem_ahk_tc(int J, int Ntp, int K) {
+    auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
+    return kz_smem_ahk(J, Ntp, K, KZ_C64) - r16((size_t)J * Ntp * sizeof(float2)) +
+           r16((size_t)J * (Ntp + 4) * sizeof(float2)) + r16((size_t)K * sizeof(int));
+}
+
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {
-    const bool bf = (L.prec == KZ_BF16_MIXED);
-    if (nw == 8) return bf ? launch_j<8, true>(L, J, grid, smem, st) : launch_j<8, false>(L, J, grid, smem, st);
-    if (nw == 16) return bf ? launch_j<16, true>(L, J, grid, smem, st) : launch_j<16, false>(L, J, grid, smem, st);
-    return cudaErrorInvalidValue;
+    if (L.tc) return L.prec == KZ_C64 ? launch_nw<2>(L, J, nw, grid, smem, st) : cudaErrorInvalidValue;
+    return L.prec == KZ_BF16_MIXED ? launch_nw<1>(L, J, nw, grid, smem, st) : launch_nw<0>(L, J, nw, grid, smem, st);
 }
 
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec) {
-    const bool bf = (prec == KZ_BF16_MIXED);
-    if (nw == 8) return bf ? occ_j<8, true>(J, smem) : occ_j<8, false>(J, smem);
-    if (nw == 16) return bf ? occ_j<16, true>(J, smem) : occ_j<16, false>(J, smem);
-    return 0;
+    return prec == KZ_BF16_MIXED ? occ_nw<1>(J, nw, smem) : occ_nw<0>(J, nw, smem);
 }
+
+int kz_occupancy_ahk_tc(int J, int nw, size_t smem) { return occ_nw<2>(J, nw, smem); }

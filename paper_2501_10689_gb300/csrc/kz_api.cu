@@ -67,6 +67,7 @@ struct kz_plan {
     int* d_tptr = nullptr;
     int* d_tnv = nullptr;
     int4* d_trow4 = nullptr;
+    int* d_vsort = nullptr;
     float2* d_Hc = nullptr;
     __nv_bfloat162* d_Hb = nullptr;
     float2* d_scratch = nullptr;  // adjoint right-hand side G~ (grown on demand)
@@ -75,7 +76,7 @@ struct kz_plan {
 
     ~kz_plan() {
         void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
-                      d_tptr, d_tnv, d_trow4, d_Hc, d_Hb, d_scratch};
+                      d_tptr, d_tnv, d_trow4, d_vsort, d_Hc, d_Hb, d_scratch};
         for (void* p : ps)
             if (p) cudaFree(p);
     }
@@ -101,6 +102,7 @@ struct kz_plan {
         I.Hb = d_Hb;
         I.nrmd = d_nrmd;
         I.in_off = d_in_off;
+        I.vsort = d_vsort;
         I.cmax = cmax;
         return I;
     }
@@ -198,6 +200,10 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
         B->cs = dual_cs(J, nw, B->K_max, B->cmax);
         B->smem = kz_smem_dual(J, nw, B->cs, B->K_max);
         occ = std::max(1, kz_occupancy_dual(J, nw, B->smem));
+    } else if (kernel == KZ_KERNEL_TC) {
+        B->cs = 0;
+        B->smem = kz_smem_ahk_tc(J, B->Ntp_max, B->K_max);
+        occ = std::max(1, kz_occupancy_ahk_tc(J, nw, B->smem));
     } else {
         B->cs = 0;
         B->smem = smem_for(B->algo, J, B->Ntp_max, B->K_max, B->prec);
@@ -208,6 +214,8 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
 }
 
 bool dual_ok(kz_algo a, kz_prec p) { return is_ahk_family(a) && p == KZ_C64; }
+
+bool tc_ok(kz_algo a, kz_prec p) { return is_ahk_family(a) && p == KZ_C64; }
 
 kz_status check_launch(cudaError_t e, const char* what) {
     if (e != cudaSuccess) {
@@ -318,6 +326,18 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     std::sort(order.begin(), order.end(), by_len);
     std::sort(Vrows.begin(), Vrows.end(), by_len);
     order.insert(order.end(), Vrows.begin(), Vrows.end());
+    // V rows, then all rows, each by the centre of the aligned interval (the
+    // tensor-core residual takes rows in blocks of 8 consecutive entries, whose
+    // union interval is then short)
+    auto by_centre = [&](int x, int y) {
+        const long cx = 2L * rows[x].x + rows[x].y, cy = 2L * rows[y].x + rows[y].y;
+        return cx != cy ? cx < cy : x < y;
+    };
+    std::vector<int> vsort(Vrows), all(K);
+    std::iota(all.begin(), all.end(), 0);
+    std::sort(vsort.begin(), vsort.end(), by_centre);
+    std::sort(all.begin(), all.end(), by_centre);
+    vsort.insert(vsort.end(), all.begin(), all.end());
 
     // X_k: users whose VR overlaps user k's (k included), via a sweep over starts
     std::vector<int> by_start(K);
@@ -378,6 +398,7 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     KZ_TRY(upload(&P->d_tptr, tptr, st));
     KZ_TRY(upload(&P->d_tnv, tnv, st));
     KZ_TRY(upload(&P->d_trow4, trow4, st));
+    KZ_TRY(upload(&P->d_vsort, vsort, st));
     KZ_TRY(cudaMalloc((void**)&P->d_Hc, std::max<int64_t>(acc, 2) * sizeof(float2)));
     if (prec == KZ_BF16_MIXED) KZ_TRY(cudaMalloc((void**)&P->d_Hb, std::max<int64_t>(acc, 2) * sizeof(__nv_bfloat162)));
     KZ_TRY(cudaMalloc((void**)&P->d_nrm, K * sizeof(float)));
@@ -477,12 +498,17 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
             kz_set_error("kz_precode_ex: the dual kernel takes 0, 8 or 16 columns per CTA");
             return KZ_ERR_INVALID_ARG;
         }
+    } else if (kernel == KZ_KERNEL_TC) {
+        if (rhs_per_cta != 0 && rhs_per_cta != 4 && rhs_per_cta != 8) {
+            kz_set_error("kz_precode_ex: the tensor-core kernel takes 0, 4 or 8 columns per CTA");
+            return KZ_ERR_INVALID_ARG;
+        }
     } else if (kernel != KZ_KERNEL_AUTO && kernel != KZ_KERNEL_RESIDENT) {
         kz_set_error("kz_precode_ex: unknown kernel %d", (int)kernel);
         return KZ_ERR_INVALID_ARG;
     }
     kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
-                                    kernel == KZ_KERNEL_DUAL ? 0 : rhs_per_cta, refresh);
+                                    (kernel == KZ_KERNEL_DUAL || kernel == KZ_KERNEL_TC) ? 0 : rhs_per_cta, refresh);
     if (rc != KZ_OK) return rc;
     if (!s || !x || !iters || !resid) {
         kz_set_error("kz_precode: s, x, iters and resid are required");
@@ -502,6 +528,10 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         kz_set_error("kz_precode_ex: the dual kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
     }
+    if (kernel == KZ_KERNEL_TC && !tc_ok(algo, prec)) {
+        kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
+        return KZ_ERR_UNSUPPORTED;
+    }
     int J, nw, cs = 0;
     size_t smem;
     if (kernel == KZ_KERNEL_DUAL) {
@@ -513,6 +543,11 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
             return KZ_ERR_UNSUPPORTED;
         }
         smem = kz_smem_dual(J, nw, cs, plan->K);
+    } else if (kernel == KZ_KERNEL_TC) {
+        J = rhs_per_cta ? rhs_per_cta
+                        : (nrhs >= 8 && kz_smem_ahk_tc(8, plan->Ntp, plan->K) <= kSmemLimit ? 8 : 4);
+        nw = choose_nw(plan->Ntp);
+        smem = kz_smem_ahk_tc(J, plan->Ntp, plan->K);
     } else {
         J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
         nw = choose_nw(plan->Ntp);
@@ -553,6 +588,10 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
     if (kernel == KZ_KERNEL_DUAL) {
         const int occ = std::max(1, kz_occupancy_dual(J, nw, smem));
         e = kz_launch_dual(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
+    } else if (kernel == KZ_KERNEL_TC) {
+        L.tc = 1;
+        const int occ = std::max(1, kz_occupancy_ahk_tc(J, nw, smem));
+        e = kz_launch_ahk(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
     } else {
         const int occ = std::max(1, occupancy_for(algo, J, nw, smem, prec));
         const int grid = std::min(L.n_items, plan->sms * occ);
@@ -709,6 +748,7 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.Ntp_max = B->Ntp_max;
     L.K_max = B->K_max;
     L.cs = B->cs;
+    L.tc = (B->kernel == KZ_KERNEL_TC);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
@@ -752,6 +792,13 @@ kz_status kz_batch_tune(kz_batch* B, kz_select sel, double tol, int32_t max_iter
     if (dual_ok(B->algo, B->prec)) {
         for (Cand c : {Cand{KZ_KERNEL_DUAL, 8, 8}, Cand{KZ_KERNEL_DUAL, 8, 16}, Cand{KZ_KERNEL_DUAL, 16, 16}})
             if (dual_cs(c.J, c.nw, B->K_max, B->cmax) > 0) cands.push_back(c);
+    }
+    if (tc_ok(B->algo, B->prec)) {
+        for (int J : {4, 8}) {
+            if (J == 8 && B->nrhs < 8) continue;
+            if (kz_smem_ahk_tc(J, B->Ntp_max, B->K_max) > kSmemLimit) continue;
+            for (int nw : {8, 16}) cands.push_back({KZ_KERNEL_TC, J, nw});
+        }
     }
     for (const Cand& cd : cands) {
         const int J = cd.J, nw = cd.nw;
@@ -815,6 +862,13 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
         if (!dual_ok(B->algo, B->prec) || dual_cs(rhs_per_cta, nw, B->K_max, B->cmax) == 0) {
             kz_set_error("kz_batch_set_launch: the dual kernel needs AHK / VR_OAHK on C64 with 8 or 16 columns "
                          "that fit shared memory");
+            return KZ_ERR_UNSUPPORTED;
+        }
+    } else if (kernel == KZ_KERNEL_TC) {
+        if (!tc_ok(B->algo, B->prec) || (rhs_per_cta != 4 && rhs_per_cta != 8) ||
+            kz_smem_ahk_tc(rhs_per_cta, B->Ntp_max, B->K_max) > kSmemLimit) {
+            kz_set_error("kz_batch_set_launch: the tensor-core kernel needs AHK / VR_OAHK on C64 with 4 or 8 "
+                         "columns that fit shared memory");
             return KZ_ERR_UNSUPPORTED;
         }
     } else if (kernel == KZ_KERNEL_RESIDENT || kernel == KZ_KERNEL_AUTO) {

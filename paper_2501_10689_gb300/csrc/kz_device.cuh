@@ -150,14 +150,39 @@ __device__ __forceinline__ void row_dot2(const KzInst& I, const int4* rows, cons
     }
 }
 
+// Knuth's TwoSum: s = fl(a + b) and the exact rounding error e (s + e == a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+
+// Compensated warp sum: hi + lo is the sum of the 32 lane values to about
+// twice FP32 precision (each butterfly level adds exactly with TwoSum and
+// carries the error terms in lo).  Partners combine in the same order, so
+// every lane ends with the same hi and lo.
+__device__ __forceinline__ void warp_sum_c(float v, float& hi, float& lo) {
+    float s = v, c = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float so = __shfl_xor_sync(KZ_FULL, s, o), co = __shfl_xor_sync(KZ_FULL, c, o);
+        float e;
+        two_sum(s, so, s, e);
+        c = (c + co) + e;
+    }
+    hi = s;
+    lo = c;
+}
+
 // True-residual variant (complex64 H): each lane sums its share of the row in
 // FP32 (the VR is split over 32 lanes, so a lane adds at most a few dozen
-// products), and the 32 lane sums are combined in FP64.  FP64 arithmetic is
-// kept out of the inner loop, where it would run at the GPU's far lower
-// double-precision rate.
+// products), and the 32 lane sums are combined with compensated FP32
+// additions: hi[j] + lo[j] = h_i . m_j.  No FP64 arithmetic, which runs at a
+// small fraction of the FP32 rate on this GPU.
 template <int J>
-__device__ __forceinline__ void row_dot_d(const KzInst& I, const int4* rows, const int* rptr, int i,
-                                          const float2* __restrict__ m_s, int Ntp, double (&ar)[J], double (&ai)[J]) {
+__device__ __forceinline__ void row_dot_c(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                          const float2* __restrict__ m_s, int Ntp, float2 (&hi)[J],
+                                          float2 (&lo)[J]) {
     float2 acc[J];
     const int lane = threadIdx.x & 31;
     const int4 rd = rows[i];
@@ -183,9 +208,15 @@ __device__ __forceinline__ void row_dot_d(const KzInst& I, const int4* rows, con
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
-        ar[j] = warp_sum_d((double)acc[j].x);
-        ai[j] = warp_sum_d((double)acc[j].y);
+        warp_sum_c(acc[j].x, hi[j].x, lo[j].x);
+        warp_sum_c(acc[j].y, hi[j].y, lo[j].y);
     }
+}
+
+// b - h_i . m - xi q from row_dot_c's hi + lo: b - hi is exact when the two
+// nearly cancel, and xi q enters through one fused multiply-add.
+__device__ __forceinline__ float2 true_resid(float2 b, float2 hi, float2 lo, float2 q, float xi) {
+    return make_float2(fmaf(-xi, q.x, (b.x - hi.x) - lo.x), fmaf(-xi, q.y, (b.y - hi.y) - lo.y));
 }
 
 // m[j][n] += g[j] * conj(H[i, n]) on row i's true VR [o, e) (warp-wide).
@@ -267,6 +298,158 @@ __device__ __forceinline__ void tile_accum(const KzInst& I, const int4* __restri
             }
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core inner products (warp-level mma.sync m16n8k8, TF32 operands,
+// FP32 accumulation).  TF32 keeps the top 10 mantissa bits of each FP32
+// operand (the low bits are ignored), so these products serve the inner
+// iteration of the correction form only: its right-hand side b = s - H m_ref
+// is recomputed from the complex64 H in FP32 at every refresh, and stops are
+// confirmed on that true residual.
+//
+// Fragment ownership (lane = 4 g + c): A (16 x 8, row-major) a0 = (g, c),
+// a1 = (g + 8, c), a2 = (g, c + 4), a3 = (g + 8, c + 4); B (8 x 8) b0 = (c, g),
+// b1 = (c + 4, g); D (16 x 8) d0 = (g, 2c), d1 = (g, 2c + 1), d2 = (g + 8, 2c),
+// d3 = (g + 8, 2c + 1).
+__device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, float a2, float a3, float b0,
+                                         float b1) {
+    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(__float_as_uint(a0)), "r"(__float_as_uint(a1)), "r"(__float_as_uint(a2)), "r"(__float_as_uint(a3)),
+          "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
+}
+
+// Products H m_j for a block of 8 rows, vs[8 b .. 8 b + 8) (fewer at the end
+// of the list, nv entries), over the union of their aligned intervals, four
+// antennas per MMA:
+//   A[(j, re)][(n, re)] = Re m_j(n),  A[(j, re)][(n, im)] = -Im m_j(n),
+//   A[(j, im)][(n, re)] = Im m_j(n),  A[(j, im)][(n, im)] =  Re m_j(n)
+// (row j of the 16 for (j, re), row j + 8 for (j, im); j < J, the rest zero),
+// B[(n, re | im)][row] = Re | Im H[row, n] (zero outside the row's interval),
+// so D[(j, re | im)][row] = Re | Im (H m_j)[row].  The K index of the MMA is
+// ordered (n, re) = c, (n, im) = c + 4 for antenna n = n0 + c, which lets
+// lane (g, c) fetch its A and B values as one complex each.  Lane (g, c)
+// returns column j = g of rows 2c (d[0] + i d[2]) and 2c + 1 (d[1] + i d[3])
+// of the block.  m_s column stride MS (even).
+template <int J>
+__device__ __forceinline__ void tc_row_block(const float2* __restrict__ Hc, const int4* rows, const int* rptr,
+                                             const int* vs, int nv, int b, const float2* __restrict__ m_s, int MS,
+                                             float (&d)[4]) {
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+    const int k = 8 * b + g;
+    int a = 0, len = 0, hb = 0, lo = 0x7fffffff, hi = 0;
+    if (k < nv) {
+        const int row = vs[k];
+        const int4 rd = rows[row];
+        a = rd.x;
+        len = rd.y;
+        hb = rptr[row] - rd.x;
+        lo = rd.x;
+        hi = rd.x + rd.y;
+    }
+#pragma unroll
+    for (int o = 4; o < 32; o <<= 1) {
+        lo = min(lo, __shfl_xor_sync(KZ_FULL, lo, o));
+        hi = max(hi, __shfl_xor_sync(KZ_FULL, hi, o));
+    }
+    float e[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] = 0.f;
+    const bool jok = g < J;
+    const float2* mj = m_s + (jok ? g : 0) * MS;
+    const float2 z = make_float2(0.f, 0.f);
+    int n0 = lo & ~3;
+    // eight chunks per step: all sixteen loads of a lane are issued before the
+    // first MMA of the step (the loop is bound by L2 latency, not MMA rate);
+    // two accumulators keep consecutive MMAs independent
+    constexpr int U = 8;
+    for (; n0 + 4 * (U - 1) < hi; n0 += 4 * U) {
+        float2 h[U], m[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int n = n0 + 4 * u + c;
+            h[u] = ((unsigned)(n - a) < (unsigned)len) ? __ldg(Hc + hb + n) : z;
+            m[u] = jok ? mj[n] : z;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u += 2) {
+            mma_tf32(d, m[u].x, m[u].y, -m[u].y, m[u].x, h[u].x, h[u].y);
+            mma_tf32(e, m[u + 1].x, m[u + 1].y, -m[u + 1].y, m[u + 1].x, h[u + 1].x, h[u + 1].y);
+        }
+    }
+    for (; n0 < hi; n0 += 4) {
+        const int n = n0 + c;
+        const float2 h1 = ((unsigned)(n - a) < (unsigned)len) ? __ldg(Hc + hb + n) : z;
+        const float2 m1 = jok ? mj[n] : z;
+        mma_tf32(d, m1.x, m1.y, -m1.y, m1.x, h1.x, h1.y);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) d[u] += e[u];
+}
+
+// u = H_V^H phi on one 64-antenna tile, antenna-major, eight covering rows
+// (list entries k0..k1 of the tile) per MMA:
+//   A[(n, re)][row] = Re H[row, n],  A[(n, im)][row] = Im H[row, n]
+//   (rows g and g + 8 of the 16 for antenna 64 tile + 8 ab + g),
+//   B[row][(j, re)] = Re phi[row][j], B[row][(j, im)] = Im phi[row][j]
+//   (columns 4 nb .. 4 nb + 3 per block nb of the 8 N entries),
+// so acc[ab][nb] holds the four real products whose sums and differences
+// give u (tc_u_combine).  coef: K x J phi in shared memory.
+template <int J>
+__device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, const int4* __restrict__ trow4, int tile,
+                                             int k0, int k1, const float2* __restrict__ coef,
+                                             float (&acc)[8][J / 4][4]) {
+    constexpr int NB = J / 4;
+    const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
+#pragma unroll
+    for (int ab = 0; ab < 8; ++ab)
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[ab][nb][u] = 0.f;
+    const int4 none = make_int4(0, 0, 0, 0);  // empty interval: never matches
+    const float2 z = make_float2(0.f, 0.f);
+    const int nb0 = tile * KZ_TILE + g;
+    int4 na = (k0 + c < k1) ? __ldg(trow4 + k0 + c) : none;
+    int4 nbx = (k0 + c + 4 < k1) ? __ldg(trow4 + k0 + c + 4) : none;
+    for (int k = k0; k < k1; k += 8) {
+        const bool va = k + c < k1, vb = k + c + 4 < k1;
+        const int4 ea = na, eb = nbx;
+        // descriptors of the next eight rows, in flight while these are used
+        na = (k + 8 + c < k1) ? __ldg(trow4 + k + 8 + c) : none;
+        nbx = (k + 12 + c < k1) ? __ldg(trow4 + k + 12 + c) : none;
+        float b0[NB], b1[NB];
+#pragma unroll
+        for (int nb = 0; nb < NB; ++nb) {
+            const int j = 4 * nb + (g & 3);
+            const float2 pa = va ? coef[ea.x * J + j] : z;
+            const float2 pb = vb ? coef[eb.x * J + j] : z;
+            b0[nb] = (g >> 2) ? pa.y : pa.x;
+            b1[nb] = (g >> 2) ? pb.y : pb.x;
+        }
+#pragma unroll
+        for (int ab = 0; ab < 8; ++ab) {
+            const int n = nb0 + 8 * ab;
+            const float2 ha = (n >= ea.z && n < ea.w) ? __ldg(Hc + ea.y + n) : z;
+            const float2 hb = (n >= eb.z && n < eb.w) ? __ldg(Hc + eb.y + n) : z;
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) mma_tf32(acc[ab][nb], ha.x, ha.y, hb.x, hb.y, b0[nb], b1[nb]);
+        }
+    }
+}
+
+// Sums and differences of tc_tile_aggr's products (all lanes take part):
+// lanes c < 2 return u at antenna 64 tile + 8 ab + g for columns
+// j = 4 nb + 2c (u0) and j + 1 (u1).  With the partner lane c + 2 (which
+// holds the Im phi products):  Re u = Re H Re phi + Im H Im phi,
+// Im u = Re H Im phi - Im H Re phi.
+__device__ __forceinline__ void tc_u_combine(const float (&a)[4], float2& u0, float2& u1) {
+    const float e0 = __shfl_xor_sync(KZ_FULL, a[0], 2), e1 = __shfl_xor_sync(KZ_FULL, a[1], 2);
+    const float e2 = __shfl_xor_sync(KZ_FULL, a[2], 2), e3 = __shfl_xor_sync(KZ_FULL, a[3], 2);
+    u0 = make_float2(a[0] + e2, e0 - a[2]);
+    u1 = make_float2(a[1] + e3, e1 - a[3]);
 }
 
 // ---------------------------------------------------------------------------

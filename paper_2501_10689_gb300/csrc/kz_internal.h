@@ -31,7 +31,7 @@ struct KzInst {
     const int4* rows;          // {a, len2, o, e} per row
     const int* rptr;           // aligned complex offset of each row
     const float* nrm;          // ||h_k||^2 (rounded from an FP64 sum)
-    const int* order;          // F rows (ascending) then V rows (ascending)
+    const int* order;          // F rows then V rows, each by decreasing VR length
     const int* xptr;           // CSR of X_k (k included)
     const int* xidx;
     const int* tptr;           // CSR of covering rows per tile
@@ -41,6 +41,7 @@ struct KzInst {
     const __nv_bfloat162* Hb;  // aligned BF16 (re, im) rows, or nullptr
     const double* nrmd;        // ||h_k||^2 in FP64
     const int* in_off;         // row k's offset in the caller's packed layout
+    const int* vsort;          // V rows (K - nF), then all K rows, each by VR centre
     int cmax;                  // most rows covering one tile
     // --- call ---
     float xi;
@@ -66,6 +67,7 @@ struct KzLaunch {
     int* status;
     int Ntp_max, K_max;
     int cs;               // dual kernel: staged rows per chunk
+    int tc;               // resident kernel: tensor-core inner products (correction form)
 };
 
 // Host-side launchers (kz_ahk.cu / kz_kacz.cu).
@@ -74,6 +76,8 @@ cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t sm
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
+size_t kz_smem_ahk_tc(int J, int Ntp, int K);
+int kz_occupancy_ahk_tc(int J, int nw, size_t smem);
 int kz_occupancy_kacz(int J, int nw, size_t smem);
 cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
 size_t kz_smem_dual(int J, int nw, int CS, int K);

@@ -171,7 +171,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             }
             __syncthreads();
             // ---------------- confirmation: m = H^H q, every residual recomputed
-            // with FP64 accumulation, then the test again on those residuals
+            // with compensated FP32 sums, then the test again on those residuals
             if (s_pending) {
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     float2 u0[J], u1[J];
@@ -185,15 +185,12 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                 }
                 __syncthreads();
                 for (int i = warp; i < K; i += NW) {
-                    double ar[J], ai[J];
-                    row_dot_d<J>(I, I.rows, I.rptr, i, m_s, Ntp, ar, ai);
+                    float2 hi[J], lo[J];
+                    row_dot_c<J>(I, I.rows, I.rptr, i, m_s, Ntp, hi, lo);
                     if (lane == 0) {
 #pragma unroll
-                        for (int j = 0; j < J; ++j) {
-                            const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
-                            r_s[i * J + j] = make_float2((float)((double)bv.x - ar[j] - (double)xi * qv.x),
-                                                         (float)((double)bv.y - ai[j] - (double)xi * qv.y));
-                        }
+                        for (int j = 0; j < J; ++j)
+                            r_s[i * J + j] = true_resid(b_s[i * J + j], hi[j], lo[j], q_s[i * J + j], xi);
                     }
                 }
                 since_refresh = 0;
@@ -329,7 +326,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             }
         }
 
-        // ---- finalise: x = H^H q, true residual with FP64 accumulation
+        // ---- finalise: x = H^H q, true residual with compensated FP32 sums
         for (int tile = warp; tile < I.ntiles; tile += NW) {
             float2 u0[J], u1[J];
             tile_accum<J, false>(I, trow4, tile, I.tptr[tile], I.tptr[tile + 1], q_s, u0, u1);
@@ -342,19 +339,16 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
         }
         __syncthreads();
         {
-            double rp[J];
+            float rp[J];
 #pragma unroll
-            for (int j = 0; j < J; ++j) rp[j] = 0.0;
+            for (int j = 0; j < J; ++j) rp[j] = 0.f;
             for (int i = warp; i < K; i += NW) {
-                double ar[J], ai[J];
-                row_dot_d<J>(I, I.rows, I.rptr, i, m_s, Ntp, ar, ai);
+                float2 hi[J], lo[J];
+                row_dot_c<J>(I, I.rows, I.rptr, i, m_s, Ntp, hi, lo);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
-                    const float2 sv = b_s[i * J + j];
-                    const float2 qv = q_s[i * J + j];
-                    const double rx = (double)sv.x - ar[j] - (double)xi * qv.x;
-                    const double ry = (double)sv.y - ai[j] - (double)xi * qv.y;
-                    rp[j] += rx * rx + ry * ry;
+                    const float2 r = true_resid(b_s[i * J + j], hi[j], lo[j], q_s[i * J + j], xi);
+                    rp[j] += r.x * r.x + r.y * r.y;
                 }
             }
             if (lane == 0) {

@@ -50,7 +50,7 @@ EXPORTS = ("kz_plan_create", "kz_plan_update", "kz_plan_destroy", "kz_plan_query
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_last_error", "kz_version")
-KERNELS = {"auto": 0, "resident": 1, "dual": 2}
+KERNELS = {"auto": 0, "resident": 1, "dual": 2, "tc": 3}
 
 
 def library_path() -> str:

@@ -1,0 +1,157 @@
+"""The tensor-core (TF32 correction form) AHK / VR-OAHK kernel against the FP64 oracle (GB300)."""
+import numpy as np
+import pytest
+
+import kzgen
+from oracle import kaczmarz as okz
+from oracle import rzf as orz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kp():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_10689_gb300 import kzprecode
+    return kzprecode
+
+
+def run(kp, inst, algo, tol=1e-7, max_iter=3000, J=0, S=None, kernel="tc", refresh=0):
+    plan = kp.plan_from_instance(inst)
+    S = inst.S if S is None else S
+    out = kp.precode(plan, kp.rhs_tensor(S), inst.xi, algo=algo, tol=tol, max_iter=max_iter, rhs_per_cta=J,
+                     kernel=kernel, refresh=refresh)
+    return {"x": out["x"].cpu().numpy().T.astype(np.complex128), "v": out["v"].cpu().numpy().T.astype(np.complex128),
+            "iters": out["iters"].cpu().numpy(), "resid": out["resid"].cpu().numpy(), "converged": out["converged"]}
+
+
+def ragged(seed=5, K=13, Nt=333, lo=17, hi=121, nrhs=11):
+    return kzgen.make_instance(seed, K, Nt, vr_len_range=(lo, hi), snr_db=10.0, nrhs=nrhs)
+
+
+@pytest.mark.parametrize("algo", ["ahk", "vr_oahk"])
+@pytest.mark.parametrize("J,nrhs", [(4, 11), (8, 11), (8, 3), (4, 1)])
+def test_tc_converges_to_rzf(kp, algo, J, nrhs):
+    inst = ragged(nrhs=nrhs)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    out = run(kp, inst, algo, J=J)
+    assert out["converged"]
+    assert np.all(orz.rel_err(out["x"], X) <= TOL_X)
+    assert np.all(orz.rel_err(out["v"], V) <= TOL_X)
+    assert np.all(out["resid"] <= 1e-7 * (1 + 1e-6))
+
+
+@pytest.mark.parametrize("algo", ["ahk", "vr_oahk"])
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_tc_first_iterates_follow_the_oracle(kp, algo, T):
+    """Before any refresh the tensor-core iterates are the oracle's up to TF32
+    rounding: a wrong fragment layout would miss by O(1)."""
+    inst = ragged(seed=3, nrhs=9)
+    ref = okz.solve(okz.System.from_instance(inst), inst.S, algo, tol=0.0, max_iter=T)
+    for J in (4, 8):
+        out = run(kp, inst, algo, tol=0.0, max_iter=T, J=J, refresh=1000)
+        assert np.all(out["iters"] == T) and not out["converged"]
+        assert np.all(orz.rel_err(out["x"], ref["x"]) <= 5e-3), (J, np.max(orz.rel_err(out["x"], ref["x"])))
+        assert np.all(orz.rel_err(out["v"], ref["v"]) <= 5e-3)
+
+
+def test_tc_matches_resident_kernel(kp):
+    inst = kzgen.config2(10.0, nrhs=32)
+    a = run(kp, inst, "vr_oahk", tol=1e-6, kernel="tc")
+    b = run(kp, inst, "vr_oahk", tol=1e-6, kernel="resident")
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    assert np.max(orz.rel_err(a["x"], X)) <= TOL_X
+    assert np.all(orz.rel_err(a["x"], b["x"]) <= 4e-6)
+    # refreshes every 16 iterations: the count may move by a few
+    assert np.mean(a["iters"]) <= 1.1 * np.mean(b["iters"]) + 2
+
+
+@pytest.mark.parametrize("snr", [0.0, 20.0])
+def test_tc_config2_full(kp, snr):
+    inst = kzgen.config2(snr)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    out = run(kp, inst, "vr_oahk", tol=1e-6, max_iter=2000)
+    assert out["converged"] and np.max(orz.rel_err(out["x"], X)) <= TOL_X
+
+
+def test_tc_edge_cases(kp):
+    inst = kzgen.make_instance(7, 1, 64, vr_len_range=(20, 20), nrhs=8)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    assert np.all(orz.rel_err(run(kp, inst, "vr_oahk")["x"], X) <= TOL_X)
+    assert np.all(orz.rel_err(run(kp, inst, "ahk")["x"], X) <= TOL_X)
+    off = [1 + 13 * k for k in range(6)]
+    inst = kzgen.make_instance(8, 6, 80, vr_override=(off, [11] * 6), nrhs=8)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    out = run(kp, inst, "vr_oahk")
+    assert np.all(out["iters"] == 1) and np.all(orz.rel_err(out["x"], X) <= 1e-6)
+    inst = ragged(seed=10, nrhs=8)
+    S = inst.S.copy()
+    S[:, 2] = 0
+    out = run(kp, inst, "vr_oahk", S=S)
+    assert out["iters"][2] == 0 and np.all(out["x"][:, 2] == 0)
+    # VRs that reach the last antenna and start at antenna 0, odd Nt
+    off = [0, 300, 150, 0, 200]
+    ln = [333, 33, 100, 7, 133]
+    inst = kzgen.make_instance(9, 5, 333, vr_override=(off, ln), nrhs=5)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    assert np.all(orz.rel_err(run(kp, inst, "vr_oahk", J=4)["x"], X) <= TOL_X)
+
+
+def test_tc_batched_and_graph(kp):
+    rng = np.random.default_rng(5)
+    insts = []
+    for i in range(7):
+        Nt = int(rng.choice([96, 257, 640]))
+        insts.append(kzgen.make_instance(500 + i, int(rng.integers(3, 40)), Nt, vr_frac_range=(0.1, 0.4), nrhs=16))
+    items = []
+    for inst in insts:
+        p = kp.plan_from_instance(inst)
+        items.append(dict(plan=p, s=kp.rhs_tensor(inst.S),
+                          x=torch.empty((16, inst.Nt), dtype=torch.complex64, device="cuda"),
+                          v=None, iters=torch.empty(16, dtype=torch.int32, device="cuda"),
+                          resid=torch.empty(16, dtype=torch.float64, device="cuda"), xi=inst.xi))
+    b = kp.kz_batch_prepare(items, 16, "vr_oahk")
+    for J, threads in ((4, 256), (4, 512), (8, 512)):
+        kp.kz_batch_set_launch(b, "tc", J, threads)
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(s):
+            kp.kz_precode_batched(b, "paper", 1e-6, 50000, 0, status=st)
+        torch.cuda.synchronize()
+        with torch.cuda.graph(g, stream=s):
+            kp.kz_precode_batched(b, "paper", 1e-6, 50000, 0, status=st)
+        for it in items:
+            it["x"].zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert st.item() == 0
+        for inst, it in zip(insts, items):
+            V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+            assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X), (J, threads)
+
+
+def test_tc_deterministic(kp):
+    inst = ragged(seed=12, K=40, Nt=700, lo=60, hi=300, nrhs=8)
+    a = run(kp, inst, "vr_oahk", tol=1e-6)
+    b = run(kp, inst, "vr_oahk", tol=1e-6)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["iters"], b["iters"])
+
+
+def test_tc_rejects_unsupported(kp):
+    inst = ragged(nrhs=4)
+    plan = kp.plan_from_instance(inst)
+    S = kp.rhs_tensor(inst.S)
+    with pytest.raises(kp.KzError):
+        kp.precode(plan, S, inst.xi, algo="grk", kernel="tc")
+    with pytest.raises(kp.KzError):
+        kp.precode(plan, S, inst.xi, algo="vr_oahk", kernel="tc", rhs_per_cta=2)
+    bplan = kp.plan_from_instance(inst, prec="bf16")
+    with pytest.raises(kp.KzError):
+        kp.precode(bplan, S, inst.xi, algo="vr_oahk", kernel="tc")
