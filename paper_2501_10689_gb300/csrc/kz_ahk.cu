@@ -66,7 +66,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     };
     // iterate columns; the tensor-core mode pads each by 4 entries so the 8
     // columns read by one MMA fragment fall in different banks
-    float2* m_s = reinterpret_cast<float2*>(carve((size_t)J * (L.Ntp_max + (TC ? 4 : 0)) * sizeof(float2)));
+    float2* m_s = reinterpret_cast<float2*>(
+        carve((L.m_elems ? (size_t)L.m_elems : (size_t)J * (L.Ntp_max + (TC ? 4 : 0))) * sizeof(float2)));
     float2* b_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* q_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* p_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
@@ -80,6 +81,16 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     int* tptr_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE + 1) * sizeof(int)));
     int* tnv_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE) * sizeof(int)));
     int* vs_s = TC ? reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int))) : nullptr;
+    // tensor-core V residual: every 8-row block's union interval is cut in
+    // two parts (tasks); part 0 sums into p_s, part 1 into pb_s, and the two
+    // are added in that order.  Tasks are dealt to warps largest first, each
+    // to the least loaded warp (fixed per item, so results are reproducible).
+    const int ntask_max = TC ? 2 * ((L.K_max + 7) / 8) : 0;
+    float2* pb_s = TC ? reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2))) : nullptr;
+    int4* task_s = TC ? reinterpret_cast<int4*>(carve((size_t)ntask_max * sizeof(int4))) : nullptr;
+    int* tcost_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
+    int* wlist_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
+    __shared__ int s_wptr[NW + 1];
     const float tol2 = (float)(L.tol * L.tol);
     const bool oahk = (L.algo == ALGO_OAHK);
 
@@ -102,12 +113,15 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         const KzInst& I = sI;
         const int K = I.K, Nt = I.Nt, Ntp = I.Ntp, nF = oahk ? I.nF : 0;
         const int MS = TC ? Ntp + 4 : Ntp;  // column stride of m_s
-        const int col0 = it.y, ncols = min(J, I.ld - col0);
+        // an item may be narrower than J (W columns): a wide channel whose J
+        // iterate columns would not fit shared memory
+        const int W = KZ_ITEM_WIDTH(it.y, J);
+        const int col0 = KZ_ITEM_COL(it.y), ncols = min(W, I.ld - col0);
         const float xi = I.xi;
         const int4* trow4 = I.trow4;
 
         // ---- initialise: m = 0, q = 0, b = s, d = ||h||^2 + xi
-        for (int e = tid; e < J * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
+        for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
         for (int e = tid; e < K * J; e += NT) {
             const int i = e / J, j = e % J;
             b_s[e] = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -131,6 +145,48 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             for (int v = tid; v < K - nF; v += NT) vs_s[v] = src[v];
         }
         __syncthreads();
+        if (TC) {
+            const int nv = K - nF, nblk = (nv + 7) >> 3;
+            for (int b = tid; b < nblk; b += NT) {
+                int lo = 0x7fffffff, hi = 0;
+                for (int r = 8 * b; r < min(8 * b + 8, nv); ++r) {
+                    const int4 rd = rows_s[vs_s[r]];
+                    lo = min(lo, rd.x);
+                    hi = max(hi, rd.x + rd.y);
+                }
+                const int lo8 = lo & ~7;
+                const int steps = (hi - lo8 + 63) >> 6;  // steps of 64 antennas
+                const int cut = lo8 + 64 * ((steps + 1) >> 1);
+                task_s[2 * b] = make_int4(lo8, min(cut, hi), b, 0);
+                task_s[2 * b + 1] = make_int4(cut, max(cut, hi), b, 1);
+                tcost_s[2 * b] = (steps + 1) >> 1;
+                tcost_s[2 * b + 1] = steps >> 1;
+            }
+            __syncthreads();
+            if (tid == 0) {  // greedy longest-first assignment to warps
+                const int nt = 2 * nblk;
+                int load[NW], cnt[NW];
+                for (int w = 0; w < NW; ++w) load[w] = cnt[w] = 0;
+                for (int q = 0; q < nt; ++q) {
+                    int best = -1;
+                    for (int t2 = 0; t2 < nt; ++t2) {  // next task: largest cost, then lowest index
+                        if (tcost_s[t2] < 0) continue;
+                        if (best < 0 || tcost_s[t2] > tcost_s[best]) best = t2;
+                    }
+                    int w0 = 0;
+                    for (int w = 1; w < NW; ++w)
+                        if (load[w] < load[w0]) w0 = w;
+                    load[w0] += tcost_s[best];
+                    tcost_s[best] = -1 - w0;  // taken, by warp w0
+                    ++cnt[w0];
+                }
+                s_wptr[0] = 0;
+                for (int w = 0; w < NW; ++w) s_wptr[w + 1] = s_wptr[w] + cnt[w];
+                for (int w = 0; w < NW; ++w) cnt[w] = s_wptr[w];
+                for (int t2 = 0; t2 < nt; ++t2) wlist_s[cnt[-1 - tcost_s[t2]]++] = t2;
+            }
+            __syncthreads();
+        }
         if (warp < J) {
             double a = 0.0;
             for (int i = lane; i < K; i += 32) {
@@ -164,7 +220,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 for (int f = warp; f < nF; f += NW) {
                     const int i = order_s[f];
                     float2 acc[J];
-                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, acc);
+                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, acc, W);
                     float2 g[J];
                     const float di = d_s[i];
 #pragma unroll
@@ -175,7 +231,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const bool on = (act >> j) & 1;
                         g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
                     }
-                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, g, lane, 32);
+                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, g, lane, 32, W);
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -192,45 +248,54 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 #pragma unroll
             for (int j = 0; j < J; ++j) pr[j] = pn[j] = pp[j] = 0.f;
             if constexpr (TC) {
-                // 8-row blocks on the tensor cores; lane (g, c) finishes column
-                // g of rows 2c and 2c + 1 of each block
-                const int g = lane >> 2, c = lane & 3;
-                float spr = 0.f, spn = 0.f, spp = 0.f;
-                const int nblk = (vcount + 7) >> 3;
-                for (int blk = warp; blk < nblk; blk += NW) {
-                    float d[4];
-                    tc_row_block<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, blk, m_s, MS, d);
-                    if (g < J) {
-                        const bool on = (act >> g) & 1;
-#pragma unroll
-                        for (int rr = 0; rr < 2; ++rr) {
-                            const int k = 8 * blk + 2 * c + rr;
-                            if (k < vcount) {
-                                const int i = vs_s[k];
-                                const float2 bv = b_s[i * J + g], qv = q_s[i * J + g];
-                                const float rx = bv.x - (rr ? d[1] : d[0]) - xi * qv.x;
-                                const float ry = bv.y - (rr ? d[3] : d[2]) - xi * qv.y;
-                                const float r2 = rx * rx + ry * ry;
-                                const float di = dinv_s[i];
-                                const float2 ph = on ? make_float2(rx * di, ry * di) : make_float2(0.f, 0.f);
-                                spr += r2;
-                                spn += on ? r2 * di : 0.f;
-                                spp += ph.x * ph.x + ph.y * ph.y;
-                                p_s[i * J + g] = ph;
-                            }
+                // 8-row blocks on the tensor cores, each in two parts
+                {
+                    const int g = lane >> 2, c = lane & 3;
+                    for (int q = s_wptr[warp]; q < s_wptr[warp + 1]; ++q) {
+                        const int4 tk = task_s[wlist_s[q]];
+                        float d[4];
+                        tc_row_part<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, tk.z, tk.x, tk.y, m_s, MS, W, d);
+                        float2* dst = tk.w ? pb_s : p_s;
+                        const int k = 8 * tk.z + 2 * c;
+                        if (g < W) {
+                            if (k < vcount) dst[vs_s[k] * J + g] = make_float2(d[0], d[2]);
+                            if (k + 1 < vcount) dst[vs_s[k + 1] * J + g] = make_float2(d[1], d[3]);
                         }
                     }
                 }
+                __syncthreads();
+                // residuals, phi and the column sums; thread tid always has
+                // column j = tid % J (J divides the block size)
+                float spr = 0.f, spn = 0.f, spp = 0.f;
+                const int j = tid % J;
+                const bool on = (act >> j) & 1;
+                for (int e = tid; e < vcount * J; e += NT) {
+                    const int i = vs_s[e / J];
+                    float2 ph = make_float2(0.f, 0.f);
+                    if (j < W) {
+                        const float2 p0 = p_s[i * J + j], p1 = pb_s[i * J + j];
+                        const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                        const float rx = bv.x - (p0.x + p1.x) - xi * qv.x;
+                        const float ry = bv.y - (p0.y + p1.y) - xi * qv.y;
+                        const float r2 = rx * rx + ry * ry;
+                        const float di = dinv_s[i];
+                        ph = on ? make_float2(rx * di, ry * di) : make_float2(0.f, 0.f);
+                        spr += r2;
+                        spn += on ? r2 * di : 0.f;
+                        spp += ph.x * ph.x + ph.y * ph.y;
+                    }
+                    p_s[i * J + j] = ph;
+                }
 #pragma unroll
-                for (int o = 1; o < 4; o <<= 1) {
+                for (int o = J; o < 32; o <<= 1) {
                     spr += __shfl_xor_sync(KZ_FULL, spr, o);
                     spn += __shfl_xor_sync(KZ_FULL, spn, o);
                     spp += __shfl_xor_sync(KZ_FULL, spp, o);
                 }
-                if (c == 0 && g < J) {
-                    s_part[warp][g] = spr;
-                    s_part[warp][J + g] = spn;
-                    s_part[warp][2 * J + g] = spp;
+                if (lane < J) {
+                    s_part[warp][lane] = spr;
+                    s_part[warp][J + lane] = spn;
+                    s_part[warp][2 * J + lane] = spp;
                 }
             } else {
             // rows v and v + NW go to the same warp together (two loads streams)
@@ -316,6 +381,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
+                        if (j >= W) continue;
                         m_s[j * MS + n] = u0[j];
                         m_s[j * MS + n + 1] = u1[j];
                     }
@@ -326,7 +392,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 for (int j = 0; j < J; ++j) rp[j] = 0.f;
                 for (int i = warp; i < K; i += NW) {
                     float2 hi[J], lo[J];
-                    row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo);
+                    row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo, W);
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -364,7 +430,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     s_pending = 0;
                 }
                 if (CORR)
-                    for (int e = tid; e < J * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
+                    for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
                 __syncthreads();
             }
             if (!s_active) break;
@@ -379,27 +445,32 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     float uu[2 * NB];
 #pragma unroll
                     for (int j = 0; j < 2 * NB; ++j) uu[j] = 0.f;
-                    for (int tile = warp; tile < I.ntiles; tile += NW) {
+                    // tasks: tile halves (32 antennas each)
+                    for (int task = warp; task < 2 * I.ntiles; task += NW) {
+                        const int tile = task >> 1, part = task & 1;
                         const int k0 = tptr_s[tile];
                         const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                         if (k0 == k1) continue;
-                        float acc[8][NB][4];
-                        tc_tile_aggr<J>(I.Hc, trow4, tile, k0, k1, p_s, acc);
+                        float acc[2][2][NB][4];
+                        tc_tile_aggr<J>(I.Hc, trow4, tile, part, k0, k1, p_s, acc);
+                        // lane (g, c < 2) holds u at the antenna pair (n, n + 1)
+                        // for columns j and j + 1: one 16-byte store per column
 #pragma unroll
-                        for (int ab = 0; ab < 8; ++ab) {
-                            const int n = tile * KZ_TILE + 8 * ab + g;
+                        for (int sp = 0; sp < 2; ++sp) {
+                            const int n = tile * KZ_TILE + 32 * part + 16 * sp + 2 * g;
 #pragma unroll
                             for (int nb = 0; nb < NB; ++nb) {
-                                float2 u0, u1;
-                                tc_u_combine(acc[ab][nb], u0, u1);
+                                float2 u0e, u1e, u0o, u1o;
+                                tc_u_combine(acc[sp][0][nb], u0e, u1e);
+                                tc_u_combine(acc[sp][1][nb], u0o, u1o);
                                 const int j = 4 * nb + 2 * c;
                                 if (c < 2) {
                                     if (n < Nt) {
-                                        if (j < ncols) I.x[(size_t)(col0 + j) * Nt + n] = u0;
-                                        if (j + 1 < ncols) I.x[(size_t)(col0 + j + 1) * Nt + n] = u1;
+                                        kz_store_pair(I.x, Nt, col0 + j, n, j < ncols, u0e, u0o);
+                                        kz_store_pair(I.x, Nt, col0 + j + 1, n, j + 1 < ncols, u1e, u1o);
                                     }
-                                    uu[2 * nb] += u0.x * u0.x + u0.y * u0.y;
-                                    uu[2 * nb + 1] += u1.x * u1.x + u1.y * u1.y;
+                                    uu[2 * nb] += u0e.x * u0e.x + u0e.y * u0e.y + u0o.x * u0o.x + u0o.y * u0o.y;
+                                    uu[2 * nb + 1] += u1e.x * u1e.x + u1e.y * u1e.y + u1o.x * u1o.x + u1o.y * u1o.y;
                                 }
                             }
                         }
@@ -499,6 +570,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
+                        if (j >= W) continue;
                         m_s[j * MS + n] = u0[j];
                         m_s[j * MS + n + 1] = u1[j];
                     }
@@ -523,6 +595,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
+                if (j >= W) continue;
                 m_s[j * MS + n] = u0[j];
                 m_s[j * MS + n + 1] = u1[j];
             }
@@ -534,7 +607,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             for (int j = 0; j < J; ++j) rp[j] = 0.f;
             for (int i = warp; i < K; i += NW) {
                 float2 hi[J], lo[J];
-                row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo);
+                row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo, W);
 #pragma unroll
                 for (int j = 0; j < J; ++j) {
                     const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -648,10 +721,12 @@ size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
            r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int));
 }
 
-size_t kz_smem_ahk_tc(int J, int Ntp, int K) {
+size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K) {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
-    return kz_smem_ahk(J, Ntp, K, KZ_C64) - r16((size_t)J * Ntp * sizeof(float2)) +
-           r16((size_t)J * (Ntp + 4) * sizeof(float2)) + r16((size_t)K * sizeof(int));
+    const size_t ntask = 2 * (size_t)((K + 7) / 8);
+    return kz_smem_ahk(J, Ntp_max, K, KZ_C64) - r16((size_t)J * Ntp_max * sizeof(float2)) +
+           r16((size_t)m_elems * sizeof(float2)) + r16((size_t)K * sizeof(int)) +
+           r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int));
 }
 
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {

@@ -111,6 +111,8 @@ struct kz_plan {
 struct kz_batch {
     int n = 0, nrhs = 0, J = 1, nw = 16, grid = 1, n_items = 0, Ntp_max = 0, K_max = 0;
     int kernel = KZ_KERNEL_RESIDENT, cs = 0, cmax = 0;
+    int m_elems = 0;               // tensor-core kernel: shared iterate entries per CTA
+    std::vector<int> Ntp_of;       // per instance
     std::vector<double> cost;  // per-instance work estimate (aligned entries + 4 Nt)
     size_t smem = 0;
     kz_algo algo = KZ_VR_OAHK;
@@ -136,8 +138,11 @@ bool is_ahk_family(kz_algo a) { return a == KZ_AHK || a == KZ_VR_OAHK; }
 
 bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_VR_OAHK; }
 
-int default_refresh(kz_algo a, kz_prec p) {
-    if (is_ahk_family(a)) return p == KZ_BF16_MIXED ? 6 : 16;
+// Refresh period: the drift correction of C64, the correction-form refresh
+// of BF16_MIXED and of the tensor-core kernel (whose TF32 inner products
+// slow the iteration when the correction grows for longer).
+int default_refresh(kz_algo a, kz_prec p, bool tc = false) {
+    if (is_ahk_family(a)) return tc ? 12 : (p == KZ_BF16_MIXED ? 6 : 16);
     return 512;
 }
 
@@ -180,10 +185,27 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
 cudaError_t batch_layout(kz_batch* B, int J, int nw, int sms, cudaStream_t st) {
     return batch_layout_k(B, KZ_KERNEL_RESIDENT, J, nw, sms, st);
 }
+// Tensor-core kernel: the width (columns) of instance b's items, the largest
+// of J, J / 2, ... (at least 4) whose iterate columns fit shared memory next to
+// the widest other instance's; 0 if even 4 do not fit.
+int tc_width(int J, int Ntp, int Ntp_max, int K_max) {
+    for (int W = J; W >= 4; W /= 2)
+        if (kz_smem_ahk_tc(J, W * (Ntp + 4), Ntp_max, K_max) <= kSmemLimit) return W;
+    return 0;
+}
+
 cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cudaStream_t st) {
     std::vector<std::pair<double, int2>> work;
-    for (int b = 0; b < B->n; ++b)
-        for (int c = 0; c < B->nrhs; c += J) work.push_back({B->cost[b], make_int2(b, c)});
+    int m_elems = 0;
+    for (int b = 0; b < B->n; ++b) {
+        int W = J;
+        if (kernel == KZ_KERNEL_TC) {
+            W = tc_width(J, B->Ntp_of[b], B->Ntp_max, B->K_max);
+            if (W == 0) return cudaErrorInvalidValue;
+            m_elems = std::max(m_elems, W * (B->Ntp_of[b] + 4));
+        }
+        for (int c = 0; c < B->nrhs; c += W) work.push_back({B->cost[b] * W, make_int2(b, c | (W << 24))});
+    }
     std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
     std::vector<int2> witems(work.size());
     for (size_t w = 0; w < work.size(); ++w) witems[w] = work[w].second;
@@ -202,7 +224,8 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
         occ = std::max(1, kz_occupancy_dual(J, nw, B->smem));
     } else if (kernel == KZ_KERNEL_TC) {
         B->cs = 0;
-        B->smem = kz_smem_ahk_tc(J, B->Ntp_max, B->K_max);
+        B->m_elems = m_elems;
+        B->smem = kz_smem_ahk_tc(J, m_elems, B->Ntp_max, B->K_max);
         occ = std::max(1, kz_occupancy_ahk_tc(J, nw, B->smem));
     } else {
         B->cs = 0;
@@ -545,9 +568,10 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         smem = kz_smem_dual(J, nw, cs, plan->K);
     } else if (kernel == KZ_KERNEL_TC) {
         J = rhs_per_cta ? rhs_per_cta
-                        : (nrhs >= 8 && kz_smem_ahk_tc(8, plan->Ntp, plan->K) <= kSmemLimit ? 8 : 4);
+                        : (nrhs >= 8 && kz_smem_ahk_tc(8, 8 * (plan->Ntp + 4), plan->Ntp, plan->K) <= kSmemLimit ? 8
+                                                                                                           : 4);
         nw = choose_nw(plan->Ntp);
-        smem = kz_smem_ahk_tc(J, plan->Ntp, plan->K);
+        smem = kz_smem_ahk_tc(J, J * (plan->Ntp + 4), plan->Ntp, plan->K);
     } else {
         J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
         nw = choose_nw(plan->Ntp);
@@ -577,7 +601,7 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
     L.prec = prec;
     L.tol = tol;
     L.max_iter = max_iter;
-    L.refresh = refresh ? refresh : default_refresh(algo, prec);
+    L.refresh = refresh ? refresh : default_refresh(algo, prec, kernel == KZ_KERNEL_TC);
     L.seed = seed;
     L.status = status;
     L.Ntp_max = plan->Ntp;
@@ -627,6 +651,11 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
             kz_set_error("kz_batch_prepare: item %d is missing a plan, buffer or positive xi", b);
             return KZ_ERR_INVALID_ARG;
         }
+        if (!aligned(it.s, 8) || !aligned(it.x, 8) || (it.v && !aligned(it.v, 8)) || !aligned(it.resid, 8) ||
+            !aligned(it.iters, 4)) {
+            kz_set_error("kz_batch_prepare: item %d has a misaligned buffer", b);
+            return KZ_ERR_INVALID_ARG;
+        }
         if (prec == KZ_BF16_MIXED && it.plan->prec != KZ_BF16_MIXED) {
             kz_set_error("kz_batch_prepare: item %d's plan has no BF16 copy", b);
             return KZ_ERR_INVALID_ARG;
@@ -668,6 +697,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
         if (!it.v) B->all_v = false;
         B->cost[b] = (double)it.plan->total2 + 4.0 * it.plan->Ntp;
         B->plans.push_back(it.plan);
+        B->Ntp_of.push_back(it.plan->Ntp);
     }
     B->h_insts = insts;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -700,6 +730,11 @@ kz_status kz_batch_rebind(kz_batch* B, const kz_batch_item* items, void* stream)
         }
         if (!it.s || !it.x || !it.iters || !it.resid || !(it.xi > 0.f)) {
             kz_set_error("kz_batch_rebind: item %d is missing a buffer or positive xi", b);
+            return KZ_ERR_INVALID_ARG;
+        }
+        if (!aligned(it.s, 8) || !aligned(it.x, 8) || (it.v && !aligned(it.v, 8)) || !aligned(it.resid, 8) ||
+            !aligned(it.iters, 4)) {
+            kz_set_error("kz_batch_rebind: item %d has a misaligned buffer", b);
             return KZ_ERR_INVALID_ARG;
         }
         KzInst& I = insts[b];
@@ -742,13 +777,14 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.prec = B->prec;
     L.tol = tol;
     L.max_iter = max_iter;
-    L.refresh = refresh ? refresh : default_refresh(B->algo, B->prec);
+    L.refresh = refresh ? refresh : default_refresh(B->algo, B->prec, B->kernel == KZ_KERNEL_TC);
     L.seed = seed;
     L.status = status;
     L.Ntp_max = B->Ntp_max;
     L.K_max = B->K_max;
     L.cs = B->cs;
     L.tc = (B->kernel == KZ_KERNEL_TC);
+    L.m_elems = L.tc ? B->m_elems : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
@@ -796,7 +832,7 @@ kz_status kz_batch_tune(kz_batch* B, kz_select sel, double tol, int32_t max_iter
     if (tc_ok(B->algo, B->prec)) {
         for (int J : {4, 8}) {
             if (J == 8 && B->nrhs < 8) continue;
-            if (kz_smem_ahk_tc(J, B->Ntp_max, B->K_max) > kSmemLimit) continue;
+            if (tc_width(J, B->Ntp_max, B->Ntp_max, B->K_max) == 0) continue;  // the widest fits at >= 4
             for (int nw : {8, 16}) cands.push_back({KZ_KERNEL_TC, J, nw});
         }
     }
@@ -866,7 +902,7 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
         }
     } else if (kernel == KZ_KERNEL_TC) {
         if (!tc_ok(B->algo, B->prec) || (rhs_per_cta != 4 && rhs_per_cta != 8) ||
-            kz_smem_ahk_tc(rhs_per_cta, B->Ntp_max, B->K_max) > kSmemLimit) {
+            tc_width(rhs_per_cta, B->Ntp_max, B->Ntp_max, B->K_max) == 0) {
             kz_set_error("kz_batch_set_launch: the tensor-core kernel needs AHK / VR_OAHK on C64 with 4 or 8 "
                          "columns that fit shared memory");
             return KZ_ERR_UNSUPPORTED;

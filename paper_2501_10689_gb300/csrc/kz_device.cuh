@@ -59,9 +59,10 @@ __device__ __forceinline__ void cmac_pair(const float4& h, const float4& mm, flo
     acc.y = fmaf(h.w, mm.z, acc.y);
 }
 
+// Columns j >= jn (a narrower work item) are neither read nor written.
 template <int J, bool BF16>
 __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const int* rptr, int i,
-                                        const float2* __restrict__ m_s, int Ntp, float2 (&acc)[J]) {
+                                        const float2* __restrict__ m_s, int Ntp, float2 (&acc)[J], int jn = J) {
     const int lane = threadIdx.x & 31;
     const int4 rd = rows[i];
     const int base = rptr[i];
@@ -77,6 +78,7 @@ __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const
         for (int u = 0; u < 4; ++u) {
 #pragma unroll
             for (int j = 0; j < J; ++j) {
+                if (j >= jn) continue;
                 const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n + 64 * u);
                 cmac_pair<J, BF16>(h[u], mm, acc[j]);
             }
@@ -87,6 +89,7 @@ __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const
         const int n = rd.x + p;
 #pragma unroll
         for (int j = 0; j < J; ++j) {
+            if (j >= jn) continue;
             const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n);
             cmac_pair<J, BF16>(h, mm, acc[j]);
         }
@@ -182,7 +185,7 @@ __device__ __forceinline__ void warp_sum_c(float v, float& hi, float& lo) {
 template <int J>
 __device__ __forceinline__ void row_dot_c(const KzInst& I, const int4* rows, const int* rptr, int i,
                                           const float2* __restrict__ m_s, int Ntp, float2 (&hi)[J],
-                                          float2 (&lo)[J]) {
+                                          float2 (&lo)[J], int jn = J) {
     float2 acc[J];
     const int lane = threadIdx.x & 31;
     const int4 rd = rows[i];
@@ -198,13 +201,15 @@ __device__ __forceinline__ void row_dot_c(const KzInst& I, const int4* rows, con
         for (int u = 0; u < 4; ++u)
 #pragma unroll
             for (int j = 0; j < J; ++j)
-                cmac_pair<J, false>(h[u], *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p + 64 * u), acc[j]);
+                if (j < jn)
+                    cmac_pair<J, false>(h[u], *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p + 64 * u),
+                                        acc[j]);
     }
     for (; p < rd.y; p += 64) {
         const float4 h = h_pair<false>(I, base + p);
 #pragma unroll
         for (int j = 0; j < J; ++j)
-            cmac_pair<J, false>(h, *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p), acc[j]);
+            if (j < jn) cmac_pair<J, false>(h, *reinterpret_cast<const float4*>(m_s + j * Ntp + rd.x + p), acc[j]);
     }
 #pragma unroll
     for (int j = 0; j < J; ++j) {
@@ -225,7 +230,7 @@ __device__ __forceinline__ float2 true_resid(float2 b, float2 hi, float2 lo, flo
 template <int J, bool BF16>
 __device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, const int* rptr, int i,
                                          float2* __restrict__ m_s, int Ntp, const float2 (&g)[J], int lane,
-                                         int nlanes) {
+                                         int nlanes, int jn = J) {
     const int4 rd = rows[i];
     const int base = rptr[i];
     for (int p = 2 * lane; p < rd.y; p += 2 * nlanes) {
@@ -235,6 +240,7 @@ __device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, cons
         const bool in1 = (n + 1 >= rd.z) && (n + 1 < rd.w);
 #pragma unroll
         for (int j = 0; j < J; ++j) {
+            if (j >= jn) continue;
             float2* mp = m_s + j * Ntp + n;
             if (in0) {
                 float2 v = mp[0];
@@ -322,126 +328,162 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, floa
 }
 
 // Products H m_j for a block of 8 rows, vs[8 b .. 8 b + 8) (fewer at the end
-// of the list, nv entries), over the union of their aligned intervals, four
-// antennas per MMA:
+// of the list, nv entries), over the antenna range [nbeg, nend) (nbeg a
+// multiple of 8, nend even; a block's union interval is cut into such parts),
+// eight antennas per pair of MMAs:
 //   A[(j, re)][(n, re)] = Re m_j(n),  A[(j, re)][(n, im)] = -Im m_j(n),
 //   A[(j, im)][(n, re)] = Im m_j(n),  A[(j, im)][(n, im)] =  Re m_j(n)
-// (row j of the 16 for (j, re), row j + 8 for (j, im); j < J, the rest zero),
+// (row j of the 16 for (j, re), row j + 8 for (j, im); j < W, the rest zero),
 // B[(n, re | im)][row] = Re | Im H[row, n] (zero outside the row's interval),
-// so D[(j, re | im)][row] = Re | Im (H m_j)[row].  The K index of the MMA is
-// ordered (n, re) = c, (n, im) = c + 4 for antenna n = n0 + c, which lets
-// lane (g, c) fetch its A and B values as one complex each.  Lane (g, c)
-// returns column j = g of rows 2c (d[0] + i d[2]) and 2c + 1 (d[1] + i d[3])
-// of the block.  m_s column stride MS (even).
+// so D[(j, re | im)][row] = Re | Im (H m_j)[row] over the range.  Lane (g, c)
+// loads the antenna pair (n0 + 2c, n0 + 2c + 1) of row g and of m_g as one
+// 16-byte load each; the first MMA of the pair takes the even antennas, the
+// second the odd ones, with the K index ordered (n, re) = c, (n, im) = c + 4.
+// (Aligned intervals start and end on even antennas, so both antennas of a
+// pair are inside or outside a row together.)  Lane (g, c) returns column
+// j = g of rows 2c (d[0] + i d[2]) and 2c + 1 (d[1] + i d[3]) of the block.
+// m_s column stride MS (even; columns 16-byte aligned).
 template <int J>
-__device__ __forceinline__ void tc_row_block(const float2* __restrict__ Hc, const int4* rows, const int* rptr,
-                                             const int* vs, int nv, int b, const float2* __restrict__ m_s, int MS,
-                                             float (&d)[4]) {
+__device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const int4* rows, const int* rptr,
+                                            const int* vs, int nv, int b, int nbeg, int nend,
+                                            const float2* __restrict__ m_s, int MS, int W, float (&d)[4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
     const int k = 8 * b + g;
-    int a = 0, len = 0, hb = 0, lo = 0x7fffffff, hi = 0;
+    int a = 0, len = 0, hb = 0;
     if (k < nv) {
         const int row = vs[k];
         const int4 rd = rows[row];
         a = rd.x;
         len = rd.y;
         hb = rptr[row] - rd.x;
-        lo = rd.x;
-        hi = rd.x + rd.y;
-    }
-#pragma unroll
-    for (int o = 4; o < 32; o <<= 1) {
-        lo = min(lo, __shfl_xor_sync(KZ_FULL, lo, o));
-        hi = max(hi, __shfl_xor_sync(KZ_FULL, hi, o));
     }
     float e[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[u] = 0.f;
-    const bool jok = g < J;
+    const bool jok = g < W;  // W <= J columns of this item
     const float2* mj = m_s + (jok ? g : 0) * MS;
-    const float2 z = make_float2(0.f, 0.f);
-    int n0 = lo & ~3;
-    // eight chunks per step: all sixteen loads of a lane are issued before the
-    // first MMA of the step (the loop is bound by L2 latency, not MMA rate);
-    // two accumulators keep consecutive MMAs independent
+    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+    // eight antenna pairs per lane per step: all eight 16-byte H loads are in
+    // flight before the first MMA of the step; the iterate is read from
+    // shared memory next to its MMAs.  Entries at or beyond nend are zero on
+    // both sides.
     constexpr int U = 8;
-    for (; n0 + 4 * (U - 1) < hi; n0 += 4 * U) {
-        float2 h[U], m[U];
+    for (int n0 = nbeg; n0 < nend; n0 += 8 * U) {
+        float4 h[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int n = n0 + 4 * u + c;
-            h[u] = ((unsigned)(n - a) < (unsigned)len) ? __ldg(Hc + hb + n) : z;
-            m[u] = jok ? mj[n] : z;
+            const int n = n0 + 8 * u + 2 * c;
+            h[u] = (n < nend && (unsigned)(n - a) < (unsigned)len)
+                       ? __ldg(reinterpret_cast<const float4*>(Hc + hb + n))
+                       : z;
         }
 #pragma unroll
-        for (int u = 0; u < U; u += 2) {
-            mma_tf32(d, m[u].x, m[u].y, -m[u].y, m[u].x, h[u].x, h[u].y);
-            mma_tf32(e, m[u + 1].x, m[u + 1].y, -m[u + 1].y, m[u + 1].x, h[u + 1].x, h[u + 1].y);
+        for (int u = 0; u < U; ++u) {
+            const int n = n0 + 8 * u + 2 * c;
+            const float4 m = (jok && n < nend) ? *reinterpret_cast<const float4*>(mj + n) : z;
+            mma_tf32(d, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
+            mma_tf32(e, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
         }
-    }
-    for (; n0 < hi; n0 += 4) {
-        const int n = n0 + c;
-        const float2 h1 = ((unsigned)(n - a) < (unsigned)len) ? __ldg(Hc + hb + n) : z;
-        const float2 m1 = jok ? mj[n] : z;
-        mma_tf32(d, m1.x, m1.y, -m1.y, m1.x, h1.x, h1.y);
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[u] += e[u];
 }
 
-// u = H_V^H phi on one 64-antenna tile, antenna-major, eight covering rows
-// (list entries k0..k1 of the tile) per MMA:
+// u = H_V^H phi on one half (32 antennas, part 0 or 1) of a 64-antenna
+// tile, antenna-major, eight covering rows (list entries k0..k1 of the tile)
+// per MMA:
 //   A[(n, re)][row] = Re H[row, n],  A[(n, im)][row] = Im H[row, n]
-//   (rows g and g + 8 of the 16 for antenna 64 tile + 8 ab + g),
+//   (rows g and g + 8 of the 16 for antenna n),
 //   B[row][(j, re)] = Re phi[row][j], B[row][(j, im)] = Im phi[row][j]
-//   (columns 4 nb .. 4 nb + 3 per block nb of the 8 N entries),
-// so acc[ab][nb] holds the four real products whose sums and differences
-// give u (tc_u_combine).  coef: K x J phi in shared memory.
+//   (columns 4 nb .. 4 nb + 3 per block nb of the 8 N entries).
+// Lane (g, c) loads the antenna pair (s + 2g, s + 2g + 1) of rows c and
+// c + 4 as one 16-byte load each, for the two 16-antenna spans s of the
+// half; acc[sp][odd][nb] holds the products of antenna s + 2g + odd, whose
+// sums and differences give u (tc_u_combine).  coef: K x J phi in shared
+// memory.  Two chunks of eight rows per step (eight 16-byte loads of a lane
+// in flight before the MMAs).
 template <int J>
 __device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, const int4* __restrict__ trow4, int tile,
-                                             int k0, int k1, const float2* __restrict__ coef,
-                                             float (&acc)[8][J / 4][4]) {
+                                             int part, int k0, int k1, const float2* __restrict__ coef,
+                                             float (&acc)[2][2][J / 4][4]) {
     constexpr int NB = J / 4;
+    constexpr int KC = 2;
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
 #pragma unroll
-    for (int ab = 0; ab < 8; ++ab)
+    for (int sp = 0; sp < 2; ++sp)
 #pragma unroll
-        for (int nb = 0; nb < NB; ++nb)
+        for (int od = 0; od < 2; ++od)
 #pragma unroll
-            for (int u = 0; u < 4; ++u) acc[ab][nb][u] = 0.f;
+            for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+                for (int u = 0; u < 4; ++u) acc[sp][od][nb][u] = 0.f;
     const int4 none = make_int4(0, 0, 0, 0);  // empty interval: never matches
     const float2 z = make_float2(0.f, 0.f);
-    const int nb0 = tile * KZ_TILE + g;
-    int4 na = (k0 + c < k1) ? __ldg(trow4 + k0 + c) : none;
-    int4 nbx = (k0 + c + 4 < k1) ? __ldg(trow4 + k0 + c + 4) : none;
-    for (int k = k0; k < k1; k += 8) {
-        const bool va = k + c < k1, vb = k + c + 4 < k1;
-        const int4 ea = na, eb = nbx;
-        // descriptors of the next eight rows, in flight while these are used
-        na = (k + 8 + c < k1) ? __ldg(trow4 + k + 8 + c) : none;
-        nbx = (k + 12 + c < k1) ? __ldg(trow4 + k + 12 + c) : none;
-        float b0[NB], b1[NB];
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    const int nbase = tile * KZ_TILE + 32 * part + 2 * g;
+    int4 nxt[KC][2];
 #pragma unroll
-        for (int nb = 0; nb < NB; ++nb) {
-            const int j = 4 * nb + (g & 3);
-            const float2 pa = va ? coef[ea.x * J + j] : z;
-            const float2 pb = vb ? coef[eb.x * J + j] : z;
-            b0[nb] = (g >> 2) ? pa.y : pa.x;
-            b1[nb] = (g >> 2) ? pb.y : pb.x;
+    for (int q = 0; q < KC; ++q)
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int kk = k0 + 8 * q + 4 * h2 + c;
+            nxt[q][h2] = (kk < k1) ? __ldg(trow4 + kk) : none;
         }
+    for (int k = k0; k < k1; k += 8 * KC) {
+        int4 e[KC][2];
 #pragma unroll
-        for (int ab = 0; ab < 8; ++ab) {
-            const int n = nb0 + 8 * ab;
-            const float2 ha = (n >= ea.z && n < ea.w) ? __ldg(Hc + ea.y + n) : z;
-            const float2 hb = (n >= eb.z && n < eb.w) ? __ldg(Hc + eb.y + n) : z;
+        for (int q = 0; q < KC; ++q) {
+            e[q][0] = nxt[q][0];
+            e[q][1] = nxt[q][1];
+        }
+        float4 h[KC][2][2];
 #pragma unroll
-            for (int nb = 0; nb < NB; ++nb) mma_tf32(acc[ab][nb], ha.x, ha.y, hb.x, hb.y, b0[nb], b1[nb]);
+        for (int q = 0; q < KC; ++q)
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp) {
+                const int n = nbase + 16 * sp;
+#pragma unroll
+                for (int h2 = 0; h2 < 2; ++h2) {
+                    const int4 en = e[q][h2];
+                    h[q][sp][h2] = (n >= en.z && n < en.w)
+                                       ? __ldg(reinterpret_cast<const float4*>(Hc + en.y + n))
+                                       : z4;
+                }
+            }
+        // descriptors of the next step, in flight while this one is used
+#pragma unroll
+        for (int q = 0; q < KC; ++q)
+#pragma unroll
+            for (int h2 = 0; h2 < 2; ++h2) {
+                const int kk = k + 8 * KC + 8 * q + 4 * h2 + c;
+                nxt[q][h2] = (kk < k1) ? __ldg(trow4 + kk) : none;
+            }
+#pragma unroll
+        for (int q = 0; q < KC; ++q) {
+            const bool va = k + 8 * q + c < k1, vb = k + 8 * q + c + 4 < k1;
+            float b0[NB], b1[NB];
+#pragma unroll
+            for (int nb = 0; nb < NB; ++nb) {
+                const int j = 4 * nb + (g & 3);
+                const float2 pa = va ? coef[e[q][0].x * J + j] : z;
+                const float2 pb = vb ? coef[e[q][1].x * J + j] : z;
+                b0[nb] = (g >> 2) ? pa.y : pa.x;
+                b1[nb] = (g >> 2) ? pb.y : pb.x;
+            }
+#pragma unroll
+            for (int sp = 0; sp < 2; ++sp)
+#pragma unroll
+                for (int nb = 0; nb < NB; ++nb) {
+                    const float4 ha = h[q][sp][0], hb = h[q][sp][1];
+                    mma_tf32(acc[sp][0][nb], ha.x, ha.y, hb.x, hb.y, b0[nb], b1[nb]);
+                    mma_tf32(acc[sp][1][nb], ha.z, ha.w, hb.z, hb.w, b0[nb], b1[nb]);
+                }
         }
     }
 }
 
 // Sums and differences of tc_tile_aggr's products (all lanes take part):
-// lanes c < 2 return u at antenna 64 tile + 8 ab + g for columns
+// lanes c < 2 return u at the products' antenna for columns
 // j = 4 nb + 2c (u0) and j + 1 (u1).  With the partner lane c + 2 (which
 // holds the Im phi products):  Re u = Re H Re phi + Im H Im phi,
 // Im u = Re H Im phi - Im H Re phi.
@@ -450,6 +492,21 @@ __device__ __forceinline__ void tc_u_combine(const float (&a)[4], float2& u0, fl
     const float e2 = __shfl_xor_sync(KZ_FULL, a[2], 2), e3 = __shfl_xor_sync(KZ_FULL, a[3], 2);
     u0 = make_float2(a[0] + e2, e0 - a[2]);
     u1 = make_float2(a[1] + e3, e1 - a[3]);
+}
+
+// Column `col` of an Nt-long complex output: entries n and n + 1 (n < Nt).
+// One 16-byte store when the pair is inside the column and its address is
+// 16-byte aligned (the caller's buffer need only be 8-byte aligned), else
+// two 8-byte stores.
+__device__ __forceinline__ void kz_store_pair(float2* out, int Nt, int col, int n, bool on, float2 a, float2 b) {
+    if (!on) return;
+    float2* p = out + (size_t)col * Nt + n;
+    if (n + 1 < Nt && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        *reinterpret_cast<float4*>(p) = make_float4(a.x, a.y, b.x, b.y);
+    } else {
+        p[0] = a;
+        if (n + 1 < Nt) p[1] = b;
+    }
 }
 
 // ---------------------------------------------------------------------------

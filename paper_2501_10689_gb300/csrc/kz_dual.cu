@@ -446,7 +446,7 @@ __global__ void __launch_bounds__(NW * 32, 1) kz_dual_kernel(const __grid_consta
         __syncthreads();
         const KzInst& I = sI;
         const int K = I.K, nF = oahk ? I.nF : 0;
-        const int col0 = it.y, ncols = min(J, I.ld - col0);
+        const int col0 = KZ_ITEM_COL(it.y), ncols = min(J, I.ld - col0);
         const float xi = I.xi;
 
         // r = s, q = 0 at w = 0

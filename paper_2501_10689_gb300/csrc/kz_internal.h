@@ -68,7 +68,13 @@ struct KzLaunch {
     int Ntp_max, K_max;
     int cs;               // dual kernel: staged rows per chunk
     int tc;               // resident kernel: tensor-core inner products (correction form)
+    int m_elems;          // resident kernel: shared iterate entries per CTA (0: J x (Ntp_max + pad))
 };
+
+// Work item {instance, first column | (columns << 24)}: the column count of
+// an item (its width, at most the kernel's J) is 0 for "J".
+#define KZ_ITEM_COL(y) ((y) & 0xffffff)
+#define KZ_ITEM_WIDTH(y, J) (((y) >> 24) ? ((y) >> 24) : (J))
 
 // Host-side launchers (kz_ahk.cu / kz_kacz.cu).
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
@@ -76,7 +82,8 @@ cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t sm
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
-size_t kz_smem_ahk_tc(int J, int Ntp, int K);
+// Tensor-core mode: m_elems shared iterate entries (columns of Ntp + 4).
+size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K);
 int kz_occupancy_ahk_tc(int J, int nw, size_t smem);
 int kz_occupancy_kacz(int J, int nw, size_t smem);
 cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);

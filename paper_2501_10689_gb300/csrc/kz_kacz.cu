@@ -64,7 +64,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
         __syncthreads();
         const KzInst& I = sI;
         const int K = I.K, Nt = I.Nt, Ntp = I.Ntp;
-        const int col0 = it.y, ncols = min(J, I.ld - col0);
+        const int col0 = KZ_ITEM_COL(it.y), ncols = min(J, I.ld - col0);
         const float xi = I.xi;
         const int4* trow4 = I.trow4;
 

@@ -155,3 +155,30 @@ def test_tc_rejects_unsupported(kp):
     bplan = kp.plan_from_instance(inst, prec="bf16")
     with pytest.raises(kp.KzError):
         kp.precode(bplan, S, inst.xi, algo="vr_oahk", kernel="tc")
+
+
+def test_tc_mixed_widths(kp):
+    """J = 8 launch over a batch whose widest channel only fits 4 iterate
+    columns: that channel's items are 4 columns wide, the others 8."""
+    insts = [kzgen.make_instance(700, 200, 4096, vr_frac_range=(0.1, 0.4), nrhs=16),
+             kzgen.make_instance(701, 30, 640, vr_frac_range=(0.1, 0.4), nrhs=16),
+             kzgen.make_instance(702, 64, 2048, vr_frac_range=(0.1, 0.4), nrhs=16)]
+    items = []
+    for inst in insts:
+        p = kp.plan_from_instance(inst)
+        items.append(dict(plan=p, s=kp.rhs_tensor(inst.S),
+                          x=torch.empty((16, inst.Nt), dtype=torch.complex64, device="cuda"),
+                          v=torch.empty((16, inst.K), dtype=torch.complex64, device="cuda"),
+                          iters=torch.empty(16, dtype=torch.int32, device="cuda"),
+                          resid=torch.empty(16, dtype=torch.float64, device="cuda"), xi=inst.xi))
+    b = kp.kz_batch_prepare(items, 16, "vr_oahk")
+    kp.kz_batch_set_launch(b, "tc", 8, 512)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_batched(b, "paper", 1e-6, 3000, 0, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    for inst, it in zip(insts, items):
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X)
+        assert np.all(orz.rel_err(it["v"].cpu().numpy().T, V) <= TOL_X)
+        assert np.all(it["resid"].cpu().numpy() <= 1e-6 * (1 + 1e-6))
