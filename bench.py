@@ -35,11 +35,12 @@ MAX_ITER = 1000
 GRK_MAX_ITER = 100000
 ERR_BAR = 1e-5
 
-# DRAM traffic of one resident-kernel launch on this workload (ncu, one pass:
-# dram__bytes_read.sum + dram__bytes_write.sum; profiles/kz_ahk_batched_512x16.md),
-# valid only for the kernel sources it was measured on (their SHA-256 prefix).
-TRAFFIC = {"sources_sha256": "ca6a2ebf809ffb4c", "bytes_per_launch": 7.59e9 + 2.00e9,
-           "launch": ("resident", 2, 512)}
+# DRAM traffic of one solver launch on this workload per launch configuration
+# (ncu, one pass: dram__bytes_read.sum + dram__bytes_write.sum; the profiles/
+# summary of this workload), valid only for the kernel sources it was measured
+# on (their SHA-256 prefix).
+TRAFFIC = {"sources_sha256": "1efd11d09e8c5dee",
+           "bytes_per_launch": {("tc", 4, 512): 3.30e9 + 1.15e9, ("tc", 8, 512): 6.28e9 + 1.76e9}}
 KERNEL_SOURCES = ("paper_2501_10689_gb300/csrc/kz_ahk.cu", "paper_2501_10689_gb300/csrc/kz_device.cuh",
                   "paper_2501_10689_gb300/csrc/kz_internal.h")
 
@@ -211,7 +212,8 @@ def run_ours(args):
                           v=torch.empty((NRHS, inst.K), dtype=torch.complex64, device=dev),
                           iters=torch.empty(NRHS, dtype=torch.int32, device=dev),
                           resid=torch.empty(NRHS, dtype=torch.float64, device=dev), xi=inst.xi))
-    batch = kp.kz_batch_prepare(items, NRHS, "vr_oahk", rhs_per_cta=args.rhs_per_cta)
+    batch = kp.kz_batch_prepare(items, NRHS, "vr_oahk",
+                                rhs_per_cta=args.rhs_per_cta if args.kernel == "resident" else 0)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
     stream = torch.cuda.Stream(device=dev)
     tuned = None
@@ -293,17 +295,23 @@ def run_ours(args):
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x clock under load
     launch_now = (tuned if tuned else (args.kernel, args.rhs_per_cta, args.threads))
     traffic = None
-    if kernel_sources_sha() == TRAFFIC["sources_sha256"] and tuple(launch_now) == TRAFFIC["launch"] \
-            and args.instances == N_INST:
-        traffic = TRAFFIC["bytes_per_launch"]
+    if kernel_sources_sha() == TRAFFIC["sources_sha256"] and args.instances == N_INST:
+        traffic = TRAFFIC["bytes_per_launch"].get(tuple(launch_now))
+    tc = launch_now[0] == "tc"
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch from ncu (one pass) on this workload and kernel build; "
                                 "null when the kernel sources or launch differ",
                 "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
-                "kernel": "kz_ahk_kernel (batched VR-OAHK)",
+                "kernel": ("kz_ahk_kernel<J, 16 warps, tensor-core mode> (batched VR-OAHK)" if tc
+                           else "kz_ahk_kernel (batched VR-OAHK)"),
                 "alu_view": {"achieved_tflops": achieved_tflops, "fp32_fma_peak_tflops": alu_peak,
                              "frac": achieved_tflops / alu_peak}}
+    if tc and "bf16_tflops" in peaks:
+        tf32_peak = float(peaks["bf16_tflops"]) / 2.0  # dense TF32 runs at half the BF16 rate
+        roofline["tensor_view"] = {"achieved_tflops": achieved_tflops, "tf32_peak_tflops": tf32_peak,
+                                   "peak_source": "measured bf16_tflops (burst) x 1/2, the nominal TF32:BF16 ratio",
+                                   "frac": achieved_tflops / tf32_peak}
 
     # ---- GRK on the same batch (comparison arm)
     grk = None
@@ -360,7 +368,11 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "precoders/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "vs_baseline": None, "dtype": "f32+tf32" if tc else "f32", "data": "synthetic",
+                "precision": ("complex64 storage; TF32 tensor-core products with FP32 sums inside the "
+                              "correction-form iteration; FP32 refresh b = s - H m_ref, true residual and "
+                              "stopping test (compensated sums)" if tc else
+                              "complex64 storage, FP32 arithmetic; true residual with compensated sums"),
                 "config": {"workload": workload_desc(), "instances_per_gpu": args.instances, "nrhs": NRHS,
                            "tol": TOL, "max_iter": MAX_ITER,
                            "launch": ({"kernel": tuned[0], "rhs_per_cta": tuned[1], "threads": tuned[2],

@@ -50,6 +50,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     __shared__ double s_sn2[J];
     __shared__ float s_gamma[J];
     __shared__ int s_iters[J];
+    __shared__ int s_wait[J];  // iterations a column spent waiting for its confirmation
     __shared__ int s_active;
     __shared__ int s_pending;
     __shared__ int s_item;
@@ -201,6 +202,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             int act = 0;
             for (int j = 0; j < ncols; ++j) {
                 s_iters[j] = L.max_iter;
+                s_wait[j] = 0;
                 if (s_sn2[j] > 0.0) act |= 1 << j;
                 else s_iters[j] = 0;
             }
@@ -345,12 +347,14 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             // a column that passes is confirmed on the true residual first)
             if (tid == 0) {
                 int a2 = s_active, pend = 0;
+                for (int j = 0; j < ncols; ++j)
+                    if (((a2 & ~act) >> j) & 1) ++s_wait[j];  // reported iterations count steps taken
                 for (int j = 0; j < ncols; ++j) {
                     if (!((a2 >> j) & 1)) continue;
                     const float rn2 = s_tot[j];
                     if (!(rn2 == rn2) || isinf(rn2)) {
                         a2 &= ~(1 << j);
-                        s_iters[j] = t;
+                        s_iters[j] = t - s_wait[j];
                         kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
                     } else if ((double)rn2 <= (double)tol2 * s_sn2[j]) {
                         pend |= 1 << j;
@@ -416,11 +420,11 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         for (int w = 0; w < NW; ++w) rn2 += s_partd[w][j];
                         if (!(rn2 == rn2) || isinf(rn2)) {
                             a2 &= ~(1 << j);
-                            s_iters[j] = t;
+                            s_iters[j] = t - s_wait[j];
                             kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
                         } else if (rn2 <= L.tol * L.tol * s_sn2[j]) {
                             a2 &= ~(1 << j);
-                            s_iters[j] = t;
+                            s_iters[j] = t - s_wait[j];
                         } else if (!oahk && t >= L.max_iter) {
                             a2 &= ~(1 << j);
                             kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
