@@ -446,7 +446,7 @@ def run_configs(args):
         plan = kp.plan_from_instance(inst, device=dev)
         S = kp.rhs_tensor(inst.S, device=dev)
         for algo, kernel in (("rk_energy", "auto"), ("grk", "auto"), ("vr_ogrk", "auto"), ("ahk", "auto"),
-                             ("vr_oahk", "resident"), ("vr_oahk", "dual")):
+                             ("ahk", "tc"), ("vr_oahk", "resident"), ("vr_oahk", "dual"), ("vr_oahk", "tc")):
             max_iter = 400000 if algo.startswith("rk") else (40000 if "grk" in algo else 4000)
             for tol in (1e-5, 3e-6, 1e-6):
                 out = kp.precode(plan, S, inst.xi, algo=algo, tol=tol, max_iter=max_iter, kernel=kernel)
@@ -462,13 +462,18 @@ def run_configs(args):
     inst = kzgen.config4()
     V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
     S = kp.rhs_tensor(inst.S, device=dev)
-    for prec in ("bf16", "c64"):
+    for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc")):
         plan = kp.plan_from_instance(inst, prec=prec, device=dev)
-        out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000)
+        try:
+            out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000, kernel=kernel)
+        except kp.KzError as e:  # e.g. the tensor-core kernel's iterate does not fit shared memory
+            emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
+                  "kernel": kernel, "unsupported": str(e)})
+            continue
         err = float(np.max(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)))
-        ms = _time_ms(lambda: solve(plan, S, inst.xi, "vr_oahk", 1e-6, 3000), reps=3)
+        ms = _time_ms(lambda: solve(plan, S, inst.xi, "vr_oahk", 1e-6, 3000, kernel), reps=3)
         emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
-              "tol": 1e-6, "ms_per_solve": ms, "precoders_per_s": 64 / (ms / 1000.0),
+              "kernel": kernel, "tol": 1e-6, "ms_per_solve": ms, "precoders_per_s": 64 / (ms / 1000.0),
               "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err_vs_fp64": err})
 
     # config 5: forward + adjoint of the sum-rate loss over 64 channels
@@ -536,6 +541,7 @@ def run_configs(args):
           "mode": "batched", "grad_evals_per_s": 64 / dt, "seconds_per_batch": dt,
           "grad_H_rel_err_vs_fp64_autograd": float(np.linalg.norm(gH - gH_ref) / np.linalg.norm(gH_ref)),
           "grad_xi_rel_err": float(abs(xb.grad[0].item() - gxi_ref) / abs(gxi_ref)),
+          "launch": list(pre._launch),
           "note": "BatchedPrecoder: plan re-pack, one batched forward solve, loss in torch, one batched adjoint "
                   "(right-hand sides, solve, contractions), host clock, mean of 5"})
 

@@ -75,7 +75,10 @@ class BatchedPrecoder:
     ``split`` views them per channel.
     """
 
-    def __init__(self, layouts, nrhs, tol=1e-6, max_iter=2000, device="cuda"):
+    def __init__(self, layouts, nrhs, tol=1e-6, max_iter=2000, device="cuda", launch=None):
+        """``launch``: (kernel, columns per CTA, threads) for both solves, or
+        None to autotune the forward batch on the first call (kz_batch_tune)
+        and reuse its choice for the adjoint."""
         self.layouts = [(np.asarray(o, np.int32), np.asarray(l, np.int32), int(nt)) for o, l, nt in layouts]
         self.n = len(self.layouts)
         self.nrhs = int(nrhs)
@@ -100,6 +103,10 @@ class BatchedPrecoder:
                                   torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev))
         self._adj = self._prepare(self._gt, self._y, torch.zeros(int(self.s_off[-1]), dtype=torch.complex64, device=dev))
         self._dense_idx = None
+        self._launch = tuple(launch) if launch is not None else None
+        if self._launch is not None:
+            kp.kz_batch_set_launch(self._fwd, *self._launch)
+            kp.kz_batch_set_launch(self._adj, *self._launch)
 
     def split(self, cat, which):
         """Per-channel (nrhs, K) or (nrhs, Nt) views of an S/V ('s') or X ('x') concatenation."""
@@ -128,6 +135,10 @@ class BatchedPrecoder:
 
     def _run(self, batch, items, status, adjoint_items=None):
         kp.kz_batch_rebind(batch, items)
+        if adjoint_items is None and self._launch is None:
+            # first forward: time the feasible launches on real data, keep the fastest
+            self._launch = kp.kz_batch_tune(batch, "paper", self.tol, self.max_iter, 0)
+            kp.kz_batch_set_launch(self._adj, *self._launch)
         if adjoint_items is None:
             kp.kz_precode_batched(batch, "paper", self.tol, self.max_iter, 0, status=status)
         else:

@@ -567,9 +567,12 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         }
         smem = kz_smem_dual(J, nw, cs, plan->K);
     } else if (kernel == KZ_KERNEL_TC) {
+        // 8 columns per CTA only when that still gives every SM a work item
         J = rhs_per_cta ? rhs_per_cta
-                        : (nrhs >= 8 && kz_smem_ahk_tc(8, 8 * (plan->Ntp + 4), plan->Ntp, plan->K) <= kSmemLimit ? 8
-                                                                                                           : 4);
+                        : ((nrhs + 7) / 8 >= plan->sms &&
+                                   kz_smem_ahk_tc(8, 8 * (plan->Ntp + 4), plan->Ntp, plan->K) <= kSmemLimit
+                               ? 8
+                               : 4);
         nw = choose_nw(plan->Ntp);
         smem = kz_smem_ahk_tc(J, J * (plan->Ntp + 4), plan->Ntp, plan->K);
     } else {
