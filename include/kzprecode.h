@@ -291,6 +291,25 @@ typedef struct {
 kz_status kz_precode_adjoint_batched(kz_batch* batch, const kz_adjoint_item* items, double tol,
                                      int32_t max_iter, int32_t* status, void* stream);
 
+/* Per-user SINR and spectral efficiency of the precoder (eq. (rate)):
+ * F = beta X with beta = 1 / ||X||_F (the power budget ||F||_F^2 <= 1 of
+ * eq. (power) met with equality), SINR_k = |h_k^H f_k|^2 /
+ * (sum_{i != k} |h_k^H f_i|^2 + 1 / snr_lin), rate = sum_k log2(1 + SINR_k).
+ * X: device, Nt x K column-major (column k is user k's precoder: the x of a
+ * solve with identity right-hand sides), 8-byte aligned; snr_lin = rho /
+ * sigma^2 > 0; sinr: device double[K] or NULL; rate: device double or NULL
+ * (not both NULL).  h_k^H f_i is summed in FP32 with compensated
+ * cross-lane additions, every square and sum after that in FP64, in a fixed
+ * order.  Asynchronous on `stream`. */
+kz_status kz_sum_rate(const kz_plan* plan, const kz_cf32* X, double snr_lin, double* sinr, double* rate,
+                      void* stream);
+
+/* kz_sum_rate for every channel of a batch, one launch, on the items' x
+ * buffers (the batch's column count must equal every item's K).  sinr:
+ * device double[n * K_max], channel b's users at b * K_max (K_max = largest K
+ * of the batch), or NULL; rate: device double[n] or NULL. */
+kz_status kz_sum_rate_batched(const kz_batch* batch, double snr_lin, double* sinr, double* rate, void* stream);
+
 /* One-line description of the last error on this thread ("" if none). */
 const char* kz_last_error(void);
 

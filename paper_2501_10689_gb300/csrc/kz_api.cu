@@ -970,6 +970,43 @@ kz_status kz_precode_adjoint_batched(kz_batch* B, const kz_adjoint_item* items, 
     return check_launch(e, "kz_precode_adjoint_batched contraction");
 }
 
+kz_status kz_sum_rate(const kz_plan* plan, const kz_cf32* X, double snr_lin, double* sinr, double* rate,
+                      void* stream) {
+    g_err.clear();
+    if (!plan || !X || !aligned(X, 8) || !(snr_lin > 0.0) || (!sinr && !rate) || (sinr && !aligned(sinr, 8)) ||
+        (rate && !aligned(rate, 8))) {
+        kz_set_error("kz_sum_rate: need a plan, an 8-byte aligned X, snr_lin > 0 and an output");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if ((2 * (size_t)plan->K + 32) * sizeof(double) > kSmemLimit) {
+        kz_set_error("kz_sum_rate: K = %d users exceed the kernel's shared memory", plan->K);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = kz_sum_rate(plan->inst(), reinterpret_cast<const float2*>(X), snr_lin, sinr, rate,
+                                static_cast<cudaStream_t>(stream));
+    return check_launch(e, "kz_sum_rate");
+}
+
+kz_status kz_sum_rate_batched(const kz_batch* B, double snr_lin, double* sinr, double* rate, void* stream) {
+    g_err.clear();
+    if (!B || !(snr_lin > 0.0) || (!sinr && !rate) || (sinr && !aligned(sinr, 8)) || (rate && !aligned(rate, 8))) {
+        kz_set_error("kz_sum_rate_batched: need a batch, snr_lin > 0 and an output");
+        return KZ_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < B->n; ++b)
+        if (B->plans[b]->K != B->nrhs) {
+            kz_set_error("kz_sum_rate_batched: item %d has K = %d users but %d columns", b, B->plans[b]->K, B->nrhs);
+            return KZ_ERR_INVALID_ARG;
+        }
+    if ((2 * (size_t)B->K_max + 32) * sizeof(double) > kSmemLimit) {
+        kz_set_error("kz_sum_rate_batched: K = %d users exceed the kernel's shared memory", B->K_max);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    cudaError_t e = kz_sum_rate_batched(B->d_insts, B->n, B->K_max, snr_lin, sinr, rate,
+                                        static_cast<cudaStream_t>(stream));
+    return check_launch(e, "kz_sum_rate_batched");
+}
+
 kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q, const kz_cf32* X,
                              const kz_cf32* G_Q, const kz_cf32* G_X, double tol, int32_t max_iter, kz_cf32* lambda,
                              kz_cf32* y, kz_cf32* grad_H_packed, float* grad_xi, int32_t* iters, double* resid,

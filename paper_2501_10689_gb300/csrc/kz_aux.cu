@@ -1,4 +1,5 @@
-// Set-up kernels (step A0) and the adjoint contractions (step A10).
+// Set-up kernels (step A0), the adjoint contractions (step A10) and the
+// per-user SINR / sum rate of the precoder (eq. (rate)).
 #include "kz_device.cuh"
 
 namespace {
@@ -193,7 +194,103 @@ __global__ void adjoint_grad_xi_batched_kernel(const KzInst* __restrict__ insts,
     }
 }
 
+// Per-user SINR and sum rate of F = X / ||X||_F (eq. (rate)) for one channel
+// per block; X is Nt x K column-major (column k: user k's precoder).  Each
+// warp owns whole rows k and sweeps the K columns in order (G_kj = h_k . x_j
+// over row k's VR, FP32 lane sums combined with compensated additions,
+// |G_kj|^2 summed in FP64), so every sum has a fixed order.
+__device__ void sum_rate_block(const KzInst& I, const float2* __restrict__ X, double snr_lin, double* sinr,
+                               double* rate, double* sm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int K = I.K, Nt = I.Nt;
+    double* sig = sm;          // K
+    double* itf = sm + K;      // K
+    double* part = sm + 2 * K; // 32 per-warp partials
+    for (int k = warp; k < K; k += nw) {
+        const int4 rd = I.rows[k];  // {a, len2, o, e}
+        const float2* h = I.Hc + I.rptr[k] - rd.x;
+        double acc_itf = 0.0, acc_sig = 0.0;
+        for (int j = 0; j < K; ++j) {
+            const float2* xj = X + (size_t)j * Nt;
+            float gx = 0.f, gy = 0.f;
+            for (int n = rd.z + lane; n < rd.w; n += 32) {
+                const float2 a = h[n], b = xj[n];
+                gx = fmaf(a.x, b.x, fmaf(-a.y, b.y, gx));
+                gy = fmaf(a.x, b.y, fmaf(a.y, b.x, gy));
+            }
+            float hx, lx, hy, ly;
+            warp_sum_c(gx, hx, lx);
+            warp_sum_c(gy, hy, ly);
+            const double re = (double)hx + lx, im = (double)hy + ly;
+            const double g2 = re * re + im * im;
+            if (j == k) acc_sig = g2;
+            else acc_itf += g2;
+        }
+        if (lane == 0) {
+            sig[k] = acc_sig;
+            itf[k] = acc_itf;
+        }
+    }
+    // ||X||_F^2, fixed order: per-thread sums, then per warp, then warp 0
+    double f = 0.0;
+    for (size_t e = threadIdx.x; e < (size_t)K * Nt; e += blockDim.x) {
+        const float2 v = X[e];
+        f += (double)v.x * v.x + (double)v.y * v.y;
+    }
+    f = warp_sum_d(f);
+    if (lane == 0) part[warp] = f;
+    __syncthreads();
+    if (warp == 0) {
+        double fr = 0.0;
+        for (int w = 0; w < nw; ++w) fr += part[w];
+        const double beta2 = fr > 0.0 ? 1.0 / fr : 0.0;
+        double r = 0.0;
+        for (int k = lane; k < K; k += 32) {
+            const double g = beta2 * sig[k] / (beta2 * itf[k] + 1.0 / snr_lin);
+            if (sinr) sinr[k] = g;
+            r += log2(1.0 + g);
+        }
+        r = warp_sum_d(r);
+        if (lane == 0 && rate) *rate = r;
+    }
+}
+
+__global__ void sum_rate_kernel(const __grid_constant__ KzInst I, const float2* X, double snr_lin, double* sinr,
+                                double* rate) {
+    extern __shared__ double kz_sr_smem[];
+    sum_rate_block(I, X, snr_lin, sinr, rate, kz_sr_smem);
+}
+
+// Batched: block b takes channel b of the batch and its x buffer; SINRs of
+// channel b at sinr[b * K_max ...], its rate at rate[b].
+__global__ void sum_rate_batched_kernel(const KzInst* __restrict__ insts, int K_max, double snr_lin, double* sinr,
+                                        double* rate) {
+    extern __shared__ double kz_sr_smem[];
+    const KzInst& I = insts[blockIdx.x];
+    sum_rate_block(I, I.x, snr_lin, sinr ? sinr + (size_t)blockIdx.x * K_max : nullptr,
+                   rate ? rate + blockIdx.x : nullptr, kz_sr_smem);
+}
+
 }  // namespace
+
+cudaError_t kz_sum_rate(const KzInst& I, const float2* X, double snr_lin, double* sinr, double* rate,
+                        cudaStream_t st) {
+    const size_t smem = (2 * (size_t)I.K + 32) * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(sum_rate_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sum_rate_kernel<<<1, 1024, smem, st>>>(I, X, snr_lin, sinr, rate);
+    return cudaGetLastError();
+}
+
+cudaError_t kz_sum_rate_batched(const KzInst* insts, int n, int K_max, double snr_lin, double* sinr, double* rate,
+                                cudaStream_t st) {
+    const size_t smem = (2 * (size_t)K_max + 32) * sizeof(double);
+    cudaError_t e =
+        cudaFuncSetAttribute(sum_rate_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    sum_rate_batched_kernel<<<n, 1024, smem, st>>>(insts, K_max, snr_lin, sinr, rate);
+    return cudaGetLastError();
+}
 
 cudaError_t kz_adjoint_rhs_batched(const KzInst* insts, const KzAdjItem* adj, int n, int K_max, int nrhs,
                                    cudaStream_t st) {

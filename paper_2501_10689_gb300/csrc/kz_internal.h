@@ -117,5 +117,12 @@ cudaError_t kz_adjoint_rhs_batched(const KzInst* insts, const KzAdjItem* adj, in
 cudaError_t kz_adjoint_contract_batched(const KzInst* insts, const KzAdjItem* adj, int n, int K_max, int nrhs,
                                         cudaStream_t st);
 
+// Per-user SINR and sum rate of F = X / ||X||_F (kz_aux.cu): one channel, or
+// every channel of a batch (its items' x, SINRs at b * K_max).
+cudaError_t kz_sum_rate(const KzInst& I, const float2* X, double snr_lin, double* sinr, double* rate,
+                        cudaStream_t st);
+cudaError_t kz_sum_rate_batched(const KzInst* insts, int n, int K_max, double snr_lin, double* sinr, double* rate,
+                                cudaStream_t st);
+
 // Thread-local last-error text (kz_api.cu).
 void kz_set_error(const char* fmt, ...);

@@ -49,7 +49,7 @@ class KzBatchItem(ctypes.Structure):
 EXPORTS = ("kz_plan_create", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
-           "kz_last_error", "kz_version")
+           "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "dual": 2, "tc": 3}
 
 
@@ -70,6 +70,10 @@ def load():
                                   ctypes.c_double, ctypes.c_uint64)
     lib.kz_plan_create.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_create.restype = I32
+    lib.kz_sum_rate.argtypes = [P, P, F64, P, P, P]
+    lib.kz_sum_rate.restype = I32
+    lib.kz_sum_rate_batched.argtypes = [P, F64, P, P, P]
+    lib.kz_sum_rate_batched.restype = I32
     lib.kz_batch_rebind.argtypes = [P, P, P]
     lib.kz_batch_rebind.restype = I32
     lib.kz_plan_update.argtypes = [P, P, P]
@@ -312,6 +316,22 @@ def kz_precode_adjoint_batched(batch: Batch, items, tol, max_iter, status=None, 
                                it["grad_H"].data_ptr(), it["grad_xi"].data_ptr())
     return _check(lib.kz_precode_adjoint_batched(batch.handle, ctypes.cast(arr, ctypes.c_void_p), float(tol),
                                                  int(max_iter), _ptr(status), _stream(stream)))
+
+
+def kz_sum_rate(plan: Plan, X, snr_lin, sinr=None, rate=None, stream=None):
+    """X: complex64 (K, Nt) (row k = user k's precoder column); sinr: float64 (K,); rate: float64 (1,)."""
+    lib = load()
+    _check_c64(X, (plan.K, plan.Nt), "X")
+    for t, shape, name in ((sinr, (plan.K,), "sinr"), (rate, (1,), "rate")):
+        if t is not None and (t.dtype != torch.float64 or tuple(t.shape) != shape):
+            raise ValueError(f"{name}: expected float64 tensor of shape {shape}")
+    return _check(lib.kz_sum_rate(plan.handle, _ptr(X), float(snr_lin), _ptr(sinr), _ptr(rate), _stream(stream)))
+
+
+def kz_sum_rate_batched(batch: Batch, snr_lin, sinr=None, rate=None, stream=None):
+    """sinr: float64 (n, K_max); rate: float64 (n,)."""
+    lib = load()
+    return _check(lib.kz_sum_rate_batched(batch.handle, float(snr_lin), _ptr(sinr), _ptr(rate), _stream(stream)))
 
 
 def kz_version() -> int:
