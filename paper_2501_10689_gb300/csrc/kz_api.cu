@@ -124,7 +124,19 @@ struct kz_batch {
     bool all_v = true;           // every item has a v buffer
     std::vector<const kz_plan*> plans;  // the items' plans, fixed at preparation
     std::vector<KzInst> h_insts;        // host copy of the instance table
+    // Tensor-core kernel at J = 8 over channels of both widths: the 4-column
+    // items run as a second launch of the J = 4 kernel, on an auxiliary stream
+    // forked from and joined to the caller's.
+    int2* d_items2 = nullptr;
+    int n_items2 = 0, grid2 = 0, m_elems2 = 0;
+    size_t smem2 = 0;
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     ~kz_batch() {
+        if (ev_fork) cudaEventDestroy(ev_fork);
+        if (ev_join) cudaEventDestroy(ev_join);
+        if (aux) cudaStreamDestroy(aux);
+        if (d_items2) cudaFree(d_items2);
         if (d_adj) cudaFree(d_adj);
         if (d_insts) cudaFree(d_insts);
         if (d_items) cudaFree(d_items);
@@ -195,24 +207,57 @@ int tc_width(int J, int Ntp, int Ntp_max, int K_max) {
 }
 
 cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cudaStream_t st) {
-    std::vector<std::pair<double, int2>> work;
-    int m_elems = 0;
+    // work items {instance, first column | width << 24} with a cost estimate;
+    // tensor-core items narrower than J go to the second list
+    std::vector<std::pair<double, int2>> work, work2;
+    int m_elems = 0, m_elems2 = 0;
+    double cost1 = 0.0, cost2 = 0.0;
     for (int b = 0; b < B->n; ++b) {
         int W = J;
         if (kernel == KZ_KERNEL_TC) {
             W = tc_width(J, B->Ntp_of[b], B->Ntp_max, B->K_max);
             if (W == 0) return cudaErrorInvalidValue;
-            m_elems = std::max(m_elems, W * (B->Ntp_of[b] + 4));
         }
-        for (int c = 0; c < B->nrhs; c += W) work.push_back({B->cost[b] * W, make_int2(b, c | (W << 24))});
+        const bool second = (W < J);
+        for (int c = 0; c < B->nrhs; c += W) {
+            // a CTA-iteration costs about the same at either width, so the
+            // cost of an item is its channel's
+            (second ? work2 : work).push_back({B->cost[b], make_int2(b, c | (W << 24))});
+            (second ? cost2 : cost1) += B->cost[b];
+        }
+        (second ? m_elems2 : m_elems) = std::max(second ? m_elems2 : m_elems, W * (B->Ntp_of[b] + 4));
     }
-    std::stable_sort(work.begin(), work.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
-    std::vector<int2> witems(work.size());
-    for (size_t w = 0; w < work.size(); ++w) witems[w] = work[w].second;
+    if (work.empty()) {  // every channel is narrower than J: one launch at that width
+        work.swap(work2);
+        m_elems = m_elems2;
+        J = 4;
+        cost1 = cost2;
+        cost2 = 0.0;
+    }
+    auto sorted_items = [](std::vector<std::pair<double, int2>>& w) {
+        std::stable_sort(w.begin(), w.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+        std::vector<int2> out(w.size());
+        for (size_t i = 0; i < w.size(); ++i) out[i] = w[i].second;
+        return out;
+    };
+    std::vector<int2> witems = sorted_items(work), witems2 = sorted_items(work2);
     if (B->d_items) cudaFree(B->d_items);
     B->d_items = nullptr;
+    if (B->d_items2) cudaFree(B->d_items2);
+    B->d_items2 = nullptr;
+    B->n_items2 = 0;
     cudaError_t e = upload(&B->d_items, witems, st);
     if (e != cudaSuccess) return e;
+    if (!witems2.empty()) {
+        e = upload(&B->d_items2, witems2, st);
+        if (e == cudaSuccess && !B->aux) e = cudaStreamCreateWithFlags(&B->aux, cudaStreamNonBlocking);
+        if (e == cudaSuccess && !B->ev_fork) e = cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess && !B->ev_join) e = cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming);
+        if (e != cudaSuccess) return e;
+        B->n_items2 = (int)witems2.size();
+        B->m_elems2 = m_elems2;
+        B->smem2 = kz_smem_ahk_tc(4, m_elems2, B->Ntp_max, B->K_max);
+    }
     B->J = J;
     B->nw = nw;
     B->kernel = kernel;
@@ -233,6 +278,15 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
         occ = std::max(1, occupancy_for(B->algo, J, nw, B->smem, B->prec));
     }
     B->grid = std::min(B->n_items, sms * occ);
+    if (B->n_items2) {
+        // both launches get the whole GPU: the narrow one (the widest channels,
+        // the longest items) is issued first and holds every SM; CTAs of the
+        // second start on the SMs it releases, so its work fills the first's tail
+        const int occ2 = std::max(1, kz_occupancy_ahk_tc(4, nw, B->smem2));
+        B->grid2 = std::min(B->n_items2, sms * occ2);
+    }
+    (void)cost1;
+    (void)cost2;
     return cudaSuccess;
 }
 
@@ -705,7 +759,7 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
     B->h_insts = insts;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(&B->d_insts, insts, st);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, 2 * sizeof(int));
     if (e == cudaSuccess) e = batch_layout(B, B->J, B->nw, sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) {
@@ -789,14 +843,34 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.tc = (B->kernel == KZ_KERNEL_TC);
     L.m_elems = L.tc ? B->m_elems : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    cudaError_t e = cudaMemsetAsync(B->d_queue, 0, sizeof(int), st);
+    cudaError_t e = cudaMemsetAsync(B->d_queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
+    if (B->n_items2) {  // fork: the narrow items run on the auxiliary stream
+        e = cudaEventRecord(B->ev_fork, st);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(B->aux, B->ev_fork, 0);
+        if (e != cudaSuccess) return check_launch(e, "kz_precode_batched fork");
+    }
+    if (B->n_items2) {  // the narrow items first, on the auxiliary stream
+        KzLaunch L2 = L;
+        L2.items = B->d_items2;
+        L2.n_items = B->n_items2;
+        L2.queue = B->d_queue + 1;
+        L2.m_elems = B->m_elems2;
+        e = kz_launch_ahk(L2, 4, B->nw, B->grid2, B->smem2, B->aux);
+        if (e == cudaSuccess) e = cudaEventRecord(B->ev_join, B->aux);
+        if (e != cudaSuccess) return check_launch(e, "kz_precode_batched second launch");
+    }
     if (B->kernel == KZ_KERNEL_DUAL)
         e = kz_launch_dual(L, B->J, B->nw, B->grid, B->smem, st);
     else
         e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
                                    : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
-    return check_launch(e, "kz_precode_batched launch");
+    if (e != cudaSuccess) return check_launch(e, "kz_precode_batched launch");
+    if (B->n_items2) {
+        e = cudaStreamWaitEvent(st, B->ev_join, 0);  // join
+        if (e != cudaSuccess) return check_launch(e, "kz_precode_batched join");
+    }
+    return KZ_OK;
 }
 
 void kz_batch_destroy(kz_batch* batch) { delete batch; }

@@ -182,3 +182,35 @@ def test_tc_mixed_widths(kp):
         assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X)
         assert np.all(orz.rel_err(it["v"].cpu().numpy().T, V) <= TOL_X)
         assert np.all(it["resid"].cpu().numpy() <= 1e-6 * (1 + 1e-6))
+
+
+def test_tc_mixed_widths_graph_replay(kp):
+    """The two launches of a mixed-width batch (forked onto an auxiliary
+    stream and joined back) are captured into one CUDA graph."""
+    insts = [kzgen.make_instance(710 + i, K, Nt, vr_frac_range=(0.1, 0.4), nrhs=16)
+             for i, (K, Nt) in enumerate([(150, 4096), (40, 1024), (90, 2048), (60, 4096)])]
+    items = []
+    for inst in insts:
+        p = kp.plan_from_instance(inst)
+        items.append(dict(plan=p, s=kp.rhs_tensor(inst.S),
+                          x=torch.empty((16, inst.Nt), dtype=torch.complex64, device="cuda"),
+                          v=None, iters=torch.empty(16, dtype=torch.int32, device="cuda"),
+                          resid=torch.empty(16, dtype=torch.float64, device="cuda"), xi=inst.xi))
+    b = kp.kz_batch_prepare(items, 16, "vr_oahk")
+    kp.kz_batch_set_launch(b, "tc", 8, 512)
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        kp.kz_precode_batched(b, "paper", 1e-6, 3000, 0, status=st)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        kp.kz_precode_batched(b, "paper", 1e-6, 3000, 0, status=st)
+    for it in items:
+        it["x"].zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    for inst, it in zip(insts, items):
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X)
