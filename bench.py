@@ -60,7 +60,7 @@ def workload_desc():
             "K in U{32..256}, VR round(U[0.1,0.4]*Nt), 16 QPSK RHS each, SNR 10 dB (xi = K/10), complex64")
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--configs", action="store_true",
                     help="measure the other workloads (configs 1, 2, 4, 5) instead of the benchmark line")
-    return ap.parse_args()
+    return ap.parse_args(argv)
 
 
 # ----------------------------------------------------------------------------- clocks
@@ -149,6 +149,27 @@ def oracle_sample_rate(insts, seconds, start=0):
     return done / el, f"{len(names)} whole instances ({done} columns) of the batch, first index {start}, {el:.1f} s"
 
 
+def shard(rank, n):
+    """Instance numbers solved by ``rank``: n per rank, disjoint across ranks
+    (weak scaling; channels are independent, so no data-path collective)."""
+    return list(range(rank * n, rank * n + n))
+
+
+def max_over_ranks(ms, dist=None, device="cpu"):
+    """The slowest rank's time (every rank calls this after the timed region)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(n_per_rank, world, ms_per_step):
+    """Precoders of all ranks per second of the slowest rank's step."""
+    return n_per_rank * NRHS * world / (ms_per_step / 1000.0)
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -196,7 +217,7 @@ def run_ours(args):
 
     # CPU baseline first (before heavy GPU work; single process, no pool)
     gen_t0 = time.perf_counter()
-    insts = [kzgen.config3_instance(rank * args.instances + i) for i in range(args.instances)]
+    insts = [kzgen.config3_instance(i) for i in shard(rank, args.instances)]
     gen_s = time.perf_counter() - gen_t0
     cpu = None
     if rank == 0:
@@ -254,14 +275,9 @@ def run_ours(args):
     if dist:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(sum(step_ms), dist, dev)
     ms_per_step = total_ms / args.steps
-    precoders = args.instances * NRHS * world
-    value = precoders / (ms_per_step / 1000.0)
+    value = whole_job_rate(args.instances, world, ms_per_step)
 
     # ---- results of the last replay: iterations and verification
     st = int(status.item())
