@@ -48,6 +48,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     __shared__ float s_tot[3 * J];
     __shared__ double s_partd[NW][J];
     __shared__ double s_sn2[J];
+    __shared__ float s_sn2f[J];  // ||s_j||^2 tol^2 for the tentative test
+    __shared__ double s_rn2[J];
     __shared__ float s_gamma[J];
     __shared__ int s_iters[J];
     __shared__ int s_wait[J];  // iterations a column spent waiting for its confirmation
@@ -92,7 +94,6 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     int* tcost_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
     int* wlist_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
     __shared__ int s_wptr[NW + 1];
-    const float tol2 = (float)(L.tol * L.tol);
     const bool oahk = (L.algo == ALGO_OAHK);
 
     int static_item = blockIdx.x;
@@ -120,6 +121,81 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         const int col0 = KZ_ITEM_COL(it.y), ncols = min(W, I.ld - col0);
         const float xi = I.xi;
         const int4* trow4 = I.trow4;
+        // True residual s - H H^H q - xi q of every row: per-warp sums of |r|^2
+        // per column into s_partd; with store_b also the correction right-hand
+        // side b = s - H H^H q.  In correction form through the Gram matrix on
+        // the overlap pattern (one pass over each row's overlap set, not its
+        // VR); in MODE 0 through the iterate m = H^H q just recomputed in m_s,
+        // the quantity the iteration itself carries (on ill-conditioned
+        // channels the two FP32 routes differ near 1e-7).  Four or eight
+        // columns: two rows per warp at a time and a compensated
+        // reduce-scatter, the s entries each lane needs fetched first.
+        auto true_residual_pass = [&](bool store_b) {
+            if constexpr (CORR) {
+                // one row per warp; lanes j < J own column j (its s entry is
+                // fetched before the row's sums)
+                float rpl = 0.f;
+                const int j = lane % J;
+                for (int i = warp; i < K; i += NW) {
+                    const bool mine = lane < J && j < ncols;
+                    const float2 sv = mine ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
+                    float2 hi, lo;
+                    gram_row_t<J>(I, i, q_s, W, hi, lo);
+                    if (lane < J) {
+                        const float2 r = true_resid(sv, hi, lo, q_s[i * J + j], xi);
+                        rpl += r.x * r.x + r.y * r.y;
+                        if (store_b) b_s[i * J + j] = make_float2((sv.x - hi.x) - lo.x, (sv.y - hi.y) - lo.y);
+                    }
+                }
+                if (lane < J) s_partd[warp][lane] = rpl;
+            } else if constexpr (J >= 4) {
+                constexpr int LPV = 32 / (4 * J);
+                const int idx = lane / LPV;
+                const int mw = idx / (2 * J), mj = (idx % (2 * J)) / 2;
+                const bool slot = (idx % 2 == 0) && (lane % LPV == 0);
+                float rpl = 0.f;
+                for (int k = warp; k < K; k += 2 * NW) {
+                    const int i0 = k, i1 = (k + NW < K) ? k + NW : -1;
+                    const int i = mw ? i1 : i0;
+                    const bool mine = slot && i >= 0;
+                    const float2 sv = (mine && mj < ncols) ? I.s[(size_t)(col0 + mj) * K + i] : make_float2(0.f, 0.f);
+                    float2 hi, lo;
+                    int which, jj;
+                    bool own;
+                    row_dot_c2<J>(I, rows_s, rptr_s, i0, i1, m_s, MS, W, hi, lo, which, jj, own);
+                    if (mine) {
+                        const float2 r = true_resid(sv, hi, lo, q_s[i * J + mj], xi);
+                        rpl += r.x * r.x + r.y * r.y;
+                        if (store_b) b_s[i * J + mj] = make_float2((sv.x - hi.x) - lo.x, (sv.y - hi.y) - lo.y);
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < J; ++j) {
+                    const float t = warp_sum(mj == j ? rpl : 0.f);
+                    if (lane == 0) s_partd[warp][j] = t;
+                }
+            } else {
+                float rp[J];
+#pragma unroll
+                for (int j = 0; j < J; ++j) rp[j] = 0.f;
+                for (int i = warp; i < K; i += NW) {
+                    float2 hi[J], lo[J];
+                    row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo, W);
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
+                        const float2 r = true_resid(sv, hi[j], lo[j], q_s[i * J + j], xi);
+                        rp[j] += r.x * r.x + r.y * r.y;
+                        if (store_b && lane == 0)
+                            b_s[i * J + j] = make_float2((sv.x - hi[j].x) - lo[j].x, (sv.y - hi[j].y) - lo[j].y);
+                    }
+                }
+                if (lane == 0) {
+#pragma unroll
+                    for (int j = 0; j < J; ++j) s_partd[warp][j] = rp[j];
+                }
+            }
+        };
 
         // ---- initialise: m = 0, q = 0, b = s, d = ||h||^2 + xi
         for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
@@ -195,7 +271,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 a += (double)v.x * v.x + (double)v.y * v.y;
             }
             a = warp_sum_d(a);
-            if (lane == 0) s_sn2[warp] = a;
+            if (lane == 0) {
+                s_sn2[warp] = a;
+                s_sn2f[warp] = (float)(a * L.tol * L.tol);
+            }
         }
         __syncthreads();
         if (tid == 0) {
@@ -356,7 +435,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         a2 &= ~(1 << j);
                         s_iters[j] = t - s_wait[j];
                         kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
-                    } else if ((double)rn2 <= (double)tol2 * s_sn2[j]) {
+                    } else if (rn2 <= s_sn2f[j]) {
                         pend |= 1 << j;
                     } else if (!oahk && t >= L.max_iter) {
                         a2 &= ~(1 << j);  // AHK: t steps done and still above tol
@@ -369,46 +448,34 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             __syncthreads();
             // ---------------- confirmation: m = H^H q from the complex64 H, the
             // true residual s - H m - xi q with compensated sums, and the test
-            // again.  In BF16_MIXED this is also the periodic refresh that sets
-            // the correction right-hand side b = s - H m and restarts m at 0.
-            // the true residual is recomputed (and, in correction form, b with
-            // it): at once for a tentative stop in MODE 0; in correction form
-            // when every active column waits, at the refresh period, or at the
-            // last iteration
+            // again; in correction form also the refresh that sets b = s - H m
+            // and restarts m at 0.  At once for a tentative stop in MODE 0; in
+            // correction form when every active column waits, at the refresh
+            // period, or at the last iteration.
             const bool last = t >= L.max_iter;
             if ((!CORR && s_pending) ||
                 (CORR && ((s_pending && (s_pending == s_active || last)) || since_refresh >= L.refresh))) {
                 since_refresh = 0;
-                for (int tile = warp; tile < I.ntiles; tile += NW) {
-                    float2 u0[J], u1[J];
-                    tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
-                    const int n = tile * KZ_TILE + 2 * lane;
+                if (!CORR) {  // the iterate itself restarts from m = H^H q (drift correction)
+                    for (int tile = warp; tile < I.ntiles; tile += NW) {
+                        float2 u0[J], u1[J];
+                        tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
+                        const int n = tile * KZ_TILE + 2 * lane;
 #pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        if (j >= W) continue;
-                        m_s[j * MS + n] = u0[j];
-                        m_s[j * MS + n + 1] = u1[j];
+                        for (int j = 0; j < J; ++j) {
+                            if (j >= W) continue;
+                            m_s[j * MS + n] = u0[j];
+                            m_s[j * MS + n + 1] = u1[j];
+                        }
                     }
                 }
                 __syncthreads();
-                float rp[J];
-#pragma unroll
-                for (int j = 0; j < J; ++j) rp[j] = 0.f;
-                for (int i = warp; i < K; i += NW) {
-                    float2 hi[J], lo[J];
-                    row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo, W);
-#pragma unroll
-                    for (int j = 0; j < J; ++j) {
-                        const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
-                        const float2 r = true_resid(sv, hi[j], lo[j], q_s[i * J + j], xi);
-                        rp[j] += r.x * r.x + r.y * r.y;
-                        if (CORR && lane == 0)
-                            b_s[i * J + j] = make_float2((sv.x - hi[j].x) - lo[j].x, (sv.y - hi[j].y) - lo[j].y);
-                    }
-                }
-                if (lane == 0) {
-#pragma unroll
-                    for (int j = 0; j < J; ++j) s_partd[warp][j] = rp[j];
+                true_residual_pass(CORR);
+                __syncthreads();
+                if (tid < J) {  // the columns' squared residual norms, one thread each
+                    double a = 0.0;
+                    for (int w = 0; w < NW; ++w) a += s_partd[w][tid];
+                    s_rn2[tid] = a;
                 }
                 __syncthreads();
                 if (tid == 0) {
@@ -416,8 +483,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int tested = CORR ? a2 : s_pending;
                     for (int j = 0; j < ncols; ++j) {
                         if (!((tested >> j) & 1) || !((a2 >> j) & 1)) continue;
-                        double rn2 = 0.0;
-                        for (int w = 0; w < NW; ++w) rn2 += s_partd[w][j];
+                        const double rn2 = s_rn2[j];
                         if (!(rn2 == rn2) || isinf(rn2)) {
                             a2 &= ~(1 << j);
                             s_iters[j] = t - s_wait[j];
@@ -530,26 +596,32 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 }
                 __syncthreads();
                 // ---------------- m += gamma u ; q_V += gamma phi_V
+                // (u of all J columns of a tile read before any is applied)
                 for (int tile = warp; tile < I.ntiles; tile += NW) {
                     const int k0 = tptr_s[tile];
                     const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                     if (k0 == k1) continue;
                     const int n = tile * KZ_TILE + 2 * lane;
+                    float2 ua[J], ub[J];
+#pragma unroll
+                    for (int j = 0; j < J; ++j) {
+                        const float2* xc = I.x + (size_t)(col0 + j) * Nt;
+                        const bool on = j < ncols && s_gamma[j] != 0.f;
+                        ua[j] = (on && n < Nt) ? xc[n] : make_float2(0.f, 0.f);
+                        ub[j] = (on && n + 1 < Nt) ? xc[n + 1] : make_float2(0.f, 0.f);
+                    }
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float g = s_gamma[j];
                         if (j < ncols && g != 0.f) {
-                            const float2* xc = I.x + (size_t)(col0 + j) * Nt;
                             float2* mp = m_s + j * MS + n;
                             if (n < Nt) {
-                                const float2 u = xc[n];
-                                mp[0].x = fmaf(g, u.x, mp[0].x);
-                                mp[0].y = fmaf(g, u.y, mp[0].y);
+                                mp[0].x = fmaf(g, ua[j].x, mp[0].x);
+                                mp[0].y = fmaf(g, ua[j].y, mp[0].y);
                             }
                             if (n + 1 < Nt) {
-                                const float2 u = xc[n + 1];
-                                mp[1].x = fmaf(g, u.x, mp[1].x);
-                                mp[1].y = fmaf(g, u.y, mp[1].y);
+                                mp[1].x = fmaf(g, ub[j].x, mp[1].x);
+                                mp[1].y = fmaf(g, ub[j].y, mp[1].y);
                             }
                         }
                     }
@@ -605,25 +677,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             }
         }
         __syncthreads();
-        {
-            float rp[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) rp[j] = 0.f;
-            for (int i = warp; i < K; i += NW) {
-                float2 hi[J], lo[J];
-                row_dot_c<J>(I, rows_s, rptr_s, i, m_s, MS, hi, lo, W);
-#pragma unroll
-                for (int j = 0; j < J; ++j) {
-                    const float2 sv = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
-                    const float2 r = true_resid(sv, hi[j], lo[j], q_s[i * J + j], xi);
-                    rp[j] += r.x * r.x + r.y * r.y;
-                }
-            }
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < J; ++j) s_partd[warp][j] = rp[j];
-            }
-        }
+        true_residual_pass(false);
         for (int j = 0; j < ncols; ++j) {
             float2* xc = I.x + (size_t)(col0 + j) * Nt;
             for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * MS + n];

@@ -68,6 +68,7 @@ struct kz_plan {
     int* d_tnv = nullptr;
     int4* d_trow4 = nullptr;
     int* d_vsort = nullptr;
+    float2* d_G = nullptr;  // H H^H on the X_k pattern
     float2* d_Hc = nullptr;
     __nv_bfloat162* d_Hb = nullptr;
     float2* d_scratch = nullptr;  // adjoint right-hand side G~ (grown on demand)
@@ -76,7 +77,7 @@ struct kz_plan {
 
     ~kz_plan() {
         void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
-                      d_tptr, d_tnv, d_trow4, d_vsort, d_Hc, d_Hb, d_scratch};
+                      d_tptr, d_tnv, d_trow4, d_vsort, d_G, d_Hc, d_Hb, d_scratch};
         for (void* p : ps)
             if (p) cudaFree(p);
     }
@@ -103,6 +104,7 @@ struct kz_plan {
         I.nrmd = d_nrmd;
         I.in_off = d_in_off;
         I.vsort = d_vsort;
+        I.G = d_G;
         I.cmax = cmax;
         return I;
     }
@@ -483,6 +485,8 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     KZ_TRY(kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, K, acc, P->d_Hc,
                         P->d_Hb, st));
     KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, st));
+    KZ_TRY(cudaMalloc((void**)&P->d_G, std::max<size_t>(P->xidx.size(), 1) * sizeof(float2)));
+    KZ_TRY(kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, K, P->d_G, st));
     KZ_TRY(cudaStreamSynchronize(st));
 #undef KZ_TRY
     *out = P;
@@ -499,6 +503,7 @@ kz_status kz_plan_update(kz_plan* P, const kz_cf32* H_packed, void* stream) {
     cudaError_t e = kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, P->K,
                                  P->total2, P->d_Hc, P->d_Hb, st);
     if (e == cudaSuccess) e = kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, P->K, P->d_nrmd, P->d_nrm, st);
+    if (e == cudaSuccess) e = kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, P->K, P->d_G, st);
     return check_launch(e, "kz_plan_update");
 }
 

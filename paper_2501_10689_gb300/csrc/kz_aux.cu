@@ -44,6 +44,34 @@ __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __re
     }
 }
 
+// Entries of the Gram matrix G = H H^H on the pattern of the overlap sets
+// (G_kl is zero when the VRs of k and l are disjoint, Lemma 1): entry e of
+// row k's CSR list (l = xidx[e]) gets sum over the overlap of the two VRs of
+// H[k, n] conj(H[l, n]), summed in FP64 and rounded once.  One block per row,
+// one warp per entry.
+__global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows, const int* __restrict__ rptr,
+                            const int* __restrict__ xptr, const int* __restrict__ xidx, float2* __restrict__ G) {
+    const int k = blockIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int4 rk = rows[k];
+    const float2* hk = Hc + rptr[k] - rk.x;
+    for (int e = xptr[k] + warp; e < xptr[k + 1]; e += nw) {
+        const int l = xidx[e];
+        const int4 rl = rows[l];
+        const float2* hl = Hc + rptr[l] - rl.x;
+        const int lo = max(rk.z, rl.z), hi = min(rk.w, rl.w);
+        double ax = 0.0, ay = 0.0;
+        for (int n = lo + lane; n < hi; n += 32) {
+            const float2 a = hk[n], b = hl[n];  // a conj(b)
+            ax += (double)a.x * b.x + (double)a.y * b.y;
+            ay += (double)a.y * b.x - (double)a.x * b.y;
+        }
+        ax = warp_sum_d(ax);
+        ay = warp_sum_d(ay);
+        if (lane == 0) G[e] = make_float2((float)ax, (float)ay);
+    }
+}
+
 // Gt[:, j] = G_Q[:, j] + H G_X[:, j]   (one block per row, one warp per column).
 __global__ void adjoint_rhs_kernel(const __grid_constant__ KzInst I, int nrhs, const float2* __restrict__ G_Q,
                                    const float2* __restrict__ G_X, float2* __restrict__ Gt) {
@@ -317,6 +345,12 @@ cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows,
 cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d, float* out_f,
                          cudaStream_t st) {
     row_norms_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, out_d, out_f);
+    return cudaGetLastError();
+}
+
+cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
+                    float2* G, cudaStream_t st) {
+    gram_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, xptr, xidx, G);
     return cudaGetLastError();
 }
 

@@ -66,10 +66,11 @@ __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const
     const int lane = threadIdx.x & 31;
     const int4 rd = rows[i];
     const int base = rptr[i];
+    const int pend = rd.y;
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
     int p = 2 * lane;
-    for (; p + 192 < rd.y; p += 256) {
+    for (; p + 192 < pend; p += 256) {
         float4 h[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) h[u] = h_pair<BF16>(I, base + p + 64 * u);
@@ -84,7 +85,7 @@ __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const
             }
         }
     }
-    for (; p < rd.y; p += 64) {
+    for (; p < pend; p += 64) {
         const float4 h = h_pair<BF16>(I, base + p);
         const int n = rd.x + p;
 #pragma unroll
@@ -218,6 +219,163 @@ __device__ __forceinline__ void row_dot_c(const KzInst& I, const int4* rows, con
     }
 }
 
+// Compensated reduce-scatter of NV (a power of two, 2 <= NV <= 32) per-lane
+// values: on return lane l holds in hi + lo the sum over the 32 lanes of
+// value l / (32 / NV).  Each level halves the values a lane keeps (its half
+// chosen by one lane bit) and adds the partner's copy of that half with
+// TwoSum, carrying the rounding errors in the compensation terms; the last
+// levels add the single remaining value.  Partners add in the same order, so
+// both hold identical sums.  NV - 1 shuffle pairs instead of 5 NV.
+template <int NV>
+__device__ __forceinline__ void warp_rs_c(float (&v)[NV], float& hi, float& lo) {
+    const int lane = threadIdx.x & 31;
+    float c[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) c[k] = 0.f;
+#pragma unroll
+    for (int n = NV, o = 16; n > 1; n >>= 1, o >>= 1) {
+        const bool upper = lane & o;
+#pragma unroll
+        for (int k = 0; k < n / 2; ++k) {
+            const float sh = upper ? v[k] : v[k + n / 2], sc = upper ? c[k] : c[k + n / 2];
+            const float kh = upper ? v[k + n / 2] : v[k], kc = upper ? c[k + n / 2] : c[k];
+            const float rh = __shfl_xor_sync(KZ_FULL, sh, o), rc = __shfl_xor_sync(KZ_FULL, sc, o);
+            float e;
+            two_sum(kh, rh, v[k], e);
+            c[k] = (kc + rc) + e;
+        }
+    }
+    float sv = v[0], cv = c[0];
+#pragma unroll
+    for (int o = 16 / NV; o > 0; o >>= 1) {
+        const float rh = __shfl_xor_sync(KZ_FULL, sv, o), rc = __shfl_xor_sync(KZ_FULL, cv, o);
+        float e;
+        two_sum(sv, rh, sv, e);
+        cv = (cv + rc) + e;
+    }
+    hi = sv;
+    lo = cv;
+}
+
+// True-residual products of two rows at once (i1 < 0: row i0 only), J = 4 or
+// 8 columns: FP32 lane sums of both rows (four antenna pairs per row in
+// flight), then one compensated reduce-scatter of the 4 J values.  The lane
+// with own = true holds row `which` (0: i0, 1: i1), column j: hi + lo = h . m_j
+// (each (row, column) has exactly one owner).  Columns j >= jn read nothing.
+template <int J>
+__device__ __forceinline__ void row_dot_c2(const KzInst& I, const int4* rows, const int* rptr, int i0, int i1,
+                                           const float2* __restrict__ m_s, int Ntp, int jn, float2& hi, float2& lo,
+                                           int& which, int& j, bool& own) {
+    static_assert(J == 4 || J == 8, "row_dot_c2 takes 4 or 8 columns");
+    constexpr int NV = 4 * J;        // (row, column, re / im)
+    constexpr int LPV = 32 / NV;     // lanes holding each value after the scatter
+    const int lane = threadIdx.x & 31;
+    const int4 r0 = rows[i0];
+    const int b0 = rptr[i0];
+    int4 r1 = make_int4(0, 0, 0, 0);
+    int b1 = 0;
+    if (i1 >= 0) {
+        r1 = rows[i1];
+        b1 = rptr[i1];
+    }
+    float2 acc0[J], acc1[J];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) acc0[jj] = acc1[jj] = make_float2(0.f, 0.f);
+    const int len = max(r0.y, r1.y);
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int p = 2 * lane; p < len; p += 256) {
+        float4 h0[4], h1[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = p + 64 * u;
+            h0[u] = (q < r0.y) ? h_pair<false>(I, b0 + q) : z4;
+            h1[u] = (q < r1.y) ? h_pair<false>(I, b1 + q) : z4;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = p + 64 * u;
+#pragma unroll
+            for (int jj = 0; jj < J; ++jj) {
+                if (jj >= jn) continue;
+                if (q < r0.y)
+                    cmac_pair<J, false>(h0[u], *reinterpret_cast<const float4*>(m_s + jj * Ntp + r0.x + q), acc0[jj]);
+                if (q < r1.y)
+                    cmac_pair<J, false>(h1[u], *reinterpret_cast<const float4*>(m_s + jj * Ntp + r1.x + q), acc1[jj]);
+            }
+        }
+    }
+    float v[NV];
+#pragma unroll
+    for (int jj = 0; jj < J; ++jj) {
+        v[2 * jj] = acc0[jj].x;
+        v[2 * jj + 1] = acc0[jj].y;
+        v[2 * J + 2 * jj] = acc1[jj].x;
+        v[2 * J + 2 * jj + 1] = acc1[jj].y;
+    }
+    float h, l;
+    warp_rs_c<NV>(v, h, l);
+    const int idx = lane / LPV;
+    // the imaginary part sits LPV lanes above the real part
+    const float him = __shfl_down_sync(KZ_FULL, h, LPV), lim = __shfl_down_sync(KZ_FULL, l, LPV);
+    hi = make_float2(h, him);
+    lo = make_float2(l, lim);
+    which = idx / (2 * J);
+    j = (idx % (2 * J)) / 2;
+    own = (idx % 2 == 0) && (lane % LPV == 0) && (which == 0 || i1 >= 0);
+}
+
+// (H H^H q)_i = sum over l in X_i of G_il q_l through the Gram matrix on the
+// overlap pattern (the VRs of rows outside X_i are disjoint from row i's, so
+// their entries are zero): the same sum as h_i . (H^H q) from one pass over
+// the row's overlap set instead of its VR.  Lane (slot, j) = (lane / J,
+// lane % J) takes column j of every (32 / J)-th entry: the warp loads 32
+// entries (index and G value) at a time, coalesced, and hands them round by
+// shuffles, so the q reads of a pass hit consecutive shared-memory words.
+// FP32 complex products; the 32 / J lanes of a column are then added with
+// compensated sums.  Every lane returns hi + lo for its column j (columns
+// j >= jn are not read and return 0).
+template <int J>
+__device__ __forceinline__ void gram_row_t(const KzInst& I, int i, const float2* __restrict__ q_s, int jn,
+                                           float2& hi, float2& lo) {
+    constexpr int EPP = 32 / J;  // entries per pass
+    const int lane = threadIdx.x & 31, slot = lane / J, j = lane % J;
+    float ax = 0.f, ay = 0.f;
+    const int e0 = __ldg(I.xptr + i), e1 = __ldg(I.xptr + i + 1);
+    for (int base = e0; base < e1; base += 32) {
+        const int e = base + lane;
+        int l = 0;
+        float2 g = make_float2(0.f, 0.f);
+        if (e < e1) {
+            l = __ldg(I.xidx + e);
+            g = __ldg(I.G + e);
+        }
+#pragma unroll
+        for (int p = 0; p < J; ++p) {
+            const int src = p * EPP + slot;
+            const int ls = __shfl_sync(KZ_FULL, l, src);
+            const float gx = __shfl_sync(KZ_FULL, g.x, src), gy = __shfl_sync(KZ_FULL, g.y, src);
+            if (base + src < e1 && j < jn) {
+                const float2 q = q_s[ls * J + j];
+                ax = fmaf(gx, q.x, fmaf(-gy, q.y, ax));
+                ay = fmaf(gx, q.y, fmaf(gy, q.x, ay));
+            }
+        }
+    }
+    float cx = 0.f, cy = 0.f;
+#pragma unroll
+    for (int o = J; o < 32; o <<= 1) {
+        const float rx = __shfl_xor_sync(KZ_FULL, ax, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
+        const float ry = __shfl_xor_sync(KZ_FULL, ay, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
+        float e;
+        two_sum(ax, rx, ax, e);
+        cx = (cx + rcx) + e;
+        two_sum(ay, ry, ay, e);
+        cy = (cy + rcy) + e;
+    }
+    hi = make_float2(ax, ay);
+    lo = make_float2(cx, cy);
+}
+
 // b - h_i . m - xi q from row_dot_c's hi + lo: b - hi is exact when the two
 // nearly cancel, and xi q enters through one fused multiply-add.
 __device__ __forceinline__ float2 true_resid(float2 b, float2 hi, float2 lo, float2 q, float xi) {
@@ -233,8 +391,8 @@ __device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, cons
                                          int nlanes, int jn = J) {
     const int4 rd = rows[i];
     const int base = rptr[i];
-    for (int p = 2 * lane; p < rd.y; p += 2 * nlanes) {
-        const float4 h = h_pair<BF16>(I, base + p);
+    const int pend = rd.y;
+    auto apply = [&](const float4& h, int p) {
         const int n = rd.x + p;
         const bool in0 = (n >= rd.z) && (n < rd.w);
         const bool in1 = (n + 1 >= rd.z) && (n + 1 < rd.w);
@@ -255,7 +413,18 @@ __device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, cons
                 mp[1] = v;
             }
         }
+    };
+    const int step = 2 * nlanes;
+    int p = 2 * lane;
+    // four antenna pairs per lane in flight before they are applied
+    for (; p + 3 * step < pend; p += 4 * step) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = h_pair<BF16>(I, base + p + u * step);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) apply(h[u], p + u * step);
     }
+    for (; p < pend; p += step) apply(h_pair<BF16>(I, base + p), p);
 }
 
 // u[j] at antennas (n, n+1), n = 64 * tile + 2 * lane:

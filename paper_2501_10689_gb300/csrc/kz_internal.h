@@ -42,6 +42,7 @@ struct KzInst {
     const double* nrmd;        // ||h_k||^2 in FP64
     const int* in_off;         // row k's offset in the caller's packed layout
     const int* vsort;          // V rows (K - nF), then all K rows, each by VR centre
+    const float2* G;           // Gram matrix H H^H on the CSR pattern of X_k (FP64 sums, rounded)
     int cmax;                  // most rows covering one tile
     // --- call ---
     float xi;
@@ -95,6 +96,8 @@ cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows,
                          int64_t total2, float2* Hc, __nv_bfloat162* Hb, cudaStream_t st);
 cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d,
                          float* out_f, cudaStream_t st);
+cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
+                    float2* G, cudaStream_t st);
 cudaError_t kz_adjoint_rhs(const KzInst& I, int nrhs, const float2* G_Q, const float2* G_X, float2* Gt,
                            cudaStream_t st);
 cudaError_t kz_adjoint_contract(const KzInst& I, int nrhs, const float2* Q, const float2* X,
