@@ -69,30 +69,23 @@ __device__ __forceinline__ void row_dot(const KzInst& I, const int4* rows, const
     const int pend = rd.y;
 #pragma unroll
     for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
-    int p = 2 * lane;
-    for (; p + 192 < pend; p += 256) {
+    // four antenna pairs per lane per step, all loads issued first; the last
+    // step is predicated, so a short row costs one round trip to memory
+    for (int p = 2 * lane; p < pend; p += 256) {
         float4 h[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) h[u] = h_pair<BF16>(I, base + p + 64 * u);
+        for (int u = 0; u < 4; ++u)
+            h[u] = (p + 64 * u < pend) ? h_pair<BF16>(I, base + p + 64 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
         const int n = rd.x + p;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            if (p + 64 * u >= pend) continue;
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 if (j >= jn) continue;
                 const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n + 64 * u);
                 cmac_pair<J, BF16>(h[u], mm, acc[j]);
             }
-        }
-    }
-    for (; p < pend; p += 64) {
-        const float4 h = h_pair<BF16>(I, base + p);
-        const int n = rd.x + p;
-#pragma unroll
-        for (int j = 0; j < J; ++j) {
-            if (j >= jn) continue;
-            const float4 mm = *reinterpret_cast<const float4*>(m_s + j * Ntp + n);
-            cmac_pair<J, BF16>(h, mm, acc[j]);
         }
     }
 #pragma unroll
@@ -415,16 +408,17 @@ __device__ __forceinline__ void row_axpy(const KzInst& I, const int4* rows, cons
         }
     };
     const int step = 2 * nlanes;
-    int p = 2 * lane;
-    // four antenna pairs per lane in flight before they are applied
-    for (; p + 3 * step < pend; p += 4 * step) {
+    // four antenna pairs per lane in flight before they are applied; the last
+    // step is predicated
+    for (int p = 2 * lane; p < pend; p += 4 * step) {
         float4 h[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) h[u] = h_pair<BF16>(I, base + p + u * step);
+        for (int u = 0; u < 4; ++u)
+            h[u] = (p + u * step < pend) ? h_pair<BF16>(I, base + p + u * step) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) apply(h[u], p + u * step);
+        for (int u = 0; u < 4; ++u)
+            if (p + u * step < pend) apply(h[u], p + u * step);
     }
-    for (; p < pend; p += step) apply(h_pair<BF16>(I, base + p), p);
 }
 
 // u[j] at antennas (n, n+1), n = 64 * tile + 2 * lane:
