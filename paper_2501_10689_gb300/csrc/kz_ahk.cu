@@ -94,6 +94,12 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     int* tcost_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
     int* wlist_s = TC ? reinterpret_cast<int*>(carve((size_t)ntask_max * sizeof(int))) : nullptr;
     __shared__ int s_wptr[NW + 1];
+    // tensor-core aggregate: the row index of every covering-list entry of the
+    // channel, staged once per item (the intervals and offsets come from
+    // rows_s / rptr_s), so no list entry is read from L2 in the iteration
+    unsigned short* trow_s =
+        (TC && L.trow_max) ? reinterpret_cast<unsigned short*>(carve((size_t)L.trow_max * sizeof(unsigned short)))
+                           : nullptr;
     const bool oahk = (L.algo == ALGO_OAHK);
 
     int static_item = blockIdx.x;
@@ -220,6 +226,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         if (TC) {  // V rows by VR centre (all rows for AHK)
             const int* src = I.vsort + (oahk ? 0 : K - I.nF);
             for (int v = tid; v < K - nF; v += NT) vs_s[v] = src[v];
+            if (trow_s)
+                for (int e = tid; e < __ldg(I.tptr + I.ntiles); e += NT) trow_s[e] = (unsigned short)I.trow4[e].x;
         }
         __syncthreads();
         if (TC) {
@@ -522,7 +530,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                         if (k0 == k1) continue;
                         float acc[2][2][NB][4];
-                        tc_tile_aggr<J>(I.Hc, trow4, tile, part, k0, k1, p_s, acc);
+                        if (trow_s)
+                            tc_tile_aggr<J, true>(I.Hc, trow4, trow_s, rows_s, rptr_s, tile, part, k0, k1, p_s, acc);
+                        else
+                            tc_tile_aggr<J, false>(I.Hc, trow4, trow_s, rows_s, rptr_s, tile, part, k0, k1, p_s, acc);
                         // lane (g, c < 2) holds u at the antenna pair (n, n + 1)
                         // for columns j and j + 1: one 16-byte store per column
 #pragma unroll
@@ -779,12 +790,13 @@ size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
            r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int));
 }
 
-size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K) {
+size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow) {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t ntask = 2 * (size_t)((K + 7) / 8);
     return kz_smem_ahk(J, Ntp_max, K, KZ_C64) - r16((size_t)J * Ntp_max * sizeof(float2)) +
            r16((size_t)m_elems * sizeof(float2)) + r16((size_t)K * sizeof(int)) +
-           r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int));
+           r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int)) +
+           r16((size_t)trow * sizeof(unsigned short));
 }
 
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {

@@ -52,6 +52,7 @@ void kz_set_error(const char* fmt, ...) {
 struct kz_plan {
     int K = 0, Nt = 0, Ntp = 0, ntiles = 0, nF = 0;
     int cmax = 0;  // largest number of rows covering one tile
+    int n_trow = 0;  // covering-list entries over all tiles
     int64_t sumL = 0, total2 = 0;
     kz_prec prec = KZ_C64;
     std::vector<int> F, xptr, xidx;
@@ -114,6 +115,7 @@ struct kz_batch {
     int n = 0, nrhs = 0, J = 1, nw = 16, grid = 1, n_items = 0, Ntp_max = 0, K_max = 0;
     int kernel = KZ_KERNEL_RESIDENT, cs = 0, cmax = 0;
     int m_elems = 0;               // tensor-core kernel: shared iterate entries per CTA
+    int trow_max = 0, trow_max2 = 0;  // tensor-core kernel: staged covering-list entries (0: none)
     std::vector<int> Ntp_of;       // per instance
     std::vector<double> cost;  // per-instance work estimate (aligned entries + 4 Nt)
     size_t smem = 0;
@@ -202,6 +204,12 @@ cudaError_t batch_layout(kz_batch* B, int J, int nw, int sms, cudaStream_t st) {
 // Tensor-core kernel: the width (columns) of instance b's items, the largest
 // of J, J / 2, ... (at least 4) whose iterate columns fit shared memory next to
 // the widest other instance's; 0 if even 4 do not fit.
+// The covering lists' row indices are staged in shared memory when they fit
+// next to everything else (16-bit indices: K below 65536).
+bool tc_stage_ok(int J, int m_elems, int Ntp_max, int K_max, int trow) {
+    return trow > 0 && K_max < 65536 && kz_smem_ahk_tc(J, m_elems, Ntp_max, K_max, trow) <= kSmemLimit;
+}
+
 int tc_width(int J, int Ntp, int Ntp_max, int K_max) {
     for (int W = J; W >= 4; W /= 2)
         if (kz_smem_ahk_tc(J, W * (Ntp + 4), Ntp_max, K_max) <= kSmemLimit) return W;
@@ -212,7 +220,7 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
     // work items {instance, first column | width << 24} with a cost estimate;
     // tensor-core items narrower than J go to the second list
     std::vector<std::pair<double, int2>> work, work2;
-    int m_elems = 0, m_elems2 = 0;
+    int m_elems = 0, m_elems2 = 0, trow1 = 0, trow2 = 0;
     double cost1 = 0.0, cost2 = 0.0;
     for (int b = 0; b < B->n; ++b) {
         int W = J;
@@ -221,6 +229,7 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
             if (W == 0) return cudaErrorInvalidValue;
         }
         const bool second = (W < J);
+        if (kernel == KZ_KERNEL_TC) (second ? trow2 : trow1) = std::max(second ? trow2 : trow1, B->plans[b]->n_trow);
         for (int c = 0; c < B->nrhs; c += W) {
             // a CTA-iteration costs about the same at either width, so the
             // cost of an item is its channel's
@@ -232,6 +241,7 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
     if (work.empty()) {  // every channel is narrower than J: one launch at that width
         work.swap(work2);
         m_elems = m_elems2;
+        trow1 = trow2;
         J = 4;
         cost1 = cost2;
         cost2 = 0.0;
@@ -258,7 +268,8 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
         if (e != cudaSuccess) return e;
         B->n_items2 = (int)witems2.size();
         B->m_elems2 = m_elems2;
-        B->smem2 = kz_smem_ahk_tc(4, m_elems2, B->Ntp_max, B->K_max);
+        B->trow_max2 = tc_stage_ok(4, m_elems2, B->Ntp_max, B->K_max, trow2) ? trow2 : 0;
+        B->smem2 = kz_smem_ahk_tc(4, m_elems2, B->Ntp_max, B->K_max, B->trow_max2);
     }
     B->J = J;
     B->nw = nw;
@@ -272,7 +283,8 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
     } else if (kernel == KZ_KERNEL_TC) {
         B->cs = 0;
         B->m_elems = m_elems;
-        B->smem = kz_smem_ahk_tc(J, m_elems, B->Ntp_max, B->K_max);
+        B->trow_max = tc_stage_ok(J, m_elems, B->Ntp_max, B->K_max, trow1) ? trow1 : 0;
+        B->smem = kz_smem_ahk_tc(J, m_elems, B->Ntp_max, B->K_max, B->trow_max);
         occ = std::max(1, kz_occupancy_ahk_tc(J, nw, B->smem));
     } else {
         B->cs = 0;
@@ -457,6 +469,7 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
             for (int k : (pass == 0 ? tv[t] : tf[t])) trow4.push_back(make_int4(k, rptr[k] - rows[k].x, rows[k].x, rows[k].x + rows[k].y));
         tptr[t + 1] = (int)trow4.size();
     }
+    P->n_trow = (int)trow4.size();
 
     cudaError_t e = cudaSuccess;
 #define KZ_TRY(x)                                            \
@@ -614,7 +627,7 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
     }
-    int J, nw, cs = 0;
+    int J, nw, cs = 0, trow_single = 0;
     size_t smem;
     if (kernel == KZ_KERNEL_DUAL) {
         J = rhs_per_cta ? rhs_per_cta : (nrhs >= 16 && dual_cs(16, 16, plan->K, plan->cmax) ? 16 : 8);
@@ -633,7 +646,8 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
                                ? 8
                                : 4);
         nw = choose_nw(plan->Ntp);
-        smem = kz_smem_ahk_tc(J, J * (plan->Ntp + 4), plan->Ntp, plan->K);
+        trow_single = tc_stage_ok(J, J * (plan->Ntp + 4), plan->Ntp, plan->K, plan->n_trow) ? plan->n_trow : 0;
+        smem = kz_smem_ahk_tc(J, J * (plan->Ntp + 4), plan->Ntp, plan->K, trow_single);
     } else {
         J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
         nw = choose_nw(plan->Ntp);
@@ -676,6 +690,7 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         e = kz_launch_dual(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
     } else if (kernel == KZ_KERNEL_TC) {
         L.tc = 1;
+        L.trow_max = trow_single;
         const int occ = std::max(1, kz_occupancy_ahk_tc(J, nw, smem));
         e = kz_launch_ahk(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
     } else {
@@ -847,6 +862,7 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.cs = B->cs;
     L.tc = (B->kernel == KZ_KERNEL_TC);
     L.m_elems = L.tc ? B->m_elems : 0;
+    L.trow_max = L.tc ? B->trow_max : 0;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = cudaMemsetAsync(B->d_queue, 0, 2 * sizeof(int), st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched memset");
@@ -861,6 +877,7 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
         L2.n_items = B->n_items2;
         L2.queue = B->d_queue + 1;
         L2.m_elems = B->m_elems2;
+        L2.trow_max = B->trow_max2;
         e = kz_launch_ahk(L2, 4, B->nw, B->grid2, B->smem2, B->aux);
         if (e == cudaSuccess) e = cudaEventRecord(B->ev_join, B->aux);
         if (e != cudaSuccess) return check_launch(e, "kz_precode_batched second launch");

@@ -565,12 +565,15 @@ __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const
 // sums and differences give u (tc_u_combine).  coef: K x J phi in shared
 // memory.  Two chunks of eight rows per step (eight 16-byte loads of a lane
 // in flight before the MMAs).
-template <int J>
-__device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, const int4* __restrict__ trow4, int tile,
-                                             int part, int k0, int k1, const float2* __restrict__ coef,
+// STAGED: the entries' row indices come from trow_s and their intervals and
+// offsets from rows / rptr (shared memory) instead of trow4 (global).
+template <int J, bool STAGED>
+__device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, const int4* __restrict__ trow4,
+                                             const unsigned short* trow_s, const int4* rows, const int* rptr,
+                                             int tile, int part, int k0, int k1, const float2* __restrict__ coef,
                                              float (&acc)[2][2][J / 4][4]) {
     constexpr int NB = J / 4;
-    constexpr int KC = 2;
+    constexpr int KC = (J == 4) ? 3 : 2;  // chunks of eight rows per step
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
 #pragma unroll
     for (int sp = 0; sp < 2; ++sp)
@@ -584,14 +587,21 @@ __device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, cons
     const float2 z = make_float2(0.f, 0.f);
     const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     const int nbase = tile * KZ_TILE + 32 * part + 2 * g;
+    auto entry = [&](int kk) -> int4 {
+        if (kk >= k1) return none;
+        if constexpr (STAGED) {
+            const int r = trow_s[kk];
+            const int4 rd = rows[r];
+            return make_int4(r, rptr[r] - rd.x, rd.x, rd.x + rd.y);
+        } else {
+            return __ldg(trow4 + kk);
+        }
+    };
     int4 nxt[KC][2];
 #pragma unroll
     for (int q = 0; q < KC; ++q)
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int kk = k0 + 8 * q + 4 * h2 + c;
-            nxt[q][h2] = (kk < k1) ? __ldg(trow4 + kk) : none;
-        }
+        for (int h2 = 0; h2 < 2; ++h2) nxt[q][h2] = entry(k0 + 8 * q + 4 * h2 + c);
     for (int k = k0; k < k1; k += 8 * KC) {
         int4 e[KC][2];
 #pragma unroll
@@ -617,10 +627,7 @@ __device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, cons
 #pragma unroll
         for (int q = 0; q < KC; ++q)
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) {
-                const int kk = k + 8 * KC + 8 * q + 4 * h2 + c;
-                nxt[q][h2] = (kk < k1) ? __ldg(trow4 + kk) : none;
-            }
+            for (int h2 = 0; h2 < 2; ++h2) nxt[q][h2] = entry(k + 8 * KC + 8 * q + 4 * h2 + c);
 #pragma unroll
         for (int q = 0; q < KC; ++q) {
             const bool va = k + 8 * q + c < k1, vb = k + 8 * q + c + 4 < k1;

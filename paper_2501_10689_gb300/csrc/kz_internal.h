@@ -70,6 +70,7 @@ struct KzLaunch {
     int cs;               // dual kernel: staged rows per chunk
     int tc;               // resident kernel: tensor-core inner products (correction form)
     int m_elems;          // resident kernel: shared iterate entries per CTA (0: J x (Ntp_max + pad))
+    int trow_max;         // tensor-core kernel: covering-list entries staged in shared memory (0: none)
 };
 
 // Work item {instance, first column | (columns << 24)}: the column count of
@@ -83,8 +84,9 @@ cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t sm
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
-// Tensor-core mode: m_elems shared iterate entries (columns of Ntp + 4).
-size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K);
+// Tensor-core mode: m_elems shared iterate entries (columns of Ntp + 4) and
+// trow covering-list row indices staged as 16-bit entries.
+size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow = 0);
 int kz_occupancy_ahk_tc(int J, int nw, size_t smem);
 int kz_occupancy_kacz(int J, int nw, size_t smem);
 cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
