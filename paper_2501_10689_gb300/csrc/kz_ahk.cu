@@ -67,10 +67,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         off += (bytes + 15) & ~(size_t)15;
         return p;
     };
-    // iterate columns; the tensor-core mode pads each by 4 entries so the 8
-    // columns read by one MMA fragment fall in different banks
+    // iterate columns; the tensor-core mode pads each by KZ_TC_PAD entries so
+    // the columns read by one MMA fragment fall in different banks
     float2* m_s = reinterpret_cast<float2*>(
-        carve((L.m_elems ? (size_t)L.m_elems : (size_t)J * (L.Ntp_max + (TC ? 4 : 0))) * sizeof(float2)));
+        carve((L.m_elems ? (size_t)L.m_elems : (size_t)J * (L.Ntp_max + (TC ? KZ_TC_PAD : 0))) * sizeof(float2)));
     float2* b_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* q_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* p_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         __syncthreads();
         const KzInst& I = sI;
         const int K = I.K, Nt = I.Nt, Ntp = I.Ntp, nF = oahk ? I.nF : 0;
-        const int MS = TC ? Ntp + 4 : Ntp;  // column stride of m_s
+        const int MS = TC ? Ntp + KZ_TC_PAD : Ntp;  // column stride of m_s
         // an item may be narrower than J (W columns): a wide channel whose J
         // iterate columns would not fit shared memory
         const int W = KZ_ITEM_WIDTH(it.y, J);

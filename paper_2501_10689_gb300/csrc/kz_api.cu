@@ -212,7 +212,7 @@ bool tc_stage_ok(int J, int m_elems, int Ntp_max, int K_max, int trow) {
 
 int tc_width(int J, int Ntp, int Ntp_max, int K_max) {
     for (int W = J; W >= 4; W /= 2)
-        if (kz_smem_ahk_tc(J, W * (Ntp + 4), Ntp_max, K_max) <= kSmemLimit) return W;
+        if (kz_smem_ahk_tc(J, W * (Ntp + KZ_TC_PAD), Ntp_max, K_max) <= kSmemLimit) return W;
     return 0;
 }
 
@@ -236,7 +236,7 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
             (second ? work2 : work).push_back({B->cost[b], make_int2(b, c | (W << 24))});
             (second ? cost2 : cost1) += B->cost[b];
         }
-        (second ? m_elems2 : m_elems) = std::max(second ? m_elems2 : m_elems, W * (B->Ntp_of[b] + 4));
+        (second ? m_elems2 : m_elems) = std::max(second ? m_elems2 : m_elems, W * (B->Ntp_of[b] + KZ_TC_PAD));
     }
     if (work.empty()) {  // every channel is narrower than J: one launch at that width
         work.swap(work2);
@@ -642,12 +642,12 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         // 8 columns per CTA only when that still gives every SM a work item
         J = rhs_per_cta ? rhs_per_cta
                         : ((nrhs + 7) / 8 >= plan->sms &&
-                                   kz_smem_ahk_tc(8, 8 * (plan->Ntp + 4), plan->Ntp, plan->K) <= kSmemLimit
+                                   kz_smem_ahk_tc(8, 8 * (plan->Ntp + KZ_TC_PAD), plan->Ntp, plan->K) <= kSmemLimit
                                ? 8
                                : 4);
         nw = choose_nw(plan->Ntp);
-        trow_single = tc_stage_ok(J, J * (plan->Ntp + 4), plan->Ntp, plan->K, plan->n_trow) ? plan->n_trow : 0;
-        smem = kz_smem_ahk_tc(J, J * (plan->Ntp + 4), plan->Ntp, plan->K, trow_single);
+        trow_single = tc_stage_ok(J, J * (plan->Ntp + KZ_TC_PAD), plan->Ntp, plan->K, plan->n_trow) ? plan->n_trow : 0;
+        smem = kz_smem_ahk_tc(J, J * (plan->Ntp + KZ_TC_PAD), plan->Ntp, plan->K, trow_single);
     } else {
         J = rhs_per_cta ? rhs_per_cta : choose_J(algo, 1, plan->Ntp, plan->K, prec, plan->sms, nrhs);
         nw = choose_nw(plan->Ntp);

@@ -23,6 +23,9 @@
 #include "../../include/kzprecode.h"
 
 #define KZ_TILE 64
+// Tensor-core mode: padding of each iterate column in shared memory (entries),
+// so the columns one MMA fragment reads start 16 banks apart
+#define KZ_TC_PAD 8
 
 struct KzInst {
     // --- channel (fixed at plan creation) ---
@@ -84,7 +87,7 @@ cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t sm
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
-// Tensor-core mode: m_elems shared iterate entries (columns of Ntp + 4) and
+// Tensor-core mode: m_elems shared iterate entries (columns of Ntp + KZ_TC_PAD) and
 // trow covering-list row indices staged as 16-bit entries.
 size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow = 0);
 int kz_occupancy_ahk_tc(int J, int nw, size_t smem);
