@@ -158,7 +158,7 @@ bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_VR_OAHK; }
 // of BF16_MIXED and of the tensor-core kernel (whose TF32 inner products
 // slow the iteration when the correction grows for longer).
 int default_refresh(kz_algo a, kz_prec p, bool tc = false) {
-    if (is_ahk_family(a)) return tc ? 12 : (p == KZ_BF16_MIXED ? 6 : 16);
+    if (is_ahk_family(a)) return tc ? 8 : (p == KZ_BF16_MIXED ? 6 : 16);
     return 512;
 }
 
