@@ -46,9 +46,21 @@ __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __re
 
 // Entries of the Gram matrix G = H H^H on the pattern of the overlap sets
 // (G_kl is zero when the VRs of k and l are disjoint, Lemma 1): entry e of
-// row k's CSR list (l = xidx[e]) gets sum over the overlap of the two VRs of
-// H[k, n] conj(H[l, n]), summed in FP64 and rounded once.  One block per row,
-// one warp per entry.
+// row k's CSR list (l = xidx[e]) gets the sum over the overlap of the two VRs
+// of H[k, n] conj(H[l, n]).  Each lane sums its share with Ogita, Rump and
+// Oishi's Dot2 (error-free TwoProduct by FMA and TwoSum, errors carried in a
+// second word), the lanes' (sum, error) pairs are combined with compensated
+// additions, and the result is rounded once: about as accurate as an FP64
+// sum, on the FP32 units (GB300's FP64 rate is a small fraction of FP32).
+// One block per row, one warp per entry.
+__device__ __forceinline__ void dot2_add(float a, float b, float& s, float& c) {
+    const float p = a * b;
+    const float pe = fmaf(a, b, -p);  // a b = p + pe exactly
+    float e;
+    two_sum(s, p, s, e);
+    c += pe + e;
+}
+
 __global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows, const int* __restrict__ rptr,
                             const int* __restrict__ xptr, const int* __restrict__ xidx, float2* __restrict__ G) {
     const int k = blockIdx.x;
@@ -60,15 +72,24 @@ __global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restric
         const int4 rl = rows[l];
         const float2* hl = Hc + rptr[l] - rl.x;
         const int lo = max(rk.z, rl.z), hi = min(rk.w, rl.w);
-        double ax = 0.0, ay = 0.0;
+        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;  // a conj(b) = (ax bx + ay by) + i (ay bx - ax by)
         for (int n = lo + lane; n < hi; n += 32) {
-            const float2 a = hk[n], b = hl[n];  // a conj(b)
-            ax += (double)a.x * b.x + (double)a.y * b.y;
-            ay += (double)a.y * b.x - (double)a.x * b.y;
+            const float2 a = hk[n], b = hl[n];
+            dot2_add(a.x, b.x, sx, cx);
+            dot2_add(a.y, b.y, sx, cx);
+            dot2_add(a.y, b.x, sy, cy);
+            dot2_add(-a.x, b.y, sy, cy);
         }
-        ax = warp_sum_d(ax);
-        ay = warp_sum_d(ay);
-        if (lane == 0) G[e] = make_float2((float)ax, (float)ay);
+        for (int o = 16; o > 0; o >>= 1) {
+            const float rsx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
+            const float rsy = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
+            float t;
+            two_sum(sx, rsx, sx, t);
+            cx = (cx + rcx) + t;
+            two_sum(sy, rsy, sy, t);
+            cy = (cy + rcy) + t;
+        }
+        if (lane == 0) G[e] = make_float2(sx + cx, sy + cy);
     }
 }
 
