@@ -224,17 +224,28 @@ def run_ours(args):
         rate, sample = oracle_sample_rate(insts, args.cpu_seconds)
         cpu = {"value": rate, "unit": "precoders/s", "cores": 1, "kind": "oracle", "sample": sample}
 
+    # the batch's right-hand sides and outputs live in four contiguous device
+    # buffers (each item a view), so the end-to-end leg moves them with one
+    # copy per direction and buffer
     plans, items = [], []
-    S_host = []
-    for inst in insts:
+    n_s = sum(NRHS * inst.K for inst in insts)
+    n_x = sum(NRHS * inst.Nt for inst in insts)
+    S_all = torch.empty(n_s, dtype=torch.complex64, device=dev)
+    X_all = torch.empty(n_x, dtype=torch.complex64, device=dev)
+    V_all = torch.empty(n_s, dtype=torch.complex64, device=dev)
+    IT_all = torch.empty(len(insts) * NRHS, dtype=torch.int32, device=dev)
+    R_all = torch.empty(len(insts) * NRHS, dtype=torch.float64, device=dev)
+    os_, ox = 0, 0
+    for b, inst in enumerate(insts):
         p = kp.plan_from_instance(inst, device=dev)
         plans.append(p)
-        S = kp.rhs_tensor(inst.S, device=dev)
-        S_host.append(S)
-        items.append(dict(plan=p, s=S, x=torch.empty((NRHS, inst.Nt), dtype=torch.complex64, device=dev),
-                          v=torch.empty((NRHS, inst.K), dtype=torch.complex64, device=dev),
-                          iters=torch.empty(NRHS, dtype=torch.int32, device=dev),
-                          resid=torch.empty(NRHS, dtype=torch.float64, device=dev), xi=inst.xi))
+        S = S_all[os_:os_ + NRHS * inst.K].view(NRHS, inst.K)
+        S.copy_(kp.rhs_tensor(inst.S, device=dev))
+        items.append(dict(plan=p, s=S, x=X_all[ox:ox + NRHS * inst.Nt].view(NRHS, inst.Nt),
+                          v=V_all[os_:os_ + NRHS * inst.K].view(NRHS, inst.K),
+                          iters=IT_all[b * NRHS:(b + 1) * NRHS], resid=R_all[b * NRHS:(b + 1) * NRHS], xi=inst.xi))
+        os_ += NRHS * inst.K
+        ox += NRHS * inst.Nt
     batch = kp.kz_batch_prepare(items, NRHS, "vr_oahk",
                                 rhs_per_cta=args.rhs_per_cta if args.kernel == "resident" else 0)
     status = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -312,6 +323,7 @@ def run_ours(args):
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x clock under load
     launch_now = (tuned if tuned else (args.kernel, args.rhs_per_cta, args.threads))
+    launches_per_step = kp.kz_batch_query(batch)["launches"]
     traffic = None
     if kernel_sources_sha() == TRAFFIC["sources_sha256"] and args.instances == N_INST:
         traffic = TRAFFIC["bytes_per_launch"].get(tuple(launch_now))
@@ -321,8 +333,9 @@ def run_ours(args):
                 "traffic_note": "DRAM bytes per launch from ncu (one pass) on this workload and kernel build; "
                                 "null when the kernel sources or launch differ",
                 "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
-                "kernel": ("kz_ahk_kernel<J, 16 warps, tensor-core mode> (batched VR-OAHK; at J = 8 with a "
-                           "concurrent J = 4 launch for channels whose 8 iterate columns do not fit)" if tc
+                "kernel": (f"kz_ahk_kernel<J = {launch_now[1]}, {launch_now[2] // 32} warps, tensor-core mode> "
+                           f"(batched VR-OAHK; {launches_per_step} launch(es) per step: a second, concurrent "
+                           "J = 4 launch only for channels whose J iterate columns do not fit)" if tc
                            else "kz_ahk_kernel (batched VR-OAHK)"),
                 "alu_view": {"achieved_tflops": achieved_tflops, "fp32_fma_peak_tflops": alu_peak,
                              "frac": achieved_tflops / alu_peak}}
@@ -359,24 +372,25 @@ def run_ours(args):
                "vroahk_speedup": (args.instances * NRHS / (ms_per_step / 1000.0)) / (args.instances * NRHS / (gms / 1000.0))}
         del gbatch
 
-    # ---- end to end through the C-ABI with host buffers
-    S_pin = [torch.empty_like(s, device="cpu").pin_memory() for s in S_host]
-    X_pin = [torch.empty_like(it["x"], device="cpu").pin_memory() for it in items]
-    for sp, s in zip(S_pin, S_host):
-        sp.copy_(s.cpu())
-    h2d = sum(s.numel() * 8 for s in S_pin)
-    d2h = sum(x.numel() * 8 for x in X_pin) + sum(NRHS * (4 + 8) for _ in items)
+    # ---- end to end through the C-ABI with host buffers: every step copies
+    # the right-hand sides in from pinned host memory and x, iterations and
+    # residuals out (one copy per buffer)
+    S_pin = S_all.cpu().pin_memory()
+    X_pin = torch.empty(X_all.shape, dtype=X_all.dtype).pin_memory()
+    IT_pin = torch.empty(IT_all.shape, dtype=IT_all.dtype).pin_memory()
+    R_pin = torch.empty(R_all.shape, dtype=R_all.dtype).pin_memory()
+    h2d = S_pin.numel() * 8
+    d2h = X_pin.numel() * 8 + IT_pin.numel() * 4 + R_pin.numel() * 8
     e2e_ms = []
     with torch.cuda.stream(stream):
         for rep in range(2 + min(args.steps, 3)):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            for sp, s in zip(S_pin, S_host):
-                s.copy_(sp, non_blocking=True)
+            S_all.copy_(S_pin, non_blocking=True)
             launch()
-            for xp, it in zip(X_pin, items):
-                xp.copy_(it["x"], non_blocking=True)
-            it_h = [it["iters"].to("cpu", non_blocking=True) for it in items]
+            X_pin.copy_(X_all, non_blocking=True)
+            IT_pin.copy_(IT_all, non_blocking=True)
+            R_pin.copy_(R_all, non_blocking=True)
             b.record(stream)
             b.synchronize()
             if rep >= 2:
@@ -389,8 +403,9 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32+tf32" if tc else "f32", "data": "synthetic",
                 "precision": ("complex64 storage; TF32 tensor-core products with FP32 sums inside the "
-                              "correction-form iteration; FP32 refresh b = s - H m_ref, true residual and "
-                              "stopping test (compensated sums)" if tc else
+                              "correction-form iteration, the correction held in FP16 scaled per column; "
+                              "refresh b = s - H H^H q through the overlap-pattern Gram matrix, true residual "
+                              "and stopping test with compensated FP32 sums" if tc else
                               "complex64 storage, FP32 arithmetic; true residual with compensated sums"),
                 "config": {"workload": workload_desc(), "instances_per_gpu": args.instances, "nrhs": NRHS,
                            "tol": TOL, "max_iter": MAX_ITER,
@@ -400,7 +415,7 @@ def run_ours(args):
                                                      "threads": args.threads, "chosen_by": "command line"}),
                            "l2": "inputs larger than L2 (packed H of the batch is %.0f MB)" % (float(sumL.sum()) * 8 / 1e6),
                            "graph": "CUDA graph replay of queue reset + persistent kernel"},
-                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps,
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * launches_per_step,
                 "clocks": clocks, "grk": grk,
                 "verify": {"instances_checked": len(verify_idx), "max_rel_err_vs_fp64_rzf": max_err,
                            "bar": ERR_BAR, "ok": bool(max_err <= ERR_BAR), "status_word": st,

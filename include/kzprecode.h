@@ -200,9 +200,12 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
  * batch->n entries, free to reuse on return. */
 kz_status kz_batch_rebind(kz_batch* batch, const kz_batch_item* items, void* stream);
 
-/* Run a prepared batch: one kernel launch after a 4-byte memset of the
- * queue counter, no host synchronisation, so it can be captured in a CUDA
- * graph.  status as in kz_precode (may be NULL). */
+/* Run a prepared batch: one kernel launch after an 8-byte memset of the
+ * queue counters (two launches, the second on a stream forked from `stream`
+ * and joined back, when a tensor-core batch holds channels whose columns per
+ * CTA do not fit shared memory: those run at 4 columns), no host
+ * synchronisation, so it can be captured in a CUDA graph.  status as in
+ * kz_precode (may be NULL). */
 kz_status kz_precode_batched(kz_batch* batch, kz_select sel, double tol, int32_t max_iter,
                              uint64_t seed, int32_t refresh, int32_t* status, void* stream);
 
@@ -211,20 +214,28 @@ void kz_batch_destroy(kz_batch* batch);
 /* Autotune a prepared batch (step A8's launch shape): time every feasible
  * launch on the batch itself -- the RESIDENT kernel with columns-per-CTA in
  * {1, 2, 4, 8} and 256 or 512 threads, and for AHK / VR_OAHK on C64 the DUAL
- * kernel with 8 columns (256 or 512 threads) or 16 columns (512 threads) --
- * three runs each, the last two timed with CUDA events on `stream`; keep the
- * fastest and write it to chosen (host int32[3]: kernel, columns per CTA,
- * threads; may be NULL).  It solves the batch repeatedly, so the batch's
- * outputs hold a valid result afterwards.  Synchronous. */
+ * kernel with 8 columns (256 or 512 threads) or 16 columns (512 threads) and
+ * the TC kernel with 4 or 8 columns (256 or 512 threads) -- three runs each,
+ * the last two timed with CUDA events on `stream`; keep the fastest and write
+ * it to chosen (host int32[3]: kernel, columns per CTA, threads; may be
+ * NULL).  It solves the batch repeatedly, so the batch's outputs hold a
+ * valid result afterwards.  Synchronous. */
 kz_status kz_batch_tune(kz_batch* batch, kz_select sel, double tol, int32_t max_iter, uint64_t seed,
                         int32_t* chosen, void* stream);
 
-/* Fix a batch's launch: kernel (RESIDENT or DUAL), columns per CTA (RESIDENT:
- * 1, 2, 4, 8; DUAL: 8, 16) and threads (256 or 512; DUAL with 16 columns:
- * 512).  Rebuilds the work list; synchronous.  KZ_ERR_UNSUPPORTED if the
- * combination does not fit shared memory or the batch's method. */
+/* Fix a batch's launch: kernel (RESIDENT, DUAL or TC), columns per CTA
+ * (RESIDENT: 1, 2, 4, 8; DUAL: 8, 16; TC: 4, 8) and threads (256 or 512;
+ * DUAL with 16 columns: 512).  Rebuilds the work list; synchronous.
+ * KZ_ERR_UNSUPPORTED if the combination does not fit shared memory or the
+ * batch's method. */
 kz_status kz_batch_set_launch(kz_batch* batch, kz_kernel kernel, int32_t rhs_per_cta, int32_t threads,
                               void* stream);
+
+/* The launch a batch runs (host outputs, each may be NULL): kernel, columns
+ * per CTA, threads, and the number of kernel launches one kz_precode_batched
+ * issues (1, or 2 for a tensor-core batch split by shared memory). */
+kz_status kz_batch_query(const kz_batch* batch, int32_t* kernel, int32_t* rhs_per_cta, int32_t* threads,
+                         int32_t* launches);
 
 /* Adjoint (implicit differentiation) of Q = (H H^H + xi I)^-1 S, X = H^H Q for
  * a real loss L.  Given the gradients G_Q (K x nrhs) and G_X (Nt x nrhs) of L

@@ -27,7 +27,12 @@
 // cores (TF32 products, FP32 sums): the V-row residuals as 8-row blocks
 // (rows sorted by VR centre, so a block's rows share most of their union
 // interval) and the aggregate H_V^H phi per tile.  The F half-step, the
-// refresh and every stopping decision stay in FP32 on the CUDA cores.
+// refresh and every stopping decision stay in FP32 on the CUDA cores.  Its
+// correction m is held in FP16 as m / sigma_j (sigma_j: the column's relative
+// residual at the last refresh times the RMS of H^H D^-1 s_j, fixed between
+// refreshes), half the shared memory of FP32, so eight columns of a
+// 4096-antenna channel fit one CTA; FP16 keeps the ten mantissa bits the
+// TF32 MMAs read.
 #include "kz_device.cuh"
 
 namespace {
@@ -51,11 +56,21 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     __shared__ float s_sn2f[J];  // ||s_j||^2 tol^2 for the tentative test
     __shared__ double s_rn2[J];
     __shared__ float s_gamma[J];
+    __shared__ float s_kap[J];  // tensor-core mode: RMS of H^H D^-1 s_j
+    __shared__ float s_sig[J];  // tensor-core mode: storage scale of column j of m
     __shared__ int s_iters[J];
     __shared__ int s_wait[J];  // iterations a column spent waiting for its confirmation
     __shared__ int s_active;
     __shared__ int s_pending;
     __shared__ int s_item;
+    // tensor-core mode, F half-step: the rows of the orthogonal set cut into
+    // at most FCAP chunks of whole 256-entry steps {F index, first entry, end,
+    // first chunk of the row | end chunk << 16}, dealt to all warps
+    constexpr int FCAP = TC ? 2 * NW : 1;
+    __shared__ int4 fch_s[FCAP];
+    __shared__ float2 fpart_s[FCAP][J];  // partial dots per chunk
+    __shared__ float2 fb_s[FCAP][J];     // b - xi q of every F row
+    __shared__ int s_nfch;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int NT = NW * 32;
@@ -69,8 +84,11 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     };
     // iterate columns; the tensor-core mode pads each by KZ_TC_PAD entries so
     // the columns read by one MMA fragment fall in different banks
+    // (FP16 pairs in the tensor-core mode)
     float2* m_s = reinterpret_cast<float2*>(
-        carve((L.m_elems ? (size_t)L.m_elems : (size_t)J * (L.Ntp_max + (TC ? KZ_TC_PAD : 0))) * sizeof(float2)));
+        carve((L.m_elems ? (size_t)L.m_elems : (size_t)J * (L.Ntp_max + (TC ? KZ_TC_PAD : 0))) *
+              (TC ? sizeof(__half2) : sizeof(float2))));
+    __half2* m16 = reinterpret_cast<__half2*>(m_s);
     float2* b_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* q_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
     float2* p_s = reinterpret_cast<float2*>(carve((size_t)L.K_max * J * sizeof(float2)));
@@ -204,7 +222,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         };
 
         // ---- initialise: m = 0, q = 0, b = s, d = ||h||^2 + xi
-        for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
+        if (TC)
+            for (int e = tid; e < W * MS; e += NT) reinterpret_cast<unsigned*>(m16)[e] = 0u;
+        else
+            for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
         for (int e = tid; e < K * J; e += NT) {
             const int i = e / J, j = e % J;
             b_s[e] = (j < ncols) ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
@@ -269,7 +290,62 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 for (int w = 0; w < NW; ++w) s_wptr[w + 1] = s_wptr[w] + cnt[w];
                 for (int w = 0; w < NW; ++w) cnt[w] = s_wptr[w];
                 for (int t2 = 0; t2 < nt; ++t2) wlist_s[cnt[-1 - tcost_s[t2]]++] = t2;
+                // F chunks: c steps each, c chosen so that the rows' chunks
+                // number at most FCAP (a row has ceil(u / c) of them); only
+                // when a row of three or more steps would hold one warp while
+                // the others wait (with shorter rows the extra barrier costs
+                // as much as the balance saves)
+                int nch = 0;
+                int U = 0, umax = 0;
+                for (int f = 0; f < nF; ++f) {
+                    const int u = (rows_s[order_s[f]].y + 255) >> 8;
+                    U += u;
+                    umax = max(umax, u);
+                }
+                if (oahk && nF > 0 && nF <= FCAP && umax >= 3) {
+                    const int c = (nF == FCAP) ? max(1, umax) : max(1, (U + FCAP - nF - 1) / (FCAP - nF));
+                    for (int f = 0; f < nF; ++f) {
+                        const int u = max(1, (rows_s[order_s[f]].y + 255) >> 8);
+                        const int c0 = nch;
+                        for (int a = 0; a < u; a += c) fch_s[nch++] = make_int4(f, 256 * a, 256 * min(u, a + c), 0);
+                        for (int k = c0; k < nch; ++k) fch_s[k].w = c0 | (nch << 16);
+                    }
+                }
+                s_nfch = nch;
             }
+            // the scale of the solution: kappa_j = RMS of H^H D^-1 s_j (one
+            // Jacobi step from 0), through p_s, which is cleared again after
+            for (int e = tid; e < K * J; e += NT) {
+                const float2 bv = b_s[e];
+                const float di = dinv_s[e / J];
+                p_s[e] = make_float2(bv.x * di, bv.y * di);
+            }
+            __syncthreads();
+            float xx[J];
+#pragma unroll
+            for (int j = 0; j < J; ++j) xx[j] = 0.f;
+            for (int tile = warp; tile < I.ntiles; tile += NW) {
+                float2 u0[J], u1[J];
+                tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], p_s, u0, u1);
+#pragma unroll
+                for (int j = 0; j < J; ++j)
+                    xx[j] += u0[j].x * u0[j].x + u0[j].y * u0[j].y + u1[j].x * u1[j].x + u1[j].y * u1[j].y;
+            }
+#pragma unroll
+            for (int j = 0; j < J; ++j) xx[j] = warp_sum(xx[j]);
+            if (lane == 0) {
+#pragma unroll
+                for (int j = 0; j < J; ++j) s_part[warp][j] = xx[j];
+            }
+            __syncthreads();
+            if (tid < J) {
+                float a = 0.f;
+                for (int w = 0; w < NW; ++w) a += s_part[w][tid];
+                const float kap = sqrtf(a / (float)Nt);
+                s_kap[tid] = (kap > 0.f && isfinite(kap)) ? kap : 1.f;
+                s_sig[tid] = s_kap[tid];
+            }
+            for (int e = tid; e < K * J; e += NT) p_s[e] = make_float2(0.f, 0.f);
             __syncthreads();
         }
         if (warp < J) {
@@ -306,10 +382,74 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             // ---------------- F half-step (VR-OAHK only)
             if (oahk) {
                 ++t;
-                for (int f = warp; f < nF; f += NW) {
+                const int nch = TC ? s_nfch : 0;
+                if (TC && nch > 0) {
+                    // chunked: partial dots of every chunk (the warp of a
+                    // row's first chunk also keeps b - xi q of the row), then
+                    // each chunk's step from its row's sum (chunks in order:
+                    // the same sum in every warp of a row), the first chunk's
+                    // warp updating q
+                    for (int ch = warp; ch < nch; ch += NW) {
+                        const int4 e = fch_s[ch];
+                        const int i = order_s[e.x];
+                        float2 acc[J];
+                        row_dot_h<J>(I, rows_s, rptr_s, i, m16, MS, acc, W, e.y, e.z);
+                        if (lane == 0) {
+                            const bool first = (e.w & 0xffff) == ch;
+#pragma unroll
+                            for (int j = 0; j < J; ++j) {
+                                fpart_s[ch][j] = acc[j];
+                                if (first) {
+                                    const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                                    fb_s[e.x][j] = make_float2(bv.x - xi * qv.x, bv.y - xi * qv.y);
+                                }
+                            }
+                        }
+                    }
+                    __syncthreads();
+                    for (int ch = warp; ch < nch; ch += NW) {
+                        const int4 e = fch_s[ch];
+                        const int f = e.x, i = order_s[f], c0 = e.w & 0xffff, c1 = e.w >> 16;
+                        const float di = d_s[i];
+                        float2 g[J], gs[J];
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            float2 a = make_float2(0.f, 0.f);
+                            for (int c = c0; c < c1; ++c) {
+                                a.x += fpart_s[c][j].x;
+                                a.y += fpart_s[c][j].y;
+                            }
+                            const float sg = s_sig[j];
+                            const float2 bq = fb_s[f][j];
+                            const float rx = bq.x - a.x * sg;
+                            const float ry = bq.y - a.y * sg;
+                            const bool on = (act >> j) & 1;
+                            g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                            gs[j] = make_float2(g[j].x / sg, g[j].y / sg);
+                        }
+                        row_axpy_h<J>(I, rows_s, rptr_s, i, m16, MS, gs, W, e.y, e.z);
+                        if (ch == c0 && lane == 0) {
+#pragma unroll
+                            for (int j = 0; j < J; ++j) {
+                                q_s[i * J + j].x += g[j].x;
+                                q_s[i * J + j].y += g[j].y;
+                            }
+                        }
+                    }
+                }
+                for (int f = (TC && nch > 0) ? nF : warp; f < nF; f += NW) {
                     const int i = order_s[f];
                     float2 acc[J];
-                    row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, acc, W);
+                    if constexpr (TC) {
+                        row_dot_h<J>(I, rows_s, rptr_s, i, m16, MS, acc, W, 0, 0x7fffffff);
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            acc[j].x *= s_sig[j];
+                            acc[j].y *= s_sig[j];
+                        }
+                    } else {
+                        row_dot<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, acc, W);
+                    }
                     float2 g[J];
                     const float di = d_s[i];
 #pragma unroll
@@ -320,7 +460,17 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         const bool on = (act >> j) & 1;
                         g[j] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
                     }
-                    row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, g, lane, 32, W);
+                    if constexpr (TC) {
+                        float2 gs[J];
+#pragma unroll
+                        for (int j = 0; j < J; ++j) {
+                            const float r = 1.f / s_sig[j];
+                            gs[j] = make_float2(g[j].x * r, g[j].y * r);
+                        }
+                        row_axpy_h<J>(I, rows_s, rptr_s, i, m16, MS, gs, W, 0, 0x7fffffff);
+                    } else {
+                        row_axpy<J, BF16>(I, rows_s, rptr_s, i, m_s, MS, g, lane, 32, W);
+                    }
                     if (lane == 0) {
 #pragma unroll
                         for (int j = 0; j < J; ++j) {
@@ -343,12 +493,13 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     for (int q = s_wptr[warp]; q < s_wptr[warp + 1]; ++q) {
                         const int4 tk = task_s[wlist_s[q]];
                         float d[4];
-                        tc_row_part<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, tk.z, tk.x, tk.y, m_s, MS, W, d);
+                        tc_row_part<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, tk.z, tk.x, tk.y, m16, MS, W, d);
                         float2* dst = tk.w ? pb_s : p_s;
                         const int k = 8 * tk.z + 2 * c;
                         if (g < W) {
-                            if (k < vcount) dst[vs_s[k] * J + g] = make_float2(d[0], d[2]);
-                            if (k + 1 < vcount) dst[vs_s[k + 1] * J + g] = make_float2(d[1], d[3]);
+                            const float sg = s_sig[g];
+                            if (k < vcount) dst[vs_s[k] * J + g] = make_float2(d[0] * sg, d[2] * sg);
+                            if (k + 1 < vcount) dst[vs_s[k + 1] * J + g] = make_float2(d[1] * sg, d[3] * sg);
                         }
                     }
                 }
@@ -484,6 +635,11 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     double a = 0.0;
                     for (int w = 0; w < NW; ++w) a += s_partd[w][tid];
                     s_rn2[tid] = a;
+                    if (TC) {  // the next correction is about rho_j times the solution's scale
+                        const double rho = s_sn2[tid] > 0.0 ? sqrt(a / s_sn2[tid]) : 1.0;
+                        const float sg = (float)(rho * (double)s_kap[tid]);
+                        s_sig[tid] = (sg > 1e-30f && isfinite(sg)) ? sg : 1e-30f;
+                    }
                 }
                 __syncthreads();
                 if (tid == 0) {
@@ -507,7 +663,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     s_active = a2;
                     s_pending = 0;
                 }
-                if (CORR)
+                if (TC)
+                    for (int e = tid; e < W * MS; e += NT) reinterpret_cast<unsigned*>(m16)[e] = 0u;
+                else if (CORR)
                     for (int e = tid; e < W * MS; e += NT) m_s[e] = make_float2(0.f, 0.f);
                 __syncthreads();
             }
@@ -618,12 +776,49 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     for (int j = 0; j < J; ++j) {
                         const float2* xc = I.x + (size_t)(col0 + j) * Nt;
                         const bool on = j < ncols && s_gamma[j] != 0.f;
-                        ua[j] = (on && n < Nt) ? xc[n] : make_float2(0.f, 0.f);
-                        ub[j] = (on && n + 1 < Nt) ? xc[n + 1] : make_float2(0.f, 0.f);
+                        // one 16-byte load when the pair is inside the column
+                        // and 16-byte aligned (the buffer need only be 8-byte
+                        // aligned), else two 8-byte loads
+                        const bool vec = n + 1 < Nt && (reinterpret_cast<uintptr_t>(xc + n) & 15) == 0;
+                        if (on && vec) {
+                            const float4 v = *reinterpret_cast<const float4*>(xc + n);
+                            ua[j] = make_float2(v.x, v.y);
+                            ub[j] = make_float2(v.z, v.w);
+                        } else {
+                            ua[j] = (on && n < Nt) ? xc[n] : make_float2(0.f, 0.f);
+                            ub[j] = (on && n + 1 < Nt) ? xc[n + 1] : make_float2(0.f, 0.f);
+                        }
                     }
 #pragma unroll
                     for (int j = 0; j < J; ++j) {
                         const float g = s_gamma[j];
+                        if constexpr (TC) {
+                            if (j < ncols && g != 0.f) {
+                                const float gs = g / s_sig[j];
+                                __half2* mp = m16 + j * MS + n;
+                                if (n + 1 < Nt) {  // both entries: one 8-byte access
+                                    uint2 raw = *reinterpret_cast<const uint2*>(mp);
+                                    float2 v = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+                                    float2 w = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+                                    v.x = fmaf(gs, ua[j].x, v.x);
+                                    v.y = fmaf(gs, ua[j].y, v.y);
+                                    w.x = fmaf(gs, ub[j].x, w.x);
+                                    w.y = fmaf(gs, ub[j].y, w.y);
+                                    const __half2 a = __float22half2_rn(v), b = __float22half2_rn(w);
+                                    raw.x = *reinterpret_cast<const unsigned*>(&a);
+                                    raw.y = *reinterpret_cast<const unsigned*>(&b);
+                                    *reinterpret_cast<uint2*>(mp) = raw;
+                                    continue;
+                                }
+                                if (n < Nt) {  // the last antenna of an odd Nt
+                                    float2 v = __half22float2(mp[0]);
+                                    v.x = fmaf(gs, ua[j].x, v.x);
+                                    v.y = fmaf(gs, ua[j].y, v.y);
+                                    mp[0] = __float22half2_rn(v);
+                                }
+                            }
+                            continue;
+                        }
                         if (j < ncols && g != 0.f) {
                             float2* mp = m_s + j * MS + n;
                             if (n < Nt) {
@@ -675,7 +870,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             }
         }
 
-        // ---- finalise: x = m = H^H q (complex64), true residual with compensated sums
+        // ---- finalise: x = m = H^H q (complex64), true residual with compensated
+        // sums; the tensor-core mode writes x straight to global memory
         for (int tile = warp; tile < I.ntiles; tile += NW) {
             float2 u0[J], u1[J];
             tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], q_s, u0, u1);
@@ -683,15 +879,24 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
 #pragma unroll
             for (int j = 0; j < J; ++j) {
                 if (j >= W) continue;
-                m_s[j * MS + n] = u0[j];
-                m_s[j * MS + n + 1] = u1[j];
+                if constexpr (TC) {
+                    if (j < ncols) {
+                        float2* xc = I.x + (size_t)(col0 + j) * Nt;
+                        if (n < Nt) xc[n] = u0[j];
+                        if (n + 1 < Nt) xc[n + 1] = u1[j];
+                    }
+                } else {
+                    m_s[j * MS + n] = u0[j];
+                    m_s[j * MS + n + 1] = u1[j];
+                }
             }
         }
         __syncthreads();
         true_residual_pass(false);
         for (int j = 0; j < ncols; ++j) {
             float2* xc = I.x + (size_t)(col0 + j) * Nt;
-            for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * MS + n];
+            if (!TC)
+                for (int n = tid; n < Nt; n += NT) xc[n] = m_s[j * MS + n];
             if (I.v) {
                 float2* vc = I.v + (size_t)(col0 + j) * K;
                 for (int i = tid; i < K; i += NT) vc[i] = q_s[i * J + j];
@@ -794,7 +999,7 @@ size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow) {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t ntask = 2 * (size_t)((K + 7) / 8);
     return kz_smem_ahk(J, Ntp_max, K, KZ_C64) - r16((size_t)J * Ntp_max * sizeof(float2)) +
-           r16((size_t)m_elems * sizeof(float2)) + r16((size_t)K * sizeof(int)) +
+           r16((size_t)m_elems * sizeof(__half2)) + r16((size_t)K * sizeof(int)) +
            r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int)) +
            r16((size_t)trow * sizeof(unsigned short));
 }

@@ -986,6 +986,20 @@ kz_status kz_batch_tune(kz_batch* B, kz_select sel, double tol, int32_t max_iter
     return KZ_OK;
 }
 
+kz_status kz_batch_query(const kz_batch* B, int32_t* kernel, int32_t* rhs_per_cta, int32_t* threads,
+                         int32_t* launches) {
+    g_err.clear();
+    if (!B) {
+        kz_set_error("kz_batch_query: null batch");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (kernel) *kernel = B->kernel;
+    if (rhs_per_cta) *rhs_per_cta = B->J;
+    if (threads) *threads = B->nw * 32;
+    if (launches) *launches = B->n_items2 ? 2 : 1;
+    return KZ_OK;
+}
+
 kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta, int32_t threads, void* stream) {
     g_err.clear();
     if (!B || (threads != 256 && threads != 512)) {

@@ -147,6 +147,114 @@ __device__ __forceinline__ void row_dot2(const KzInst& I, const int4* rows, cons
     }
 }
 
+// ---------------------------------------------------------------------------
+// FP16 iterate of the tensor-core mode.  The correction m of the correction
+// form is stored per column as m / sigma_j in FP16 (re, im) pairs, sigma_j the
+// column's relative residual at the last refresh, so the stored values keep
+// the scale of the solution however small the correction gets; the MMAs read
+// ten mantissa bits of their operands either way (TF32).  Antenna pair
+// (n, n+1) of a column, n even: one 8-byte load.
+__device__ __forceinline__ float4 m16_pair(const __half2* p) {
+    const uint2 raw = *reinterpret_cast<const uint2*>(p);
+    const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// row_dot on the FP16 iterate (the caller scales by sigma_j), over the
+// packed entries [p0, p1) of row i (p0 a multiple of 256).
+template <int J>
+__device__ __forceinline__ void row_dot_h(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                          const __half2* __restrict__ m16, int MS, float2 (&acc)[J], int jn,
+                                          int p0, int p1) {
+    const int lane = threadIdx.x & 31;
+    const int4 rd = rows[i];
+    const int base = rptr[i];
+    const int pend = min(rd.y, p1);
+#pragma unroll
+    for (int j = 0; j < J; ++j) acc[j] = make_float2(0.f, 0.f);
+    for (int p = p0 + 2 * lane; p < pend; p += 256) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            h[u] = (p + 64 * u < pend) ? h_pair<false>(I, base + p + 64 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int n = rd.x + p;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (p + 64 * u >= pend) continue;
+#pragma unroll
+            for (int j = 0; j < J; ++j) {
+                if (j >= jn) continue;
+                cmac_pair<J, false>(h[u], m16_pair(m16 + j * MS + n + 64 * u), acc[j]);
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        acc[j].x = warp_sum(acc[j].x);
+        acc[j].y = warp_sum(acc[j].y);
+    }
+}
+
+// m16[j][n] += g[j] conj(H[i, n]) on row i's true VR (g already divided by
+// sigma_j), warp-wide, over the packed entries [p0, p1) (p0 a multiple of
+// 256).  Both entries of a pair are read and written together when both
+// lie in the true VR (one 8-byte access).
+template <int J>
+__device__ __forceinline__ void row_axpy_h(const KzInst& I, const int4* rows, const int* rptr, int i,
+                                           __half2* __restrict__ m16, int MS, const float2 (&g)[J], int jn, int p0,
+                                           int p1) {
+    const int lane = threadIdx.x & 31;
+    const int4 rd = rows[i];
+    const int base = rptr[i];
+    const int pend = min(rd.y, p1);
+    auto apply = [&](const float4& h, int p) {
+        const int n = rd.x + p;
+        const bool in0 = (n >= rd.z) && (n < rd.w);
+        const bool in1 = (n + 1 >= rd.z) && (n + 1 < rd.w);
+#pragma unroll
+        for (int j = 0; j < J; ++j) {
+            if (j >= jn) continue;
+            __half2* mp = m16 + j * MS + n;
+            if (in0 && in1) {
+                uint2 raw = *reinterpret_cast<const uint2*>(mp);
+                float2 v = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+                float2 w = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+                v.x = fmaf(h.x, g[j].x, fmaf(h.y, g[j].y, v.x));
+                v.y = fmaf(h.x, g[j].y, fmaf(-h.y, g[j].x, v.y));
+                w.x = fmaf(h.z, g[j].x, fmaf(h.w, g[j].y, w.x));
+                w.y = fmaf(h.z, g[j].y, fmaf(-h.w, g[j].x, w.y));
+                const __half2 a = __float22half2_rn(v), b = __float22half2_rn(w);
+                raw.x = *reinterpret_cast<const unsigned*>(&a);
+                raw.y = *reinterpret_cast<const unsigned*>(&b);
+                *reinterpret_cast<uint2*>(mp) = raw;
+                continue;
+            }
+            if (in0) {
+                float2 v = __half22float2(mp[0]);
+                v.x = fmaf(h.x, g[j].x, fmaf(h.y, g[j].y, v.x));
+                v.y = fmaf(h.x, g[j].y, fmaf(-h.y, g[j].x, v.y));
+                mp[0] = __float22half2_rn(v);
+            }
+            if (in1) {
+                float2 v = __half22float2(mp[1]);
+                v.x = fmaf(h.z, g[j].x, fmaf(h.w, g[j].y, v.x));
+                v.y = fmaf(h.z, g[j].y, fmaf(-h.w, g[j].x, v.y));
+                mp[1] = __float22half2_rn(v);
+            }
+        }
+    };
+    for (int p = p0 + 2 * lane; p < pend; p += 256) {
+        float4 h[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            h[u] = (p + 64 * u < pend) ? h_pair<false>(I, base + p + 64 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (p + 64 * u < pend) apply(h[u], p + 64 * u);
+    }
+}
+
 // Knuth's TwoSum: s = fl(a + b) and the exact rounding error e (s + e == a + b).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
     s = a + b;
@@ -505,11 +613,12 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, floa
 // (Aligned intervals start and end on even antennas, so both antennas of a
 // pair are inside or outside a row together.)  Lane (g, c) returns column
 // j = g of rows 2c (d[0] + i d[2]) and 2c + 1 (d[1] + i d[3]) of the block.
-// m_s column stride MS (even; columns 16-byte aligned).
-template <int J>
+// m_s column stride MS (even; columns 16-byte aligned): float2 entries, or
+// FP16 pairs (__half2) of the scaled iterate.
+template <int J, class MT>
 __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const int4* rows, const int* rptr,
                                             const int* vs, int nv, int b, int nbeg, int nend,
-                                            const float2* __restrict__ m_s, int MS, int W, float (&d)[4]) {
+                                            const MT* __restrict__ m_s, int MS, int W, float (&d)[4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
     const int k = 8 * b + g;
     int a = 0, len = 0, hb = 0;
@@ -520,11 +629,13 @@ __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const
         len = rd.y;
         hb = rptr[row] - rd.x;
     }
-    float e[4] = {0.f, 0.f, 0.f, 0.f};
+    // four accumulator sets (even / odd antenna of the pair x even / odd
+    // step u), so no MMA waits on the one before it
+    float e[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[u] = 0.f;
     const bool jok = g < W;  // W <= J columns of this item
-    const float2* mj = m_s + (jok ? g : 0) * MS;
+    const MT* mj = m_s + (jok ? g : 0) * MS;
     const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
     // eight antenna pairs per lane per step: all eight 16-byte H loads are in
     // flight before the first MMA of the step; the iterate is read from
@@ -543,13 +654,22 @@ __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int n = n0 + 8 * u + 2 * c;
-            const float4 m = (jok && n < nend) ? *reinterpret_cast<const float4*>(mj + n) : z;
-            mma_tf32(d, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
-            mma_tf32(e, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
+            float4 m = z;
+            if (jok && n < nend) {
+                if constexpr (sizeof(MT) == 4) m = m16_pair(reinterpret_cast<const __half2*>(mj + n));
+                else m = *reinterpret_cast<const float4*>(mj + n);
+            }
+            if (u & 1) {
+                mma_tf32(d2, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
+                mma_tf32(e2, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
+            } else {
+                mma_tf32(d, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
+                mma_tf32(e, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
+            }
         }
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) d[u] += e[u];
+    for (int u = 0; u < 4; ++u) d[u] = (d[u] + e[u]) + (d2[u] + e2[u]);
 }
 
 // u = H_V^H phi on one half (32 antennas, part 0 or 1) of a 64-antenna

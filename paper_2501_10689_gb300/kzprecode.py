@@ -48,6 +48,7 @@ class KzBatchItem(ctypes.Structure):
 
 EXPORTS = ("kz_plan_create", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
+           "kz_batch_query",
            "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "dual": 2, "tc": 3}
@@ -90,6 +91,8 @@ def load():
     lib.kz_precode_ex.restype = I32
     lib.kz_batch_set_launch.argtypes = [P, I32, I32, I32, P]
     lib.kz_batch_set_launch.restype = I32
+    lib.kz_batch_query.argtypes = [P, P, P, P, P]
+    lib.kz_batch_query.restype = I32
     lib.kz_batch_prepare.argtypes = [ctypes.POINTER(P), P, I32, I32, I32, I32, I32, P]
     lib.kz_batch_prepare.restype = I32
     lib.kz_precode_batched.argtypes = [P, I32, F64, I32, U64, I32, P, P]
@@ -277,6 +280,16 @@ def kz_batch_tune(batch: Batch, sel, tol, max_iter, seed, stream=None):
                              int(seed), chosen.ctypes.data_as(ctypes.c_void_p), _stream(stream)))
     names = {v: k for k, v in KERNELS.items()}
     return names[int(chosen[0])], int(chosen[1]), int(chosen[2])
+
+
+def kz_batch_query(batch: Batch):
+    """The batch's launch: dict(kernel, rhs_per_cta, threads, launches)."""
+    lib = load()
+    v = [ctypes.c_int32() for _ in range(4)]
+    _check(lib.kz_batch_query(batch.handle, *[ctypes.byref(x) for x in v]))
+    names = {k: n for n, k in KERNELS.items()}
+    return {"kernel": names.get(v[0].value, v[0].value), "rhs_per_cta": v[1].value, "threads": v[2].value,
+            "launches": v[3].value}
 
 
 def kz_batch_set_launch(batch: Batch, kernel, rhs_per_cta, threads, stream=None):

@@ -160,7 +160,7 @@ def test_tc_rejects_unsupported(kp):
 def test_tc_mixed_widths(kp):
     """J = 8 launch over a batch whose widest channel only fits 4 iterate
     columns: that channel's items are 4 columns wide, the others 8."""
-    insts = [kzgen.make_instance(700, 200, 4096, vr_frac_range=(0.1, 0.4), nrhs=16),
+    insts = [kzgen.make_instance(700, 200, 6144, vr_frac_range=(0.1, 0.4), nrhs=16),
              kzgen.make_instance(701, 30, 640, vr_frac_range=(0.1, 0.4), nrhs=16),
              kzgen.make_instance(702, 64, 2048, vr_frac_range=(0.1, 0.4), nrhs=16)]
     items = []
@@ -173,6 +173,7 @@ def test_tc_mixed_widths(kp):
                           resid=torch.empty(16, dtype=torch.float64, device="cuda"), xi=inst.xi))
     b = kp.kz_batch_prepare(items, 16, "vr_oahk")
     kp.kz_batch_set_launch(b, "tc", 8, 512)
+    assert kp.kz_batch_query(b) == {"kernel": "tc", "rhs_per_cta": 8, "threads": 512, "launches": 2}
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     kp.kz_precode_batched(b, "paper", 1e-6, 3000, 0, status=st)
     torch.cuda.synchronize()
@@ -188,7 +189,7 @@ def test_tc_mixed_widths_graph_replay(kp):
     """The two launches of a mixed-width batch (forked onto an auxiliary
     stream and joined back) are captured into one CUDA graph."""
     insts = [kzgen.make_instance(710 + i, K, Nt, vr_frac_range=(0.1, 0.4), nrhs=16)
-             for i, (K, Nt) in enumerate([(150, 4096), (40, 1024), (90, 2048), (60, 4096)])]
+             for i, (K, Nt) in enumerate([(150, 6144), (40, 1024), (90, 2048), (60, 4096)])]
     items = []
     for inst in insts:
         p = kp.plan_from_instance(inst)
@@ -198,6 +199,7 @@ def test_tc_mixed_widths_graph_replay(kp):
                           resid=torch.empty(16, dtype=torch.float64, device="cuda"), xi=inst.xi))
     b = kp.kz_batch_prepare(items, 16, "vr_oahk")
     kp.kz_batch_set_launch(b, "tc", 8, 512)
+    assert kp.kz_batch_query(b)["launches"] == 2
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     s = torch.cuda.Stream()
     with torch.cuda.stream(s):
@@ -214,3 +216,53 @@ def test_tc_mixed_widths_graph_replay(kp):
     for inst, it in zip(insts, items):
         V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
         assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X)
+
+
+def _one_item_batch(kp, inst, J, threads, tol):
+    p = kp.plan_from_instance(inst)
+    n = inst.nrhs
+    it = dict(plan=p, s=kp.rhs_tensor(inst.S), x=torch.empty((n, inst.Nt), dtype=torch.complex64, device="cuda"),
+              v=torch.empty((n, inst.K), dtype=torch.complex64, device="cuda"),
+              iters=torch.empty(n, dtype=torch.int32, device="cuda"),
+              resid=torch.empty(n, dtype=torch.float64, device="cuda"), xi=inst.xi)
+    b = kp.kz_batch_prepare([it], n, "vr_oahk")
+    kp.kz_batch_set_launch(b, "tc", J, threads)
+    assert kp.kz_batch_query(b) == {"kernel": "tc", "rhs_per_cta": J, "threads": threads, "launches": 1}
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_batched(b, "paper", tol, 3000, 0, status=st)
+    torch.cuda.synchronize()
+    return st.item(), it, p
+
+
+def _check_rzf(inst, it, tol):
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X)
+    assert np.all(orz.rel_err(it["v"].cpu().numpy().T, V) <= TOL_X)
+    assert np.all(it["resid"].cpu().numpy() <= tol * (1 + 1e-6))
+
+
+@pytest.mark.parametrize("threads", [256, 512])
+@pytest.mark.parametrize("J", [4, 8])
+def test_tc_long_orthogonal_rows(kp, J, threads):
+    """Rows of the orthogonal set longer than two 256-entry steps: the F
+    half-step is cut into chunks dealt to every warp (partial dots, then each
+    chunk's step from its row's sum)."""
+    inst = kzgen.make_instance(720, 48, 8192 if J == 4 else 4096, vr_len_range=(600, 1000), snr_db=10.0, nrhs=16)
+    st, it, p = _one_item_batch(kp, inst, J, threads, 1e-7)
+    F, _, _ = kp.kz_plan_query(p)
+    assert max(int(inst.vr_len[f]) for f in F) > 512
+    assert st == 0
+    _check_rzf(inst, it, 1e-7)
+
+
+@pytest.mark.parametrize("threads", [256, 512])
+def test_tc_many_orthogonal_rows(kp, threads):
+    """17 long rows in the orthogonal set: more than the 16 chunks a 256-thread
+    CTA deals (that launch takes the F rows one per warp), fewer than the 32
+    of a 512-thread CTA (chunked)."""
+    inst = kzgen.make_instance(733, 96, 10240, vr_len_range=(514, 540), snr_db=10.0, nrhs=8)
+    st, it, p = _one_item_batch(kp, inst, 4, threads, 1e-7)
+    F, _, _ = kp.kz_plan_query(p)
+    assert 16 < len(F) <= 32
+    assert st == 0
+    _check_rzf(inst, it, 1e-7)
