@@ -39,10 +39,9 @@ ERR_BAR = 1e-5
 # (ncu, one pass: dram__bytes_read.sum + dram__bytes_write.sum; the profiles/
 # summary of this workload), valid only for the kernel sources it was measured
 # on (their SHA-256 prefix).
-TRAFFIC = {"sources_sha256": "96ea6b6c22c80b2c",
-           "bytes_per_launch": {("tc", 4, 512): 3.40e9 + 1.19e9,
-                                # two launches per step: J = 4 over the 4096-antenna channels, J = 8 over the rest
-                                ("tc", 8, 512): (2.59e9 + 0.941e9) + (1.10e9 + 0.448e9)}}
+TRAFFIC = {"sources_sha256": "82ae1cfa61da0e52",
+           # one J = 8 launch per step over the whole batch (read + write)
+           "bytes_per_launch": {("tc", 8, 512): 11.83e9 + 2.52e9}}
 KERNEL_SOURCES = ("paper_2501_10689_gb300/csrc/kz_ahk.cu", "paper_2501_10689_gb300/csrc/kz_device.cuh",
                   "paper_2501_10689_gb300/csrc/kz_internal.h")
 
