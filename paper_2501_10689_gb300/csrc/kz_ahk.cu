@@ -269,25 +269,47 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 tcost_s[2 * b + 1] = steps >> 1;
             }
             __syncthreads();
-            if (tid == 0) {  // greedy longest-first assignment to warps
-                const int nt = 2 * nblk;
-                int load[NW], cnt[NW];
-                for (int w = 0; w < NW; ++w) load[w] = cnt[w] = 0;
-                for (int q = 0; q < nt; ++q) {
-                    int best = -1;
-                    for (int t2 = 0; t2 < nt; ++t2) {  // next task: largest cost, then lowest index
-                        if (tcost_s[t2] < 0) continue;
-                        if (best < 0 || tcost_s[t2] > tcost_s[best]) best = t2;
-                    }
-                    int w0 = 0;
-                    for (int w = 1; w < NW; ++w)
-                        if (load[w] < load[w0]) w0 = w;
-                    load[w0] += tcost_s[best];
-                    tcost_s[best] = -1 - w0;  // taken, by warp w0
-                    ++cnt[w0];
+            // greedy longest-first assignment to warps: tasks ranked by
+            // (cost descending, index ascending) in parallel into wlist_s,
+            // then warp 0 gives each, in that order, to the least loaded
+            // warp (lowest index on ties)
+            const int nt = 2 * nblk;
+            for (int t2 = tid; t2 < nt; t2 += NT) {
+                const int c2 = tcost_s[t2];
+                int rank = 0;
+                for (int t3 = 0; t3 < nt; ++t3) {
+                    const int c3 = tcost_s[t3];
+                    rank += (c3 > c2) || (c3 == c2 && t3 < t2);
                 }
-                s_wptr[0] = 0;
-                for (int w = 0; w < NW; ++w) s_wptr[w + 1] = s_wptr[w] + cnt[w];
+                wlist_s[rank] = t2;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                int load = 0, cnt = 0;  // of warp `lane` (lanes < NW)
+                for (int q = 0; q < nt; ++q) {
+                    const int t2 = wlist_s[q];
+                    const int c2 = tcost_s[t2];
+                    const int key = lane < NW ? (load << 5) | lane : 0x7fffffff;
+                    const int w0 = __reduce_min_sync(KZ_FULL, key) & 31;
+                    if (lane == w0) {
+                        load += c2;
+                        ++cnt;
+                    }
+                    __syncwarp();
+                    if (lane == 0) tcost_s[t2] = -1 - w0;  // taken, by warp w0
+                }
+                int incl = cnt;  // prefix sums of the counts
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(KZ_FULL, incl, o);
+                    if (lane >= o) incl += v;
+                }
+                if (lane < NW) s_wptr[lane + 1] = incl;
+                if (lane == 0) s_wptr[0] = 0;
+                __syncwarp();
+            }
+            if (tid == 0) {
+                int cnt[NW];
                 for (int w = 0; w < NW; ++w) cnt[w] = s_wptr[w];
                 for (int t2 = 0; t2 < nt; ++t2) wlist_s[cnt[-1 - tcost_s[t2]]++] = t2;
                 // F chunks: c steps each, c chosen so that the rows' chunks
@@ -313,39 +335,24 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 }
                 s_nfch = nch;
             }
-            // the scale of the solution: kappa_j = RMS of H^H D^-1 s_j (one
-            // Jacobi step from 0), through p_s, which is cleared again after
-            for (int e = tid; e < K * J; e += NT) {
-                const float2 bv = b_s[e];
-                const float di = dinv_s[e / J];
-                p_s[e] = make_float2(bv.x * di, bv.y * di);
-            }
-            __syncthreads();
-            float xx[J];
-#pragma unroll
-            for (int j = 0; j < J; ++j) xx[j] = 0.f;
-            for (int tile = warp; tile < I.ntiles; tile += NW) {
-                float2 u0[J], u1[J];
-                tile_accum<J, false>(I, trow4, tile, tptr_s[tile], tptr_s[tile + 1], p_s, u0, u1);
-#pragma unroll
-                for (int j = 0; j < J; ++j)
-                    xx[j] += u0[j].x * u0[j].x + u0[j].y * u0[j].y + u1[j].x * u1[j].x + u1[j].y * u1[j].y;
-            }
-#pragma unroll
-            for (int j = 0; j < J; ++j) xx[j] = warp_sum(xx[j]);
-            if (lane == 0) {
-#pragma unroll
-                for (int j = 0; j < J; ++j) s_part[warp][j] = xx[j];
-            }
-            __syncthreads();
-            if (tid < J) {
+            // the scale of the solution: kappa_j^2 = (1 / Nt) sum_i |s_ij|^2
+            // ||h_i||^2 / d_i^2, the diagonal part of ||H^H D^-1 s_j||^2 (one
+            // Jacobi step from 0; the storage scale only needs its order of
+            // magnitude)
+            if (warp < J) {
                 float a = 0.f;
-                for (int w = 0; w < NW; ++w) a += s_part[w][tid];
-                const float kap = sqrtf(a / (float)Nt);
-                s_kap[tid] = (kap > 0.f && isfinite(kap)) ? kap : 1.f;
-                s_sig[tid] = s_kap[tid];
+                for (int i = lane; i < K; i += 32) {
+                    const float2 bv = b_s[i * J + warp];
+                    const float di = dinv_s[i];
+                    a += (bv.x * bv.x + bv.y * bv.y) * (d_s[i] - xi) * di * di;
+                }
+                a = warp_sum(a);
+                if (lane == 0) {
+                    const float kap = sqrtf(a / (float)Nt);
+                    s_kap[warp] = (kap > 0.f && isfinite(kap)) ? kap : 1.f;
+                    s_sig[warp] = s_kap[warp];
+                }
             }
-            for (int e = tid; e < K * J; e += NT) p_s[e] = make_float2(0.f, 0.f);
             __syncthreads();
         }
         if (warp < J) {

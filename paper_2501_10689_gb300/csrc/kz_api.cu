@@ -117,7 +117,7 @@ struct kz_batch {
     int m_elems = 0;               // tensor-core kernel: shared iterate entries per CTA
     int trow_max = 0, trow_max2 = 0;  // tensor-core kernel: staged covering-list entries (0: none)
     std::vector<int> Ntp_of;       // per instance
-    std::vector<double> cost;  // per-instance work estimate (aligned entries + 4 Nt)
+    std::vector<double> cost;  // per-instance work estimate ((aligned entries + 4 Nt) x (0.036 + coupling))
     size_t smem = 0;
     kz_algo algo = KZ_VR_OAHK;
     kz_prec prec = KZ_C64;
@@ -779,6 +779,23 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
     B->h_insts = insts;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = upload(&B->d_insts, insts, st);
+    // work estimate of a channel: aligned entries + 4 Nt per iteration, times
+    // the expected iterations, taken as proportional to 0.036 + mu (mu the
+    // largest squared off-diagonal row mass of the row-normalised system, the
+    // worst-coupled user; least-squares fit of the iterations of near-field
+    // channels of 1024-4096 antennas: 2.7 + 75 mu).  It only orders the queue.
+    if (e == cudaSuccess) {
+        float* d_mu = nullptr;
+        std::vector<float> mu(n, 0.f);
+        e = cudaMalloc((void**)&d_mu, n * sizeof(float));
+        if (e == cudaSuccess) e = kz_coupling(B->d_insts, n, d_mu, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(mu.data(), d_mu, n * sizeof(float), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (d_mu) cudaFree(d_mu);
+        if (e == cudaSuccess)
+            for (int b = 0; b < n; ++b)
+                if (std::isfinite(mu[b])) B->cost[b] *= 0.036 + (double)mu[b];
+    }
     if (e == cudaSuccess) e = cudaMalloc((void**)&B->d_queue, 2 * sizeof(int));
     if (e == cudaSuccess) e = batch_layout(B, B->J, B->nw, sms, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);

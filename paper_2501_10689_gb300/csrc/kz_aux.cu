@@ -369,6 +369,36 @@ cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, in
     return cudaGetLastError();
 }
 
+__global__ void coupling_kernel(const KzInst* __restrict__ insts, float* __restrict__ mu) {
+    const KzInst& I = insts[blockIdx.x];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __shared__ float s_max[32];
+    float best = 0.f;
+    for (int k = warp; k < I.K; k += nw) {
+        const float dk = I.nrm[k] + I.xi;
+        float a = 0.f;
+        for (int e = I.xptr[k] + lane; e < I.xptr[k + 1]; e += 32) {
+            const int l = I.xidx[e];
+            if (l == k) continue;
+            const float2 g = I.G[e];
+            a += (g.x * g.x + g.y * g.y) / (dk * (I.nrm[l] + I.xi));
+        }
+        best = fmaxf(best, warp_sum(a));
+    }
+    if (lane == 0) s_max[warp] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < nw; ++w) m = fmaxf(m, s_max[w]);
+        mu[blockIdx.x] = m;
+    }
+}
+
+cudaError_t kz_coupling(const KzInst* insts, int n, float* mu, cudaStream_t st) {
+    coupling_kernel<<<n, 256, 0, st>>>(insts, mu);
+    return cudaGetLastError();
+}
+
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st) {
     gram_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, xptr, xidx, G);

@@ -46,7 +46,7 @@ struct KzInst {
     const double* nrmd;        // ||h_k||^2 in FP64
     const int* in_off;         // row k's offset in the caller's packed layout
     const int* vsort;          // V rows (K - nF), then all K rows, each by VR centre
-    const float2* G;           // Gram matrix H H^H on the CSR pattern of X_k (FP64 sums, rounded)
+    const float2* G;           // H H^H on the CSR pattern of X_k (compensated FP32 sums)
     int cmax;                  // most rows covering one tile
     // --- call ---
     float xi;
@@ -104,6 +104,10 @@ cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, in
                          float* out_f, cudaStream_t st);
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st);
+// Coupling of every channel of a batch: mu[b] = max_k sum_{l in X_k, l != k}
+// |G_kl|^2 / (d_k d_l), d = ||h||^2 + xi (the largest squared off-diagonal
+// row mass of the row-normalised system), one block per channel.
+cudaError_t kz_coupling(const KzInst* insts, int n, float* mu, cudaStream_t st);
 cudaError_t kz_adjoint_rhs(const KzInst& I, int nrhs, const float2* G_Q, const float2* G_X, float2* Gt,
                            cudaStream_t st);
 cudaError_t kz_adjoint_contract(const KzInst& I, int nrhs, const float2* Q, const float2* X,

@@ -266,3 +266,18 @@ def test_tc_many_orthogonal_rows(kp, threads):
     assert 16 < len(F) <= 32
     assert st == 0
     _check_rzf(inst, it, 1e-7)
+
+
+@pytest.mark.parametrize("c", [1e-4, 1e4])
+def test_tc_scale_range(kp, c):
+    """H -> c H with xi -> c^2 xi scales x by 1 / c: the FP16 correction
+    (stored divided by a per-column scale taken from the data) converges to
+    the RZF solution across eight orders of magnitude of the solution."""
+    import dataclasses
+    base = kzgen.make_instance(740, 40, 2048, vr_frac_range=(0.1, 0.4), snr_db=10.0, nrhs=16)
+    inst = dataclasses.replace(base, H_packed=(base.H_packed * np.float32(c)).astype(np.complex64),
+                               xi=float(base.xi * c * c))
+    for J in (4, 8):
+        st, it, _ = _one_item_batch(kp, inst, J, 512, 1e-6)
+        assert st == 0
+        _check_rzf(inst, it, 1e-6)
