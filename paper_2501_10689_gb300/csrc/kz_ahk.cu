@@ -29,9 +29,9 @@
 // interval) and the aggregate H_V^H phi per tile.  The F half-step, the
 // refresh and every stopping decision stay in FP32 on the CUDA cores.  Its
 // correction m is held in FP16 as m / sigma_j (sigma_j: the column's relative
-// residual at the last refresh times the RMS of H^H D^-1 s_j, fixed between
-// refreshes), half the shared memory of FP32, so eight columns of a
-// 4096-antenna channel fit one CTA; FP16 keeps the ten mantissa bits the
+// residual at the last refresh times an estimate of the RMS of H^H D^-1 s_j,
+// fixed between refreshes), half the shared memory of FP32, so eight columns
+// of a 4096-antenna channel fit one CTA; FP16 keeps the ten mantissa bits the
 // TF32 MMAs read.
 #include "kz_device.cuh"
 
