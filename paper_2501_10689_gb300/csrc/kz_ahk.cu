@@ -444,7 +444,41 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         }
                     }
                 }
-                for (int f = (TC && nch > 0) ? nF : warp; f < nF; f += NW) {
+                if constexpr (TC) {
+                    // few short rows: each row's columns split between two
+                    // warps (both read the row; no cross-warp sums)
+                    constexpr int JH = J > 1 ? J / 2 : 1;
+                    if (nch == 0 && 2 * nF <= NW && warp < 2 * nF) {
+                        const int f = warp >> 1, j0 = (warp & 1) * JH;
+                        const int i = order_s[f];
+                        const int jn = min(JH, W - j0);
+                        float2 acc[JH];
+                        row_dot_h<JH>(I, rows_s, rptr_s, i, m16 + j0 * MS, MS, acc, jn, 0, 0x7fffffff);
+                        const float di = d_s[i];
+                        float2 g[JH], gs[JH];
+#pragma unroll
+                        for (int jj = 0; jj < JH; ++jj) {
+                            const int j = j0 + jj;
+                            const float sg = s_sig[j];
+                            const float2 bv = b_s[i * J + j], qv = q_s[i * J + j];
+                            const float rx = bv.x - acc[jj].x * sg - xi * qv.x;
+                            const float ry = bv.y - acc[jj].y * sg - xi * qv.y;
+                            const bool on = jj < jn && ((act >> j) & 1);
+                            g[jj] = on ? make_float2(rx / di, ry / di) : make_float2(0.f, 0.f);
+                            const float r = 1.f / sg;
+                            gs[jj] = make_float2(g[jj].x * r, g[jj].y * r);
+                        }
+                        row_axpy_h<JH>(I, rows_s, rptr_s, i, m16 + j0 * MS, MS, gs, jn, 0, 0x7fffffff);
+                        if (lane == 0) {
+#pragma unroll
+                            for (int jj = 0; jj < JH; ++jj) {
+                                q_s[i * J + j0 + jj].x += g[jj].x;
+                                q_s[i * J + j0 + jj].y += g[jj].y;
+                            }
+                        }
+                    }
+                }
+                for (int f = (TC && (nch > 0 || 2 * nF <= NW)) ? nF : warp; f < nF; f += NW) {
                     const int i = order_s[f];
                     float2 acc[J];
                     if constexpr (TC) {
