@@ -186,9 +186,15 @@ typedef struct {
 /* Prepare one persistent launch over n instances of uneven K, Nt and VR
  * lengths (step A8): copies the instance table to the device, orders the
  * work (one item = one instance x rhs_per_cta columns) by estimated cost,
- * largest first, and allocates the work-queue counter.  rhs_per_cta and
- * threads as in kz_precode (0 = tuned).  The plans and buffers named by the
- * items must stay valid while the batch is used.  Synchronous. */
+ * largest first, and allocates the work-queue counters.  The estimate is the
+ * per-iteration work (aligned VR entries + 4 Nt) times a predicted iteration
+ * count that grows with the coupling of the users (the largest squared
+ * off-diagonal row mass of the row-normalised system, from the plan's inner
+ * products of overlapping rows and the item's xi); it only orders the queue
+ * and is fixed here (kz_batch_rebind and kz_plan_update keep the order).
+ * rhs_per_cta and threads as in kz_precode (0 = tuned).  The plans and
+ * buffers named by the items must stay valid while the batch is used.
+ * Synchronous. */
 kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n, int32_t nrhs,
                            kz_algo algo, kz_prec prec, int32_t rhs_per_cta, void* stream);
 
