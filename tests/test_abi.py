@@ -86,3 +86,12 @@ def test_binding_fails_loudly_without_library(monkeypatch, tmp_path):
     monkeypatch.setattr(kzprecode, "library_path", lambda: str(tmp_path / "missing.so"))
     with pytest.raises(RuntimeError, match="missing"):
         kzprecode.load()
+
+
+def test_batch_query_and_launch_reject_null(lib):
+    from paper_2501_10689_gb300.kzprecode import KZ_ERR_INVALID_ARG
+    v = [ctypes.c_int32() for _ in range(4)]
+    rc = lib.kz_batch_query(None, *[ctypes.byref(x) for x in v])
+    assert rc == KZ_ERR_INVALID_ARG and "batch" in lib.kz_last_error().decode()
+    assert lib.kz_batch_set_launch(None, 3, 8, 512, None) == KZ_ERR_INVALID_ARG
+    assert lib.kz_batch_rebind(None, None, None) == KZ_ERR_INVALID_ARG
