@@ -91,11 +91,7 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
 
 /* Which kernel runs AHK / VR_OAHK.  RESIDENT keeps the iterate m of J
  * columns in shared memory and streams H per column group (every method,
- * both precisions).  DUAL (AHK / VR_OAHK, C64) keeps only q and the residual
- * r = s - B B^H q of 8 or 16 columns, updates r by r -= gamma (H H^H phi + xi phi)
- * (the same iterates as eq. (update4)), stages each 64-antenna tile of H in
- * shared memory once per pass for all its columns, and recomputes the true
- * residual to confirm stops.  TC (AHK / VR_OAHK, C64, 4 or 8 columns) is
+ * both precisions).  TC (AHK / VR_OAHK, C64, 4 or 8 columns) is
  * RESIDENT in correction form with the two contractions of each iteration
  * (the V-row residuals and H_V^H phi) on the tensor cores in TF32 with FP32
  * sums; the right-hand side b = s - H m_ref is recomputed from the complex64
@@ -103,7 +99,7 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * residual, so results meet the same tolerance as RESIDENT.  AUTO: RESIDENT
  * for kz_precode; the batch default is RESIDENT until kz_batch_tune or
  * kz_batch_set_launch chooses. */
-typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_DUAL = 2, KZ_KERNEL_TC = 3 } kz_kernel;
+typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_TC = 3 } kz_kernel;
 
 typedef struct kz_plan kz_plan;
 typedef struct kz_batch kz_batch;
@@ -124,6 +120,17 @@ typedef struct kz_batch kz_batch;
  * On success *out owns all device memory of the plan until kz_plan_destroy. */
 kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset,
                          const int32_t* vr_len, const kz_cf32* H_packed, kz_prec prec, void* stream);
+
+/* kz_plan_create from a dense channel matrix: H_dense is device kz_cf32
+ * [K * Nt], row-major (entry (k, n) at H_dense[k * Nt + n]), 8-byte aligned.
+ * Only the entries inside each user's VR are read; the channel is zero
+ * outside it by the VR model h_k = hbar_k (.) u_k (Sec. II, eqs. (3)-(4)),
+ * whatever H_dense holds there.  Every other argument, the resulting plan and
+ * the errors are those of kz_plan_create; the plan is the one kz_plan_create
+ * builds from the same VR entries packed (so kz_plan_update and the adjoint's
+ * packed gradient keep the packed layout).  H_dense is not retained. */
+kz_status kz_plan_dense(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset,
+                        const int32_t* vr_len, const kz_cf32* H_dense, kz_prec prec, void* stream);
 
 /* Replace the channel of an existing plan (same K, Nt and VRs): re-pack
  * H_packed (device, layout as in kz_plan_create, 8-byte aligned) into the
@@ -161,11 +168,9 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
                      kz_cf32* v, int32_t* iters, double* resid, int32_t* status, int32_t rhs_per_cta,
                      int32_t refresh, void* stream);
 
-/* kz_precode with an explicit kernel (see kz_kernel).  With KZ_KERNEL_DUAL,
- * rhs_per_cta must be 0, 8 or 16 (0: 16 when nrhs >= 16 and it fits, else 8)
- * and algo AHK or VR_OAHK on a C64 plan (else KZ_ERR_UNSUPPORTED).  With
- * KZ_KERNEL_TC, rhs_per_cta must be 0, 4 or 8 (0: 8 when nrhs >= 8 and it
- * fits, else 4), same algorithms and plans. */
+/* kz_precode with an explicit kernel (see kz_kernel).  With KZ_KERNEL_TC,
+ * rhs_per_cta must be 0, 4 or 8 (0: 8 when nrhs >= 8 and it fits, else 4)
+ * and algo AHK or VR_OAHK on a C64 plan (else KZ_ERR_UNSUPPORTED). */
 kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
                         kz_select sel, double tol, int32_t max_iter, uint64_t seed, kz_cf32* x,
                         kz_cf32* v, int32_t* iters, double* resid, int32_t* status, kz_kernel kernel,
@@ -219,9 +224,8 @@ void kz_batch_destroy(kz_batch* batch);
 
 /* Autotune a prepared batch (step A8's launch shape): time every feasible
  * launch on the batch itself -- the RESIDENT kernel with columns-per-CTA in
- * {1, 2, 4, 8} and 256 or 512 threads, and for AHK / VR_OAHK on C64 the DUAL
- * kernel with 8 columns (256 or 512 threads) or 16 columns (512 threads) and
- * the TC kernel with 4 or 8 columns (256 or 512 threads) -- three runs each,
+ * {1, 2, 4, 8} and 256 or 512 threads, and for AHK / VR_OAHK on C64 the TC
+ * kernel with 4 or 8 columns (256 or 512 threads) -- three runs each,
  * the last two timed with CUDA events on `stream`; keep the fastest and write
  * it to chosen (host int32[3]: kernel, columns per CTA, threads; may be
  * NULL).  It solves the batch repeatedly, so the batch's outputs hold a
@@ -229,9 +233,9 @@ void kz_batch_destroy(kz_batch* batch);
 kz_status kz_batch_tune(kz_batch* batch, kz_select sel, double tol, int32_t max_iter, uint64_t seed,
                         int32_t* chosen, void* stream);
 
-/* Fix a batch's launch: kernel (RESIDENT, DUAL or TC), columns per CTA
- * (RESIDENT: 1, 2, 4, 8; DUAL: 8, 16; TC: 4, 8) and threads (256 or 512;
- * DUAL with 16 columns: 512).  Rebuilds the work list; synchronous.
+/* Fix a batch's launch: kernel (RESIDENT or TC), columns per CTA
+ * (RESIDENT: 1, 2, 4, 8; TC: 4, 8) and threads (256 or 512).  Rebuilds the
+ * work list; synchronous.
  * KZ_ERR_UNSUPPORTED if the combination does not fit shared memory or the
  * batch's method. */
 kz_status kz_batch_set_launch(kz_batch* batch, kz_kernel kernel, int32_t rhs_per_cta, int32_t threads,
@@ -263,10 +267,10 @@ kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf3
 
 /* The adjoint above without any device allocation.  The paper has no
  * counterpart; this entry exists for callers that cannot allocate device memory
- * when they differentiate: a backward pass recorded into a CUDA graph (a device
- * allocation is not a stream operation, so a replay would not repeat it), a
- * real-time loop that must not block in the driver's allocator, or a process
- * whose device memory is reserved up front by another allocator.
+ * when they differentiate: a real-time loop that must not block in the
+ * driver's allocator, a process whose device memory is all reserved up front by
+ * another allocator (so a cudaMalloc would fail), or a runtime that forbids
+ * allocation after start-up.
  * kz_precode_adjoint keeps its right-hand side G~ (K x nrhs) in plan-owned
  * memory that it allocates on first use; this variant keeps G~ in one
  * file-scope device array of 262144 complex entries (2 MiB), which every GPU
@@ -276,10 +280,13 @@ kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf3
  *   returns KZ_ERR_INVALID_ARG with a message; nothing is enqueued then.
  *   The first call on a device looks up the array's device address (with that
  *   device current) and caches it; make that first call before any stream
- *   capture.  All calls share the one array, which keeps the last call's
- *   contents: calls that overlap on the GPU (different streams or devices
- *   sharing nothing but the library) race on it, so serialise them.  Every
- *   entry of G~ the solve reads is written first, so nothing needs clearing. */
+ *   capture.  cudaDeviceReset on a device invalidates the cached address:
+ *   do not call this entry on that device again in the same process.
+ *   Each device has its own copy of the array.  On one device all calls share
+ *   it, and it keeps the last call's contents: calls that overlap on the GPU
+ *   (through different streams, for example) race on it, so serialise them.
+ *   Every entry of G~ the solve reads is written first, so nothing needs
+ *   clearing. */
 kz_status kz_precode_adjoint_noalloc(kz_plan* plan, int32_t nrhs, float xi, const kz_cf32* Q,
                                      const kz_cf32* X, const kz_cf32* G_Q, const kz_cf32* G_X,
                                      double tol, int32_t max_iter, kz_cf32* lambda, kz_cf32* y,

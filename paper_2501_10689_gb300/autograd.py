@@ -20,7 +20,7 @@ from . import kzprecode as kp
 
 class KzPrecodeFn(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, H_packed, xi, S, vr_offset, vr_len, Nt, tol, max_iter):
+    def forward(ctx, H_packed, xi, S, vr_offset, vr_len, Nt, tol, max_iter, adj_max_iter=None):
         K = len(vr_len)
         plan = kp.kz_plan_create(K, Nt, vr_offset, vr_len, H_packed.detach().contiguous())
         xi_f = float(xi)
@@ -29,7 +29,7 @@ class KzPrecodeFn(torch.autograd.Function):
             raise kp.KzError(kp.KZ_NOT_CONVERGED, "forward solve did not converge")
         ctx.plan = plan
         ctx.xi = xi_f
-        ctx.tol, ctx.max_iter = tol, max_iter
+        ctx.tol, ctx.max_iter = tol, max_iter if adj_max_iter is None else adj_max_iter
         ctx.xi_is_tensor = isinstance(xi, torch.Tensor)
         ctx.save_for_backward(out["x"], out["v"])
         return out["x"], out["v"]
@@ -50,11 +50,16 @@ class KzPrecodeFn(torch.autograd.Function):
         gX = gX.contiguous() if gX is not None else None
         gV = gV.contiguous() if gV is not None else None
         if gX is None and gV is None:
-            return None, None, None, None, None, None, None, None
+            return None, None, None, None, None, None, None, None, None
         kp.kz_precode_adjoint(plan, nrhs, ctx.xi, V, X, gV, gX, ctx.tol, ctx.max_iter, lam, y, gH, gxi, iters,
                               resid, status)
+        st = int(status.item())  # waits for the adjoint solve
+        if st & kp.KZ_STATUS_BIT_NUMERIC:
+            raise kp.KzError(kp.KZ_ERR_NUMERIC, "adjoint solve: NaN or Inf in a residual")
+        if st & kp.KZ_STATUS_BIT_NOT_CONVERGED:
+            raise kp.KzError(kp.KZ_NOT_CONVERGED, "adjoint solve did not converge")
         grad_xi = gxi.reshape(()) if ctx.xi_is_tensor else None
-        return gH, grad_xi, lam, None, None, None, None, None
+        return gH, grad_xi, lam, None, None, None, None, None, None
 
 
 class BatchedPrecoder:
@@ -224,10 +229,12 @@ def sum_rate_loss_batched(H_dense, X, snr_lin):
     return -torch.sum(torch.log2(1.0 + sinr))
 
 
-def precode(H_packed, xi, S, vr_offset, vr_len, Nt, tol=1e-7, max_iter=2000):
-    """Differentiable (X, V) = (H^H V, (H H^H + xi I)^-1 S)."""
+def precode(H_packed, xi, S, vr_offset, vr_len, Nt, tol=1e-7, max_iter=2000, adj_max_iter=None):
+    """Differentiable (X, V) = (H^H V, (H H^H + xi I)^-1 S).  The backward's
+    adjoint solve uses ``adj_max_iter`` (default: max_iter) and raises KzError
+    when it does not converge or meets a NaN / Inf."""
     return KzPrecodeFn.apply(H_packed, xi, S, np.asarray(vr_offset, np.int32), np.asarray(vr_len, np.int32),
-                             int(Nt), float(tol), int(max_iter))
+                             int(Nt), float(tol), int(max_iter), None if adj_max_iter is None else int(adj_max_iter))
 
 
 def sum_rate_loss(H_dense, X, snr_lin):

@@ -373,8 +373,12 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             for (int j = 0; j < ncols; ++j) {
                 s_iters[j] = L.max_iter;
                 s_wait[j] = 0;
-                if (s_sn2[j] > 0.0) act |= 1 << j;
-                else s_iters[j] = 0;
+                if (s_sn2[j] > 0.0 && isfinite(s_sn2[j])) {
+                    act |= 1 << j;
+                } else {  // a zero column is solved by x = 0; a NaN / Inf one is reported
+                    s_iters[j] = 0;
+                    if (!(s_sn2[j] == 0.0)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+                }
             }
             s_active = act;
             s_pending = 0;

@@ -1,5 +1,6 @@
 // C-ABI of libkzprecode: argument checking, the per-channel host set-up
 // (step A0) and the launches.  See include/kzprecode.h for the contract.
+#include <atomic>
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -113,7 +114,7 @@ struct kz_plan {
 
 struct kz_batch {
     int n = 0, nrhs = 0, J = 1, nw = 16, grid = 1, n_items = 0, Ntp_max = 0, K_max = 0;
-    int kernel = KZ_KERNEL_RESIDENT, cs = 0, cmax = 0;
+    int kernel = KZ_KERNEL_RESIDENT, cmax = 0;
     int m_elems = 0;               // tensor-core kernel: shared iterate entries per CTA
     int trow_max = 0, trow_max2 = 0;  // tensor-core kernel: staged covering-list entries (0: none)
     std::vector<int> Ntp_of;       // per instance
@@ -183,17 +184,6 @@ int choose_J(kz_algo a, int nrhs_total_items_base, int Ntp, int K, kz_prec p, in
 }
 
 int choose_nw(int Ntp) { return (Ntp / KZ_TILE) >= 16 ? 16 : 8; }
-
-// Dual kernel: staged rows per chunk (all rows of the most-covered tile when
-// they fit, else as many as fit, at least 32).  Returns 0 if nothing fits.
-int dual_cs(int J, int nw, int K, int cmax) {
-    if (!((J == 8 && (nw == 8 || nw == 16)) || (J == 16 && nw == 16))) return 0;
-    const size_t base = kz_smem_dual(J, nw, 0, K);
-    const size_t per_row = 2 * ((KZ_TILE + 1) * sizeof(float2) + 2 * sizeof(int));  // two staging buffers
-    if (base + 32 * per_row > kSmemLimit) return 0;
-    const int fit = (int)((kSmemLimit - base) / per_row);
-    return std::max(32, std::min(fit, std::max(cmax, 1)));
-}
 
 // Work items of a batch for J columns per CTA and nw warps: {instance, first
 // column} ordered by estimated cost, largest first; grid = resident CTAs.
@@ -276,18 +266,12 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
     B->kernel = kernel;
     B->n_items = (int)witems.size();
     int occ = 1;
-    if (kernel == KZ_KERNEL_DUAL) {
-        B->cs = dual_cs(J, nw, B->K_max, B->cmax);
-        B->smem = kz_smem_dual(J, nw, B->cs, B->K_max);
-        occ = std::max(1, kz_occupancy_dual(J, nw, B->smem));
-    } else if (kernel == KZ_KERNEL_TC) {
-        B->cs = 0;
+    if (kernel == KZ_KERNEL_TC) {
         B->m_elems = m_elems;
         B->trow_max = tc_stage_ok(J, m_elems, B->Ntp_max, B->K_max, trow1) ? trow1 : 0;
         B->smem = kz_smem_ahk_tc(J, m_elems, B->Ntp_max, B->K_max, B->trow_max);
         occ = std::max(1, kz_occupancy_ahk_tc(J, nw, B->smem));
     } else {
-        B->cs = 0;
         B->smem = smem_for(B->algo, J, B->Ntp_max, B->K_max, B->prec);
         occ = std::max(1, occupancy_for(B->algo, J, nw, B->smem, B->prec));
     }
@@ -303,8 +287,6 @@ cudaError_t batch_layout_k(kz_batch* B, int kernel, int J, int nw, int sms, cuda
     (void)cost2;
     return cudaSuccess;
 }
-
-bool dual_ok(kz_algo a, kz_prec p) { return is_ahk_family(a) && p == KZ_C64; }
 
 bool tc_ok(kz_algo a, kz_prec p) { return is_ahk_family(a) && p == KZ_C64; }
 
@@ -324,34 +306,40 @@ const char* kz_last_error(void) { return g_err.c_str(); }
 
 int32_t kz_version(void) { return 1 * 10000 + 0 * 100 + 0; }
 
-kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset, const int32_t* vr_len,
-                         const kz_cf32* H_packed, kz_prec prec, void* stream) {
+}  // extern "C"
+
+// Step A0 for kz_plan_create (H given packed) and kz_plan_dense (H given as a
+// dense K x Nt matrix): exactly one of H_packed / H_dense is non-NULL.
+static kz_status plan_build(const char* fn, kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset,
+                            const int32_t* vr_len, const kz_cf32* H_packed, const kz_cf32* H_dense, kz_prec prec,
+                            void* stream) {
     g_err.clear();
     if (!out) {
-        kz_set_error("kz_plan_create: out is NULL");
+        kz_set_error("%s: out is NULL", fn);
         return KZ_ERR_INVALID_ARG;
     }
     *out = nullptr;
     if (K < 1 || Nt < 2 || K >= Nt) {
-        kz_set_error("kz_plan_create: need 1 <= K < Nt (got K=%d, Nt=%d)", K, Nt);
+        kz_set_error("%s: need 1 <= K < Nt (got K=%d, Nt=%d)", fn, K, Nt);
         return KZ_ERR_INVALID_ARG;
     }
-    if (!vr_offset || !vr_len || !H_packed) {
-        kz_set_error("kz_plan_create: NULL vr_offset, vr_len or H_packed");
+    const kz_cf32* Hin = H_packed ? H_packed : H_dense;
+    if (!vr_offset || !vr_len || !Hin) {
+        kz_set_error("%s: NULL vr_offset, vr_len or H", fn);
         return KZ_ERR_INVALID_ARG;
     }
-    if (!aligned(H_packed, 8)) {
-        kz_set_error("kz_plan_create: H_packed must be 8-byte aligned");
+    if (!aligned(Hin, 8)) {
+        kz_set_error("%s: H must be 8-byte aligned", fn);
         return KZ_ERR_INVALID_ARG;
     }
     if (prec != KZ_C64 && prec != KZ_BF16_MIXED) {
-        kz_set_error("kz_plan_create: unknown precision %d", (int)prec);
+        kz_set_error("%s: unknown precision %d", fn, (int)prec);
         return KZ_ERR_INVALID_ARG;
     }
     for (int k = 0; k < K; ++k) {
         const long o = vr_offset[k], L = vr_len[k];
         if (L < 1 || o < 0 || o + L > Nt) {
-            kz_set_error("kz_plan_create: VR of user %d is [%ld, %ld), outside [0, %d) or empty", k, o, o + L, Nt);
+            kz_set_error("%s: VR of user %d is [%ld, %ld), outside [0, %d) or empty", fn, k, o, o + L, Nt);
             return KZ_ERR_INVALID_ARG;
         }
     }
@@ -379,7 +367,7 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     }
     if (acc >= (int64_t)1 << 31) {
         delete P;
-        kz_set_error("kz_plan_create: channel too large (%lld aligned entries)", (long long)acc);
+        kz_set_error("%s: channel too large (%lld aligned entries)", fn, (long long)acc);
         return KZ_ERR_UNSUPPORTED;
     }
     P->total2 = acc;
@@ -476,7 +464,7 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     do {                                                     \
         e = (x);                                             \
         if (e != cudaSuccess) {                              \
-            kz_set_error("kz_plan_create: %s", cudaGetErrorString(e)); \
+            kz_set_error("%s: %s", fn, cudaGetErrorString(e)); \
             delete P;                                        \
             return e == cudaErrorMemoryAllocation ? KZ_ERR_NOMEM : KZ_ERR_CUDA; \
         }                                                    \
@@ -495,8 +483,12 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
     if (prec == KZ_BF16_MIXED) KZ_TRY(cudaMalloc((void**)&P->d_Hb, std::max<int64_t>(acc, 2) * sizeof(__nv_bfloat162)));
     KZ_TRY(cudaMalloc((void**)&P->d_nrm, K * sizeof(float)));
     KZ_TRY(cudaMalloc((void**)&P->d_nrmd, K * sizeof(double)));
-    KZ_TRY(kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, K, acc, P->d_Hc,
-                        P->d_Hb, st));
+    if (H_packed)
+        KZ_TRY(kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, K, acc,
+                            P->d_Hc, P->d_Hb, st));
+    else
+        KZ_TRY(kz_pack_dense(reinterpret_cast<const float2*>(H_dense), Nt, P->d_rows, P->d_rptr, K, P->d_Hc, P->d_Hb,
+                             st));
     KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, st));
     KZ_TRY(cudaMalloc((void**)&P->d_G, std::max<size_t>(P->xidx.size(), 1) * sizeof(float2)));
     KZ_TRY(kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, K, P->d_G, st));
@@ -504,6 +496,33 @@ kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr
 #undef KZ_TRY
     *out = P;
     return KZ_OK;
+}
+
+extern "C" {
+
+kz_status kz_plan_create(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset, const int32_t* vr_len,
+                         const kz_cf32* H_packed, kz_prec prec, void* stream) {
+    if (!H_packed) {
+        g_err.clear();
+        kz_set_error("kz_plan_create: H_packed is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    return plan_build("kz_plan_create", out, K, Nt, vr_offset, vr_len, H_packed, nullptr, prec, stream);
+}
+
+kz_status kz_plan_dense(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_offset, const int32_t* vr_len,
+                        const kz_cf32* H_dense, kz_prec prec, void* stream) {
+    if (!H_dense) {
+        g_err.clear();
+        kz_set_error("kz_plan_dense: H_dense is NULL");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if ((int64_t)K * Nt >= ((int64_t)1 << 40)) {
+        g_err.clear();
+        kz_set_error("kz_plan_dense: K x Nt too large");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    return plan_build("kz_plan_dense", out, K, Nt, vr_offset, vr_len, nullptr, H_dense, prec, stream);
 }
 
 kz_status kz_plan_update(kz_plan* P, const kz_cf32* H_packed, void* stream) {
@@ -588,12 +607,7 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
                         double* resid, int32_t* status, kz_kernel kernel, int32_t rhs_per_cta, int32_t refresh,
                         void* stream) {
     g_err.clear();
-    if (kernel == KZ_KERNEL_DUAL) {
-        if (rhs_per_cta != 0 && rhs_per_cta != 8 && rhs_per_cta != 16) {
-            kz_set_error("kz_precode_ex: the dual kernel takes 0, 8 or 16 columns per CTA");
-            return KZ_ERR_INVALID_ARG;
-        }
-    } else if (kernel == KZ_KERNEL_TC) {
+    if (kernel == KZ_KERNEL_TC) {
         if (rhs_per_cta != 0 && rhs_per_cta != 4 && rhs_per_cta != 8) {
             kz_set_error("kz_precode_ex: the tensor-core kernel takes 0, 4 or 8 columns per CTA");
             return KZ_ERR_INVALID_ARG;
@@ -603,7 +617,7 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         return KZ_ERR_INVALID_ARG;
     }
     kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
-                                    (kernel == KZ_KERNEL_DUAL || kernel == KZ_KERNEL_TC) ? 0 : rhs_per_cta, refresh);
+                                    kernel == KZ_KERNEL_TC ? 0 : rhs_per_cta, refresh);
     if (rc != KZ_OK) return rc;
     if (!s || !x || !iters || !resid) {
         kz_set_error("kz_precode: s, x, iters and resid are required");
@@ -619,26 +633,13 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         kz_set_error("kz_precode: BF16_MIXED is provided for AHK and VR_OAHK only");
         return KZ_ERR_UNSUPPORTED;
     }
-    if (kernel == KZ_KERNEL_DUAL && !dual_ok(algo, prec)) {
-        kz_set_error("kz_precode_ex: the dual kernel runs AHK / VR_OAHK on C64 plans");
-        return KZ_ERR_UNSUPPORTED;
-    }
     if (kernel == KZ_KERNEL_TC && !tc_ok(algo, prec)) {
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
     }
-    int J, nw, cs = 0, trow_single = 0;
+    int J, nw, trow_single = 0;
     size_t smem;
-    if (kernel == KZ_KERNEL_DUAL) {
-        J = rhs_per_cta ? rhs_per_cta : (nrhs >= 16 && dual_cs(16, 16, plan->K, plan->cmax) ? 16 : 8);
-        nw = (J == 16) ? 16 : 8;
-        cs = dual_cs(J, nw, plan->K, plan->cmax);
-        if (cs == 0) {
-            kz_set_error("kz_precode_ex: K = %d does not fit the dual kernel's shared memory", plan->K);
-            return KZ_ERR_UNSUPPORTED;
-        }
-        smem = kz_smem_dual(J, nw, cs, plan->K);
-    } else if (kernel == KZ_KERNEL_TC) {
+    if (kernel == KZ_KERNEL_TC) {
         // 8 columns per CTA only when that still gives every SM a work item
         J = rhs_per_cta ? rhs_per_cta
                         : ((nrhs + 7) / 8 >= plan->sms &&
@@ -682,13 +683,9 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
     L.status = status;
     L.Ntp_max = plan->Ntp;
     L.K_max = plan->K;
-    L.cs = cs;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
-    if (kernel == KZ_KERNEL_DUAL) {
-        const int occ = std::max(1, kz_occupancy_dual(J, nw, smem));
-        e = kz_launch_dual(L, J, nw, std::min(L.n_items, plan->sms * occ), smem, st);
-    } else if (kernel == KZ_KERNEL_TC) {
+    if (kernel == KZ_KERNEL_TC) {
         L.tc = 1;
         L.trow_max = trow_single;
         const int occ = std::max(1, kz_occupancy_ahk_tc(J, nw, smem));
@@ -876,7 +873,6 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
     L.status = status;
     L.Ntp_max = B->Ntp_max;
     L.K_max = B->K_max;
-    L.cs = B->cs;
     L.tc = (B->kernel == KZ_KERNEL_TC);
     L.m_elems = L.tc ? B->m_elems : 0;
     L.trow_max = L.tc ? B->trow_max : 0;
@@ -899,11 +895,8 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
         if (e == cudaSuccess) e = cudaEventRecord(B->ev_join, B->aux);
         if (e != cudaSuccess) return check_launch(e, "kz_precode_batched second launch");
     }
-    if (B->kernel == KZ_KERNEL_DUAL)
-        e = kz_launch_dual(L, B->J, B->nw, B->grid, B->smem, st);
-    else
-        e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
-                                   : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
+    e = is_ahk_family(B->algo) ? kz_launch_ahk(L, B->J, B->nw, B->grid, B->smem, st)
+                               : kz_launch_kacz(L, B->J, B->nw, B->grid, B->smem, st);
     if (e != cudaSuccess) return check_launch(e, "kz_precode_batched launch");
     if (B->n_items2) {
         e = cudaStreamWaitEvent(st, B->ev_join, 0);  // join
@@ -940,10 +933,6 @@ kz_status kz_batch_tune(kz_batch* B, kz_select sel, double tol, int32_t max_iter
         if (J > B->nrhs) continue;
         if (smem_for(B->algo, J, B->Ntp_max, B->K_max, B->prec) > kSmemLimit) continue;
         for (int nw : {8, 16}) cands.push_back({KZ_KERNEL_RESIDENT, J, nw});
-    }
-    if (dual_ok(B->algo, B->prec)) {
-        for (Cand c : {Cand{KZ_KERNEL_DUAL, 8, 8}, Cand{KZ_KERNEL_DUAL, 8, 16}, Cand{KZ_KERNEL_DUAL, 16, 16}})
-            if (dual_cs(c.J, c.nw, B->K_max, B->cmax) > 0) cands.push_back(c);
     }
     if (tc_ok(B->algo, B->prec)) {
         for (int J : {4, 8}) {
@@ -1024,13 +1013,7 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
         return KZ_ERR_INVALID_ARG;
     }
     const int nw = threads / 32;
-    if (kernel == KZ_KERNEL_DUAL) {
-        if (!dual_ok(B->algo, B->prec) || dual_cs(rhs_per_cta, nw, B->K_max, B->cmax) == 0) {
-            kz_set_error("kz_batch_set_launch: the dual kernel needs AHK / VR_OAHK on C64 with 8 or 16 columns "
-                         "that fit shared memory");
-            return KZ_ERR_UNSUPPORTED;
-        }
-    } else if (kernel == KZ_KERNEL_TC) {
+    if (kernel == KZ_KERNEL_TC) {
         if (!tc_ok(B->algo, B->prec) || (rhs_per_cta != 4 && rhs_per_cta != 8) ||
             tc_width(rhs_per_cta, B->Ntp_max, B->Ntp_max, B->K_max) == 0) {
             kz_set_error("kz_batch_set_launch: the tensor-core kernel needs AHK / VR_OAHK on C64 with 4 or 8 "
@@ -1183,19 +1166,22 @@ kz_status kz_precode_adjoint(kz_plan* plan, int32_t nrhs, float xi, const kz_cf3
 
 // ---------------------------------------------------------------------------
 // Allocation-free adjoint.  Some callers cannot allocate device memory at the
-// time they differentiate: a backward pass recorded into a CUDA graph (a
-// device allocation is not a stream operation and would not be replayed), a
-// real-time loop that must not block in the driver's allocator, or a process
-// whose device memory is reserved up front by another allocator.  For them
-// the right-hand side G~ = G_Q + H G_X, the only scratch of the adjoint, lives
-// in this file-scope device array instead of plan-owned memory.
+// time they differentiate: a real-time loop that must not block in the
+// driver's allocator, a process whose device memory is all reserved up front
+// by another allocator (so a cudaMalloc would fail), or a runtime that forbids
+// allocation after start-up.  For them the right-hand side G~ = G_Q + H G_X,
+// the only scratch of the adjoint, lives in this file-scope device array
+// instead of plan-owned memory.  Each device's context holds its own copy.
 namespace {
 
 constexpr int64_t kNoAllocMaxElems = 262144;  // K * nrhs complex entries (2 MiB)
 static __device__ __align__(256) float2 g_kz_adjoint_scratch[kNoAllocMaxElems];
 
 constexpr int kNoAllocMaxDevices = 64;
-float2* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+// Cached device address of the array, per device.  Atomic so that two host
+// threads making their first call on one device do not race: both may look
+// the address up, and both store the same value.
+std::atomic<float2*> g_noalloc_ptr[kNoAllocMaxDevices];
 
 // Host code cannot use the array's name as a device address; fetch the
 // address once per device, with that device current.
@@ -1207,13 +1193,15 @@ kz_status noalloc_scratch(float2** out) {
         kz_set_error("kz_precode_adjoint_noalloc: device %d is beyond the supported %d", dev, kNoAllocMaxDevices);
         return KZ_ERR_UNSUPPORTED;
     }
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_kz_adjoint_scratch);
+    float2* p = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+    if (!p) {
+        void* a = nullptr;
+        e = cudaGetSymbolAddress(&a, g_kz_adjoint_scratch);
         if (e != cudaSuccess) return check_launch(e, "kz_precode_adjoint_noalloc cudaGetSymbolAddress");
-        g_noalloc_ptr[dev] = static_cast<float2*>(p);
+        p = static_cast<float2*>(a);
+        g_noalloc_ptr[dev].store(p, std::memory_order_release);
     }
-    *out = g_noalloc_ptr[dev];
+    *out = p;
     return KZ_OK;
 }
 

@@ -21,6 +21,23 @@ __global__ void pack_rows_kernel(const float2* __restrict__ Hin, const int* __re
     }
 }
 
+// The same packing from a dense K x Nt row-major matrix: row k's VR [o, e)
+// is read from Hd[k * Nt + n]; entries outside the VR are never read (the
+// channel is zero there, eq. (3)).
+__global__ void pack_dense_kernel(const float2* __restrict__ Hd, int Nt, const int4* __restrict__ rows,
+                                  const int* __restrict__ rptr, float2* Hc, __nv_bfloat162* Hb) {
+    const int k = blockIdx.x;
+    const int4 rd = rows[k];  // {a, len2, o, e}
+    const float2* src = Hd + (int64_t)k * Nt;
+    const int dst = rptr[k];
+    for (int p = threadIdx.x; p < rd.y; p += blockDim.x) {
+        const int n = rd.x + p;
+        const float2 h = (n >= rd.z && n < rd.w) ? src[n] : make_float2(0.f, 0.f);
+        Hc[dst + p] = h;
+        if (Hb) Hb[dst + p] = __float22bfloat162_rn(h);
+    }
+}
+
 // ||h_k||^2 with FP64 accumulation (one block per row).
 __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows,
                                  const int* __restrict__ rptr, double* out_d, float* out_f) {
@@ -360,6 +377,12 @@ cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows,
                          int64_t total2, float2* Hc, __nv_bfloat162* Hb, cudaStream_t st) {
     (void)total2;
     pack_rows_kernel<<<K, 256, 0, st>>>(Hin, in_off, rows, rptr, Hc, Hb);
+    return cudaGetLastError();
+}
+
+cudaError_t kz_pack_dense(const float2* Hd, int Nt, const int4* rows, const int* rptr, int K, float2* Hc,
+                          __nv_bfloat162* Hb, cudaStream_t st) {
+    pack_dense_kernel<<<K, 256, 0, st>>>(Hd, Nt, rows, rptr, Hc, Hb);
     return cudaGetLastError();
 }
 

@@ -71,7 +71,6 @@ struct KzLaunch {
     unsigned long long seed;
     int* status;
     int Ntp_max, K_max;
-    int cs;               // dual kernel: staged rows per chunk
     int tc;               // resident kernel: tensor-core inner products (correction form)
     int m_elems;          // resident kernel: shared iterate entries per CTA (0: J x (Ntp_max + pad))
     int trow_max;         // tensor-core kernel: covering-list entries staged in shared memory (0: none)
@@ -93,13 +92,12 @@ int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);
 size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow = 0);
 int kz_occupancy_ahk_tc(int J, int nw, size_t smem);
 int kz_occupancy_kacz(int J, int nw, size_t smem);
-cudaError_t kz_launch_dual(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
-size_t kz_smem_dual(int J, int nw, int CS, int K);
-int kz_occupancy_dual(int J, int nw, size_t smem);
 
 // Auxiliary kernels (kz_aux.cu).
 cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows, const int* rptr, int K,
                          int64_t total2, float2* Hc, __nv_bfloat162* Hb, cudaStream_t st);
+cudaError_t kz_pack_dense(const float2* Hd, int Nt, const int4* rows, const int* rptr, int K, float2* Hc,
+                          __nv_bfloat162* Hb, cudaStream_t st);
 cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d,
                          float* out_f, cudaStream_t st);
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,

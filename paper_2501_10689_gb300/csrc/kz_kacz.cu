@@ -102,8 +102,12 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             for (int j = 0; j < ncols; ++j) {
                 s_iters[j] = L.max_iter;
                 s_sel[j] = -1;
-                if (s_sn2[j] > 0.0) act |= 1 << j;
-                else s_iters[j] = 0;
+                if (s_sn2[j] > 0.0 && isfinite(s_sn2[j])) {
+                    act |= 1 << j;
+                } else {  // a zero column is solved by x = 0; a NaN / Inf one is reported
+                    s_iters[j] = 0;
+                    if (!(s_sn2[j] == 0.0)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+                }
             }
             s_active = act;
             s_pending = 0;
@@ -231,8 +235,9 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                                 sel = warp_pick(K, u, [&](int i) { return (double)d_s[i]; });
                             else
                                 sel = warp_pick(K, u, [&](int i) { return 1.0; });
-                            const int4 rd = I.rows[sel];
-                            const int base = I.rptr[sel];
+                            // no positive weight (every d_i NaN): sel < 0 stops the column below
+                            const int4 rd = sel >= 0 ? I.rows[sel] : make_int4(0, 0, 0, 0);
+                            const int base = sel >= 0 ? I.rptr[sel] : 0;
                             float ax = 0.f, ay = 0.f;
                             for (int p = 2 * lane; p < rd.y; p += 64) {
                                 const float4 h = h_pair<false>(I, base + p);
@@ -242,7 +247,8 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                             }
                             ax = warp_sum(ax);
                             ay = warp_sum(ay);
-                            const float2 bv = b_s[sel * J + j], qv = q_s[sel * J + j];
+                            const float2 bv = sel >= 0 ? b_s[sel * J + j] : make_float2(0.f, 0.f);
+                            const float2 qv = sel >= 0 ? q_s[sel * J + j] : make_float2(0.f, 0.f);
                             r = make_float2(bv.x - ax - xi * qv.x, bv.y - ay - xi * qv.y);
                         } else {
                             if (L.sel == KZ_SEL_ARGMAX) {

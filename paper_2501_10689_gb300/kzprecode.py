@@ -46,12 +46,12 @@ class KzBatchItem(ctypes.Structure):
                 ("xi", ctypes.c_float)]
 
 
-EXPORTS = ("kz_plan_create", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
+EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_query",
            "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
-KERNELS = {"auto": 0, "resident": 1, "dual": 2, "tc": 3}
+KERNELS = {"auto": 0, "resident": 1, "tc": 3}
 
 
 def library_path() -> str:
@@ -71,6 +71,8 @@ def load():
                                   ctypes.c_double, ctypes.c_uint64)
     lib.kz_plan_create.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_create.restype = I32
+    lib.kz_plan_dense.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
+    lib.kz_plan_dense.restype = I32
     lib.kz_sum_rate.argtypes = [P, P, F64, P, P, P]
     lib.kz_sum_rate.restype = I32
     lib.kz_sum_rate_batched.argtypes = [P, F64, P, P, P]
@@ -165,6 +167,20 @@ def kz_plan_create(K, Nt, vr_offset, vr_len, H_packed, prec="c64", stream=None) 
     h = ctypes.c_void_p()
     _check(lib.kz_plan_create(ctypes.byref(h), K, Nt, off.ctypes.data_as(ctypes.c_void_p),
                               ln.ctypes.data_as(ctypes.c_void_p), _ptr(H_packed), PREC[prec], _stream(stream)))
+    return Plan(h, K, Nt, int(ln.sum()), prec)
+
+
+def kz_plan_dense(K, Nt, vr_offset, vr_len, H_dense, prec="c64", stream=None) -> Plan:
+    """Plan from a dense (K, Nt) complex64 CUDA tensor (only VR entries are read)."""
+    lib = load()
+    off = np.ascontiguousarray(vr_offset, dtype=np.int32)
+    ln = np.ascontiguousarray(vr_len, dtype=np.int32)
+    if off.shape != (K,) or ln.shape != (K,):
+        raise ValueError("vr_offset and vr_len must have K entries")
+    _check_c64(H_dense, (K, Nt), "H_dense")
+    h = ctypes.c_void_p()
+    _check(lib.kz_plan_dense(ctypes.byref(h), K, Nt, off.ctypes.data_as(ctypes.c_void_p),
+                             ln.ctypes.data_as(ctypes.c_void_p), _ptr(H_dense), PREC[prec], _stream(stream)))
     return Plan(h, K, Nt, int(ln.sum()), prec)
 
 
@@ -309,8 +325,9 @@ def kz_precode_adjoint(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam,
 def kz_precode_adjoint_noalloc(plan: Plan, nrhs, xi, Q, X, G_Q, G_X, tol, max_iter, lam, y, grad_H_packed, grad_xi,
                                iters, resid, status=None, stream=None):
     """The adjoint without device allocation (for callers that cannot allocate
-    when they differentiate, e.g. inside a captured CUDA graph); its scratch is a
-    fixed 2 MiB device array shared by all calls, so K * nrhs <= 262144."""
+    when they differentiate, e.g. a real-time loop or a process whose device
+    memory is reserved by another allocator); its scratch is a fixed 2 MiB
+    device array shared by all calls on a device, so K * nrhs <= 262144."""
     lib = load()
     return _check(lib.kz_precode_adjoint_noalloc(plan.handle, nrhs, float(xi), _ptr(Q), _ptr(X), _ptr(G_Q),
                                                  _ptr(G_X), float(tol), int(max_iter), _ptr(lam), _ptr(y),

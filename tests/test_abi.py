@@ -95,3 +95,24 @@ def test_batch_query_and_launch_reject_null(lib):
     assert rc == KZ_ERR_INVALID_ARG and "batch" in lib.kz_last_error().decode()
     assert lib.kz_batch_set_launch(None, 3, 8, 512, None) == KZ_ERR_INVALID_ARG
     assert lib.kz_batch_rebind(None, None, None) == KZ_ERR_INVALID_ARG
+
+
+def test_plan_dense_rejects_bad_input(lib):
+    """kz_plan_dense validates like kz_plan_create, on the host, before any CUDA call."""
+    import numpy as np
+    from paper_2501_10689_gb300.kzprecode import KZ_ERR_INVALID_ARG
+
+    def dense(K, Nt, off, ln, H=FAKE):
+        o = np.asarray(off, dtype=np.int32)
+        l = np.asarray(ln, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = lib.kz_plan_dense(ctypes.byref(h), K, Nt, o.ctypes.data_as(ctypes.c_void_p),
+                               l.ctypes.data_as(ctypes.c_void_p), H, 0, None)
+        return rc, lib.kz_last_error().decode()
+
+    assert dense(4, 4, [0] * 4, [1] * 4)[0] == KZ_ERR_INVALID_ARG      # K >= Nt
+    rc, msg = dense(2, 8, [0, 5], [3, 4])                               # VR past the array
+    assert rc == KZ_ERR_INVALID_ARG and "kz_plan_dense" in msg
+    rc, msg = dense(2, 8, [0, 1], [3, 4], H=None)
+    assert rc == KZ_ERR_INVALID_ARG and "H_dense" in msg
+    assert dense(2, 8, [0, 1], [3, 4], H=ctypes.c_void_p(0x10004))[0] == KZ_ERR_INVALID_ARG  # misaligned

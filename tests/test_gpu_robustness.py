@@ -1,0 +1,192 @@
+"""Full-size parity of the benchmarked launch, corrupted inputs, dense plans and
+full-size gradients (GB300, through the C ABI).
+
+* The 512-channel, 16-column batch the benchmark times, run in the launch the
+  benchmark runs (``kz_batch_tune`` on the batch, and the tensor-core J = 8
+  launch it picks): every channel's x and v against the FP64 RZF at 1e-5
+  (eq. (precoding), Thm. 1).
+* NaN in one entry of H, and separately in one entry of s, on the FP32
+  resident kernel, the tensor-core kernel and the Kaczmarz row kernel: the call
+  returns, and the status word carries KZ_STATUS_BIT_NUMERIC.  (The corruption
+  is made on the host; nothing here faults the GPU.)
+* A plan built from a dense K x Nt matrix solves bit-identically to the plan
+  built from the same VR entries packed (Sec. II, eqs. (3)-(4)).
+* The batched gradient on config-5-sized channels against the FP64 dense-RZF
+  autograd gradient at 1e-4, and the per-channel backward raising when its
+  adjoint solve does not converge or meets a NaN.
+"""
+import numpy as np
+import pytest
+
+import kzgen
+from oracle import adjoint as oadj
+from oracle import rzf as orz
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL_X = 1e-5
+
+
+@pytest.fixture(scope="module")
+def kp():
+    import __graft_entry__
+    __graft_entry__.build()
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2501_10689_gb300 import kzprecode
+    return kzprecode
+
+
+# ---------------------------------------------------------------- full-size benchmark batch
+@pytest.fixture(scope="module")
+def config3_batch(kp):
+    import bench
+    insts = kzgen.config3(bench.N_INST)
+    items = []
+    for inst in insts:
+        p = kp.plan_from_instance(inst)
+        items.append(dict(plan=p, s=kp.rhs_tensor(inst.S),
+                          x=torch.empty((bench.NRHS, inst.Nt), dtype=torch.complex64, device="cuda"),
+                          v=torch.empty((bench.NRHS, inst.K), dtype=torch.complex64, device="cuda"),
+                          iters=torch.empty(bench.NRHS, dtype=torch.int32, device="cuda"),
+                          resid=torch.empty(bench.NRHS, dtype=torch.float64, device="cuda"), xi=inst.xi))
+    ref = [orz.rzf(inst.dense(), inst.xi, inst.S) for inst in insts]
+    return insts, items, ref
+
+
+def _check_all(kp, insts, items, ref, tol):
+    worst_x = worst_v = 0.0
+    for inst, it, (V, X) in zip(insts, items, ref):
+        ex = orz.rel_err(it["x"].cpu().numpy().T, X)
+        ev = orz.rel_err(it["v"].cpu().numpy().T, V)
+        worst_x, worst_v = max(worst_x, float(ex.max())), max(worst_v, float(ev.max()))
+        assert np.all(it["resid"].cpu().numpy() <= tol * (1 + 1e-6))
+    assert worst_x <= TOL_X and worst_v <= TOL_X, (worst_x, worst_v)
+
+
+@pytest.mark.parametrize("launch", ["bench", ("tc", 8, 512)])
+def test_benchmark_batch_every_channel(kp, config3_batch, launch):
+    """All 512 channels (8192 columns) of the benchmark batch, in the launch the
+    benchmark times (autotuned as bench.py does) and in the tensor-core J = 8 launch."""
+    import bench
+    insts, items, ref = config3_batch
+    b = kp.kz_batch_prepare(items, bench.NRHS, "vr_oahk")
+    if launch == "bench":
+        kp.kz_batch_tune(b, "paper", bench.TOL, bench.MAX_ITER, 0)
+    else:
+        kp.kz_batch_set_launch(b, *launch)
+    for it in items:
+        it["x"].zero_()
+        it["v"].zero_()
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_batched(b, "paper", bench.TOL, bench.MAX_ITER, 0, status=st)
+    torch.cuda.synchronize()
+    assert st.item() == 0
+    _check_all(kp, insts, items, ref, bench.TOL)
+
+
+# ---------------------------------------------------------------- corrupted inputs
+def _nan_case(kp, where, algo, sel, kernel):
+    inst = kzgen.make_instance(81, 24, 400, vr_len_range=(40, 160), nrhs=8, snr_db=10.0)
+    Hp = inst.H_packed.copy()
+    S = inst.S.copy()
+    if where == "H":
+        Hp[int(inst.vr_len[:5].sum()) + 7] = np.complex64(complex(np.nan, 0.0))  # user 5, 8th VR entry
+    else:
+        S[3, 2] = np.complex64(complex(0.0, np.nan))
+    plan = kp.kz_plan_create(inst.K, inst.Nt, inst.vr_offset, inst.vr_len, torch.from_numpy(Hp).cuda())
+    out = {}
+    x = torch.empty((8, inst.Nt), dtype=torch.complex64, device="cuda")
+    v = torch.empty((8, inst.K), dtype=torch.complex64, device="cuda")
+    iters = torch.empty(8, dtype=torch.int32, device="cuda")
+    resid = torch.empty(8, dtype=torch.float64, device="cuda")
+    status = torch.zeros(1, dtype=torch.int32, device="cuda")
+    kp.kz_precode_ex(plan, kp.rhs_tensor(S), 8, inst.xi, algo, sel, 1e-6, 200, 0, x, v, iters, resid, status,
+                     kernel, 0, 0)
+    torch.cuda.synchronize()
+    out["status"] = int(status.item())
+    out["iters"] = iters.cpu().numpy()
+    return out
+
+
+@pytest.mark.parametrize("where", ["H", "s"])
+@pytest.mark.parametrize("algo,sel,kernel", [("vr_oahk", "paper", "resident"), ("vr_oahk", "paper", "tc"),
+                                             ("ahk", "paper", "tc"), ("grk", "paper", "auto"),
+                                             ("vr_ogrk", "argmax", "auto"), ("rk_energy", "paper", "auto")])
+def test_nan_input_sets_numeric_bit(kp, where, algo, sel, kernel):
+    out = _nan_case(kp, where, algo, sel, kernel)
+    assert out["status"] & kp.KZ_STATUS_BIT_NUMERIC, out
+
+
+# ---------------------------------------------------------------- dense plans
+@pytest.mark.parametrize("prec", ["c64", "bf16"])
+def test_dense_plan_matches_packed_plan_bitwise(kp, prec):
+    inst = kzgen.make_instance(91, 30, 513, vr_len_range=(37, 201), nrhs=6, snr_db=10.0)
+    D = inst.dense().copy()
+    # entries outside the VRs are not part of the channel (eq. (3)): fill them
+    # with garbage, which kz_plan_dense must never read
+    mask = np.zeros_like(D, dtype=bool)
+    for k in range(inst.K):
+        mask[k, inst.vr_offset[k]:inst.vr_offset[k] + inst.vr_len[k]] = True
+    D[~mask] = np.complex64(1e3 + 1e3j)
+    pd = kp.kz_plan_dense(inst.K, inst.Nt, inst.vr_offset, inst.vr_len, torch.from_numpy(D).cuda(), prec=prec)
+    pp = kp.plan_from_instance(inst, prec=prec)
+    assert kp.kz_plan_query(pd)[0].tolist() == kp.kz_plan_query(pp)[0].tolist()
+    S = kp.rhs_tensor(inst.S)
+    for algo in (("vr_oahk", "paper"), ("grk", "argmax")):
+        if prec == "bf16" and algo[0] == "grk":
+            continue
+        a = kp.precode(pd, S, inst.xi, algo=algo[0], sel=algo[1], tol=1e-7, max_iter=20000)
+        b = kp.precode(pp, S, inst.xi, algo=algo[0], sel=algo[1], tol=1e-7, max_iter=20000)
+        assert torch.equal(a["x"], b["x"]) and torch.equal(a["iters"], b["iters"])
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        assert np.all(orz.rel_err(a["x"].cpu().numpy().T, X) <= TOL_X)
+
+
+# ---------------------------------------------------------------- gradients
+def test_batched_gradient_config5_size_vs_fp64(kp):
+    """Four channels of the gradient workload (Nt = 2048, K = 128, VR 256-1024,
+    identity symbols), batched forward + adjoint in the tuned launch, against
+    the FP64 dense-RZF autograd gradient at 1e-4."""
+    from paper_2501_10689_gb300 import autograd as kad
+    insts = [kzgen.config5_instance(i) for i in range(4)]
+    pre = kad.BatchedPrecoder([(i.vr_offset, i.vr_len, i.Nt) for i in insts], nrhs=128, tol=1e-6, max_iter=3000)
+    H = torch.tensor(np.concatenate([i.H_packed for i in insts]), device="cuda", requires_grad=True)
+    xi = torch.tensor([i.xi for i in insts], dtype=torch.float32, device="cuda", requires_grad=True)
+    S = torch.cat([kp.rhs_tensor(i.S).reshape(-1) for i in insts])
+    X, V = pre(H, xi, S)
+    snr = 10.0 ** (insts[0].snr_db / 10.0)
+    L = kad.sum_rate_loss_batched(pre.dense(H), X.view(len(insts), 128, -1), snr)
+    L.backward()
+    gH = H.grad.cpu().numpy().astype(np.complex128)
+    gxi = xi.grad.cpu().numpy()
+    off = 0
+    for c, inst in enumerate(insts):
+        L_ref, gH_ref, gxi_ref = oadj.reference_gradient(inst)
+        n = inst.H_packed.size
+        assert np.linalg.norm(gH[off:off + n] - gH_ref) <= 1e-4 * np.linalg.norm(gH_ref), c
+        assert abs(gxi[c] - gxi_ref) <= 1e-4 * abs(gxi_ref), c
+        off += n
+
+
+def test_backward_raises_when_adjoint_does_not_converge(kp):
+    from paper_2501_10689_gb300 import autograd as kad
+    inst = kzgen.make_instance(5, 8, 96, vr_len_range=(12, 40), nrhs=8, rhs="identity", snr_db=20.0)
+    Hp = torch.tensor(inst.H_packed, device="cuda", requires_grad=True)
+    S = kp.rhs_tensor(inst.S)
+    X, V = kad.precode(Hp, inst.xi, S, inst.vr_offset, inst.vr_len, inst.Nt, tol=1e-7, adj_max_iter=1)
+    L = kad.sum_rate_loss(kad.dense_from_packed(Hp, inst.vr_offset, inst.vr_len, inst.Nt), X, 10.0)
+    with pytest.raises(kp.KzError, match="did not converge"):
+        L.backward()
+
+
+def test_backward_raises_on_nan_gradient(kp):
+    from paper_2501_10689_gb300 import autograd as kad
+    inst = kzgen.make_instance(6, 8, 96, vr_len_range=(12, 40), nrhs=8, rhs="identity", snr_db=10.0)
+    Hp = torch.tensor(inst.H_packed, device="cuda", requires_grad=True)
+    X, V = kad.precode(Hp, inst.xi, kp.rhs_tensor(inst.S), inst.vr_offset, inst.vr_len, inst.Nt, tol=1e-7)
+    g = torch.zeros_like(X)
+    g[2, 5] = complex(float("nan"), 0.0)
+    with pytest.raises(kp.KzError, match="NaN"):
+        X.backward(g)

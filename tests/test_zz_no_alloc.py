@@ -1,12 +1,13 @@
 """The allocation-free adjoint against the allocating one (GB300).
 
 kz_precode_adjoint_noalloc serves callers that cannot allocate device memory
-when they differentiate (a backward pass captured into a CUDA graph, a
-real-time loop that must not block in the driver's allocator, or a process
-whose memory is reserved up front by another allocator): its scratch is a
-fixed device array inside the library.  Both entry points must give the same
-lambda, y, grad_H and grad_xi, on two calls in a row (the shared array keeps
-the previous call's contents, which must not leak into the next).
+when they differentiate (a real-time loop that must not block in the driver's
+allocator, a process whose device memory is reserved up front by another
+allocator, or a runtime that forbids allocation after start-up): its scratch
+is a fixed device array inside the library.  Both entry points must give the
+same lambda, y, grad_H and grad_xi, on two calls in a row (the shared array
+keeps the previous call's contents, which must not leak into the next), after
+a larger problem, with only G_Q given, and at exactly the array's size.
 """
 import numpy as np
 import pytest
@@ -77,3 +78,36 @@ def test_noalloc_adjoint_rejects_oversized_problem(kp):
     X = torch.zeros((nrhs, 1200), dtype=torch.complex64, device="cuda")
     with pytest.raises(kp.KzError, match="exceeds the static scratch"):
         _adjoint(kp, kp.kz_precode_adjoint_noalloc, plan, nrhs, inst.xi, V, X, V, X)
+
+
+def _random_like(rng, t):
+    return torch.tensor((rng.normal(size=t.shape) + 1j * rng.normal(size=t.shape)).astype(np.complex64),
+                        device="cuda")
+
+
+def _compare(kp, inst, nrhs, rng, with_gx=True, tol=1e-7):
+    plan = kp.plan_from_instance(inst)
+    S = kp.rhs_tensor(inst.S)
+    fwd = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=tol, max_iter=4000)
+    V, X = fwd["v"], fwd["x"]
+    gV = _random_like(rng, V)
+    gX = _random_like(rng, X) if with_gx else None
+    ref = _adjoint(kp, kp.kz_precode_adjoint, plan, nrhs, inst.xi, V, X, gV, gX)
+    got = _adjoint(kp, kp.kz_precode_adjoint_noalloc, plan, nrhs, inst.xi, V, X, gV, gX)
+    assert got["status"][0] == 0 and ref["status"][0] == 0
+    for k in ("lam", "y", "gH", "gxi"):
+        assert _close(got[k], ref[k]), k
+    np.testing.assert_array_equal(got["iters"], ref["iters"])
+
+
+def test_noalloc_adjoint_full_array_then_smaller_gq_only(kp):
+    """A call at exactly the array's size (K * nrhs = 256 * 1024 = 262144),
+    then calls with far fewer entries, the first with only G_Q (its right-hand
+    side is copied into the array, not formed): the full call's entries beyond
+    the later calls' K * nrhs must not reach them."""
+    rng = np.random.default_rng(13)
+    full = kzgen.make_instance(33, 256, 640, vr_len_range=(20, 60), nrhs=1024, snr_db=10.0)
+    _compare(kp, full, 1024, rng, tol=1e-6)
+    small = kzgen.make_instance(32, 9, 200, vr_len_range=(30, 90), nrhs=5, snr_db=10.0)
+    _compare(kp, small, 5, rng, with_gx=False)
+    _compare(kp, small, 5, rng, with_gx=True)
