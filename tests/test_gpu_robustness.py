@@ -187,6 +187,6 @@ def test_backward_raises_on_nan_gradient(kp):
     Hp = torch.tensor(inst.H_packed, device="cuda", requires_grad=True)
     X, V = kad.precode(Hp, inst.xi, kp.rhs_tensor(inst.S), inst.vr_offset, inst.vr_len, inst.Nt, tol=1e-7)
     g = torch.zeros_like(X)
-    g[2, 5] = complex(float("nan"), 0.0)
+    g[2, int(inst.vr_offset[0]) + 1] = complex(float("nan"), 0.0)  # an antenna user 0 sees: H G_X carries it
     with pytest.raises(kp.KzError, match="NaN"):
         X.backward(g)
