@@ -59,6 +59,7 @@ typedef enum {
 /* Bits the kernels OR into the optional device status word. */
 #define KZ_STATUS_BIT_NOT_CONVERGED 1
 #define KZ_STATUS_BIT_NUMERIC 2
+#define KZ_STATUS_BIT_TIMEOUT 4  /* a bounded device wait expired (the call's outputs are not valid) */
 
 /* Methods.  RK_ENERGY / RK_UNIFORM: Alg. 1 with p_i = ||b_i||^2/||B||_F^2 or 1/K
  * (Sec. III-A).  GRK: greedy selection with every residual recomputed
@@ -96,10 +97,22 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * (the V-row residuals and H_V^H phi) on the tensor cores in TF32 with FP32
  * sums; the right-hand side b = s - H m_ref is recomputed from the complex64
  * H every `refresh` iterations and every stop is confirmed on the true
- * residual, so results meet the same tolerance as RESIDENT.  AUTO: RESIDENT
+ * residual, so results meet the same tolerance as RESIDENT.  GROUP (AHK /
+ * VR_OAHK, one channel shared by many columns) spreads one channel over a
+ * group of CTAs -- each owns a 128-antenna block of the iterate for 16, 32
+ * or 64 columns and keeps the block's rows in shared memory -- and runs both
+ * contractions of each half-step on the Blackwell tensor cores (tcgen05.mma,
+ * FP32 accumulators in tensor memory) with 16-bit operands: FP16 (H scaled
+ * by a power of two) on C64 plans, BF16 on BF16_MIXED plans; in correction
+ * form with the refresh through the plan's inner products of overlapping
+ * rows, every stop confirmed on the true residual.  A group is one cluster of
+ * CTAs for channels up to 2048 antennas, else every CTA of a cooperative
+ * launch (then one launch serves at most SMs / blocks groups; more columns
+ * take further launches).  KZ_ERR_UNSUPPORTED when a 128-antenna block is
+ * seen by more than 256 users.  AUTO: RESIDENT
  * for kz_precode; the batch default is RESIDENT until kz_batch_tune or
  * kz_batch_set_launch chooses. */
-typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_TC = 3 } kz_kernel;
+typedef enum { KZ_KERNEL_AUTO = 0, KZ_KERNEL_RESIDENT = 1, KZ_KERNEL_TC = 3, KZ_KERNEL_GROUP = 4 } kz_kernel;
 
 typedef struct kz_plan kz_plan;
 typedef struct kz_batch kz_batch;

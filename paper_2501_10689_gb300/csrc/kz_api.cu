@@ -50,6 +50,28 @@ void kz_set_error(const char* fmt, ...) {
     g_err = buf;
 }
 
+// Set-up of the group kernel (built on its first use): per 128-antenna block
+// the rows meeting it and their 16-bit tile image, the compact index of the
+// residual partial sums, and the kernel's scratch (grown on demand).
+struct GrpPlan {
+    bool built = false;
+    int fmt = -1, AB = 0, rtmax = 1, n_slots = 0;
+    int *d_slot = nullptr, *d_nrt = nullptr, *d_nb = nullptr, *d_coff = nullptr, *d_cptr = nullptr,
+        *d_cidx = nullptr;
+    long long* d_toff = nullptr;
+    unsigned char* d_inF = nullptr;
+    uint8_t* d_tiles = nullptr;
+    float* d_stat = nullptr;
+    void* d_scr = nullptr;
+    size_t scr_bytes = 0;
+    void release() {
+        void* ps[] = {d_slot, d_nrt, d_nb, d_coff, d_cptr, d_cidx, d_toff, d_inF, d_tiles, d_stat, d_scr};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+        *this = GrpPlan();
+    }
+};
+
 struct kz_plan {
     int K = 0, Nt = 0, Ntp = 0, ntiles = 0, nF = 0;
     int cmax = 0;  // largest number of rows covering one tile
@@ -76,12 +98,15 @@ struct kz_plan {
     float2* d_scratch = nullptr;  // adjoint right-hand side G~ (grown on demand)
     size_t scratch_elems = 0;
     int sms = 1;
+    std::vector<int> vr_off, vr_len;  // the caller's VRs
+    GrpPlan grp;
 
     ~kz_plan() {
         void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
                       d_tptr, d_tnv, d_trow4, d_vsort, d_G, d_Hc, d_Hb, d_scratch};
         for (void* p : ps)
             if (p) cudaFree(p);
+        grp.release();
     }
 
     KzInst inst() const {
@@ -298,6 +323,197 @@ kz_status check_launch(cudaError_t e, const char* what) {
     return KZ_OK;
 }
 
+KzGrpChan grp_chan(const kz_plan* P) {
+    const GrpPlan& G = P->grp;
+    KzGrpChan C;
+    memset(&C, 0, sizeof(C));
+    C.K = P->K;
+    C.Nt = P->Nt;
+    C.AB = G.AB;
+    C.n_slots = G.n_slots;
+    C.slot_row = G.d_slot;
+    C.blk_nrt = G.d_nrt;
+    C.blk_nb = G.d_nb;
+    C.blk_coff = G.d_coff;
+    C.blk_toff = G.d_toff;
+    C.tiles = G.d_tiles;
+    C.cptr = G.d_cptr;
+    C.cidx = G.d_cidx;
+    C.nrm = P->d_nrm;
+    C.inF = G.d_inF;
+    C.xptr = P->d_xptr;
+    C.xidx = P->d_xidx;
+    C.G = P->d_G;
+    C.Hc = P->d_Hc;
+    C.rows = P->d_rows;
+    C.rptr = P->d_rptr;
+    C.stat = G.d_stat;
+    return C;
+}
+
+// The group kernel's set-up for operand format fmt (0 FP16, 1 BF16): rows per
+// 128-antenna block from the VRs, tile images filled on `st`.
+kz_status build_grp(kz_plan* P, int fmt, cudaStream_t st) {
+    GrpPlan& G = P->grp;
+    if (G.built && G.fmt == fmt) return KZ_OK;
+    const int K = P->K, AB = (P->Nt + 127) / 128;
+    std::vector<int> nb(AB, 0);
+    for (int k = 0; k < K; ++k)
+        for (int b = P->vr_off[k] / 128; b <= (P->vr_off[k] + P->vr_len[k] - 1) / 128; ++b) ++nb[b];
+    for (int b = 0; b < AB; ++b)
+        if (nb[b] > 256) {
+            kz_set_error("group kernel: antennas [%d, %d) are seen by %d users (at most 256 per 128-antenna block)",
+                         128 * b, 128 * b + 128, nb[b]);
+            return KZ_ERR_UNSUPPORTED;
+        }
+    std::vector<int> nrt(AB), coff(AB), cnt(AB, 0), slot((size_t)AB * 256, -1), cptr(K + 1, 0), cidx;
+    std::vector<long long> toff(AB);
+    int rtmax = 1, n_slots = 0;
+    long long bytes = 0;
+    for (int b = 0; b < AB; ++b) {
+        nrt[b] = std::max(1, (nb[b] + 127) / 128);
+        rtmax = std::max(rtmax, nrt[b]);
+        coff[b] = n_slots;
+        n_slots += nb[b];
+        toff[b] = bytes;
+        bytes += 2LL * 128 * nrt[b] * 256;
+    }
+    for (int k = 0; k < K; ++k) {
+        for (int b = P->vr_off[k] / 128; b <= (P->vr_off[k] + P->vr_len[k] - 1) / 128; ++b) {
+            slot[(size_t)b * 256 + cnt[b]] = k;
+            cidx.push_back(coff[b] + cnt[b]);
+            ++cnt[b];
+        }
+        cptr[k + 1] = (int)cidx.size();
+    }
+    std::vector<unsigned char> inF(K, 0);
+    for (int k : P->F) inF[k] = 1;
+    G.release();
+    cudaError_t e = cudaSuccess;
+#define GRP_TRY(x)              \
+    do {                        \
+        e = (x);                \
+        if (e != cudaSuccess) { \
+            G.release();        \
+            return check_launch(e, "group kernel set-up"); \
+        }                       \
+    } while (0)
+    GRP_TRY(upload(&G.d_slot, slot, st));
+    GRP_TRY(upload(&G.d_nrt, nrt, st));
+    GRP_TRY(upload(&G.d_nb, nb, st));
+    GRP_TRY(upload(&G.d_coff, coff, st));
+    GRP_TRY(upload(&G.d_toff, toff, st));
+    GRP_TRY(upload(&G.d_cptr, cptr, st));
+    GRP_TRY(upload(&G.d_cidx, cidx, st));
+    GRP_TRY(upload(&G.d_inF, inF, st));
+    GRP_TRY(cudaMalloc((void**)&G.d_tiles, (size_t)bytes));
+    GRP_TRY(cudaMalloc((void**)&G.d_stat, 2 * sizeof(float)));
+    G.AB = AB;
+    G.rtmax = rtmax;
+    G.n_slots = n_slots;
+    G.fmt = fmt;
+    GRP_TRY(kz_grp_prepare(grp_chan(P), P->d_Hc, P->total2, P->d_rows, P->d_rptr, P->d_nrm, G.d_stat, fmt, st));
+    GRP_TRY(cudaStreamSynchronize(st));  // the host vectors above are released on return
+#undef GRP_TRY
+    G.built = true;
+    return KZ_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) / 256 * 256; }
+
+// One group-kernel solve (possibly several launches over column chunks).
+kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo, double tol, int max_iter,
+                  kz_cf32* x, kz_cf32* v, int32_t* iters, double* resid, int32_t* status, int rhs_per_cta,
+                  int refresh, cudaStream_t st) {
+    const int fmt = (P->prec == KZ_BF16_MIXED) ? 1 : 0;
+    kz_status rc = build_grp(P, fmt, st);
+    if (rc != KZ_OK) return rc;
+    GrpPlan& G = P->grp;
+    const int AB = G.AB, sms = P->sms;
+    const bool cluster = AB <= 16;
+    const int rpc = (P->K + AB - 1) / AB;
+    const size_t smem_limit = 227 * 1024 - 12 * 1024;  // the kernel's static shared memory is below 12 KiB
+    int NC = 0;
+    for (int nc : {16, 32, 64}) {
+        if (rhs_per_cta && nc != rhs_per_cta) continue;
+        if ((G.rtmax + 2) * 2 * nc > 512 || kz_grp_smem(nc, G.rtmax, rpc) > smem_limit) continue;
+        NC = nc;
+        if (rhs_per_cta || (long)AB * ((nrhs + nc - 1) / nc) <= sms) break;  // smallest width that fills the GPU once
+    }
+    if (NC == 0) {
+        kz_set_error("group kernel: %s", rhs_per_cta ? "rhs_per_cta must be 0, 16, 32 or 64 and fit" :
+                                                       "the channel's tiles do not fit shared memory");
+        return rhs_per_cta ? KZ_ERR_INVALID_ARG : KZ_ERR_UNSUPPORTED;
+    }
+    int tcols = 32;
+    while (tcols < (G.rtmax + 2) * 2 * NC) tcols *= 2;
+    // A CTA that holds more than half of the SM's 512 tensor-memory columns
+    // must never share its SM (a second CTA's allocation would wait for the
+    // first, which may wait for it at a group barrier): its shared memory is
+    // padded past half of the SM's 228 KiB.
+    const size_t smem = std::max(kz_grp_smem(NC, G.rtmax, rpc), tcols > 256 ? (size_t)120 * 1024 : (size_t)0);
+    const int CG_all = (nrhs + NC - 1) / NC;
+    const int CG = cluster ? CG_all : std::min(CG_all, sms / AB);
+    if (CG < 1 || !kz_grp_fits(AB, cluster ? 1 : CG, cluster, smem)) {
+        kz_set_error("group kernel: %d blocks of 128 antennas cannot be resident at once", AB);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    // scratch
+    const size_t b_pp = align256((size_t)CG * G.n_slots * NC * sizeof(float2));
+    const size_t b_phi = align256((size_t)CG * P->K * 2 * NC * sizeof(uint16_t));
+    const size_t b_q = align256((size_t)CG * P->K * NC * sizeof(float2));
+    const size_t b_cp = align256((size_t)CG * 7 * AB * NC * sizeof(float));
+    const size_t b_bar = align256((size_t)(1 + CG) * sizeof(unsigned));
+    const size_t need = b_pp + b_phi + b_q + b_cp + b_bar;
+    if (G.scr_bytes < need) {
+        if (G.d_scr) cudaFree(G.d_scr);
+        G.d_scr = nullptr;
+        G.scr_bytes = 0;
+        cudaError_t e = cudaMalloc(&G.d_scr, need);
+        if (e != cudaSuccess) {
+            kz_set_error("group kernel scratch: %s", cudaGetErrorString(e));
+            return KZ_ERR_NOMEM;
+        }
+        G.scr_bytes = need;
+    }
+    uint8_t* base = static_cast<uint8_t*>(G.d_scr);
+    KzGrpLaunch L;
+    memset(&L, 0, sizeof(L));
+    L.C = grp_chan(P);
+    L.xi = xi;
+    L.NC = NC;
+    L.algo = algo;
+    L.fmt = fmt;
+    L.tol = tol;
+    L.max_iter = max_iter;
+    L.refresh = refresh ? refresh : 8;
+    L.status = status;
+    L.Ppart = reinterpret_cast<float2*>(base);
+    L.Phi = reinterpret_cast<uint16_t*>(base + b_pp);
+    L.Qg = reinterpret_cast<float2*>(base + b_pp + b_phi);
+    L.colpart = reinterpret_cast<float*>(base + b_pp + b_phi + b_q);
+    L.gbar = reinterpret_cast<unsigned*>(base + b_pp + b_phi + b_q + b_cp);
+    L.rpc = rpc;
+    L.rtmax = G.rtmax;
+    L.tmem_cols = tcols;
+    // column chunks of CG groups, one launch each
+    for (int c0 = 0; c0 < nrhs; c0 += CG * NC) {
+        const int n = std::min(nrhs - c0, CG * NC);
+        L.nrhs = n;
+        L.CG = (n + NC - 1) / NC;
+        L.s = reinterpret_cast<const float2*>(s) + (size_t)c0 * P->K;
+        L.x = reinterpret_cast<float2*>(x) + (size_t)c0 * P->Nt;
+        L.v = v ? reinterpret_cast<float2*>(v) + (size_t)c0 * P->K : nullptr;
+        L.iters = iters + c0;
+        L.resid = resid + c0;
+        cudaError_t e = cudaMemsetAsync(L.gbar, 0, sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.gbar + 1, 0xff, (size_t)L.CG * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = kz_launch_grp(L, cluster, smem, st);
+        if (e != cudaSuccess) return check_launch(e, "group kernel launch");
+    }
+    return KZ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -372,6 +588,8 @@ static kz_status plan_build(const char* fn, kz_plan** out, int32_t K, int32_t Nt
     }
     P->total2 = acc;
     P->sumL = acc_in;
+    P->vr_off.assign(vr_offset, vr_offset + K);
+    P->vr_len.assign(vr_len, vr_len + K);
 
     // orthogonal set F: earliest-end greedy on the VR intervals (exact maximum
     // independent set of an interval graph); ties: later start, then lower index.
@@ -536,6 +754,8 @@ kz_status kz_plan_update(kz_plan* P, const kz_cf32* H_packed, void* stream) {
                                  P->total2, P->d_Hc, P->d_Hb, st);
     if (e == cudaSuccess) e = kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, P->K, P->d_nrmd, P->d_nrm, st);
     if (e == cudaSuccess) e = kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, P->K, P->d_G, st);
+    if (e == cudaSuccess && P->grp.built)
+        e = kz_grp_prepare(grp_chan(P), P->d_Hc, P->total2, P->d_rows, P->d_rptr, P->d_nrm, P->grp.d_stat, P->grp.fmt, st);
     return check_launch(e, "kz_plan_update");
 }
 
@@ -612,12 +832,17 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
             kz_set_error("kz_precode_ex: the tensor-core kernel takes 0, 4 or 8 columns per CTA");
             return KZ_ERR_INVALID_ARG;
         }
+    } else if (kernel == KZ_KERNEL_GROUP) {
+        if (rhs_per_cta != 0 && rhs_per_cta != 16 && rhs_per_cta != 32 && rhs_per_cta != 64) {
+            kz_set_error("kz_precode_ex: the group kernel takes 0, 16, 32 or 64 columns per group");
+            return KZ_ERR_INVALID_ARG;
+        }
     } else if (kernel != KZ_KERNEL_AUTO && kernel != KZ_KERNEL_RESIDENT) {
         kz_set_error("kz_precode_ex: unknown kernel %d", (int)kernel);
         return KZ_ERR_INVALID_ARG;
     }
     kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
-                                    kernel == KZ_KERNEL_TC ? 0 : rhs_per_cta, refresh);
+                                    (kernel == KZ_KERNEL_TC || kernel == KZ_KERNEL_GROUP) ? 0 : rhs_per_cta, refresh);
     if (rc != KZ_OK) return rc;
     if (!s || !x || !iters || !resid) {
         kz_set_error("kz_precode: s, x, iters and resid are required");
@@ -636,6 +861,14 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
     if (kernel == KZ_KERNEL_TC && !tc_ok(algo, prec)) {
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
+    }
+    if (kernel == KZ_KERNEL_GROUP) {
+        if (!is_ahk_family(algo)) {
+            kz_set_error("kz_precode_ex: the group kernel runs AHK / VR_OAHK");
+            return KZ_ERR_UNSUPPORTED;
+        }
+        return run_grp(plan, s, nrhs, xi, algo, tol, max_iter, x, v, iters, resid, status, rhs_per_cta, refresh,
+                       static_cast<cudaStream_t>(stream));
     }
     int J, nw, trow_single = 0;
     size_t smem;

@@ -135,5 +135,57 @@ cudaError_t kz_sum_rate(const KzInst& I, const float2* X, double snr_lin, double
 cudaError_t kz_sum_rate_batched(const KzInst* insts, int n, int K_max, double snr_lin, double* sinr, double* rate,
                                 cudaStream_t st);
 
+// Group kernel (kz_grp.cu): one channel, the CTAs of a column group share it
+// by antenna blocks of 128; contractions on tcgen05 tensor cores.
+struct KzGrpChan {
+    int K, Nt, AB, n_slots;
+    const int* slot_row;        // [AB][256] row of slot r of block b (-1: padding), rows ascending
+    const int* blk_nrt;         // [AB] row tiles of 128 slots (1 or 2)
+    const int* blk_nb;          // [AB] rows meeting the block
+    const int* blk_coff;        // [AB] first compact partial slot of the block
+    const long long* blk_toff;  // [AB] byte offset of the block's tile image
+    const uint8_t* tiles;       // 16-bit tile images
+    const int* cptr;            // [K + 1] CSR over rows: compact partial slots of the blocks row k meets
+    const int* cidx;
+    const float* nrm;           // ||h_k||^2
+    const unsigned char* inF;   // [K] 1: row k is in the orthogonal set F
+    const int* xptr;            // X_k pattern and H H^H on it (refresh)
+    const int* xidx;
+    const float2* G;
+    const float2* Hc;           // aligned complex64 rows (x = H^H q at the end)
+    const int4* rows;
+    const int* rptr;
+    const float* stat;          // [2] sigma_H (power of two, tiles hold H / sigma_H), mean ||h_k||^2
+};
+
+struct KzGrpLaunch {
+    KzGrpChan C;
+    float xi;
+    int nrhs;               // columns of s / x / v handled by this launch
+    int NC, CG;             // columns per group, groups (gridDim.y)
+    int algo, fmt;          // KZ_AHK / KZ_VR_OAHK; 0 FP16, 1 BF16 operands
+    double tol;
+    int max_iter, refresh;
+    const float2* s;        // K x nrhs (column-major), x Nt x nrhs, v K x nrhs (may be NULL)
+    float2* x;
+    float2* v;
+    int* iters;
+    double* resid;
+    int* status;            // may be NULL
+    // scratch (device)
+    float2* Ppart;          // [CG][n_slots][NC] residual partial sums
+    uint16_t* Phi;          // [CG][K][2][NC] 16-bit phi / tau
+    float2* Qg;             // [CG][K][NC] q at the last refresh
+    float* colpart;         // [CG][7][AB][NC] per-CTA column partials
+    unsigned* gbar;         // [0] grid barrier counter (0), [1 + g] abort epochs (0xffffffff)
+    int rpc, rtmax, tmem_cols;
+};
+
+cudaError_t kz_grp_prepare(const KzGrpChan& C, const float2* Hc, long long total2, const int4* rows, const int* rptr,
+                           const float* nrm, float* stat, int fmt, cudaStream_t st);
+size_t kz_grp_smem(int NC, int rtmax, int rpc);
+bool kz_grp_fits(int AB, int CG, bool cluster, size_t smem);
+cudaError_t kz_launch_grp(const KzGrpLaunch& L, bool cluster, size_t smem, cudaStream_t st);
+
 // Thread-local last-error text (kz_api.cu).
 void kz_set_error(const char* fmt, ...);

@@ -21,7 +21,7 @@ from . import _build
 
 # enums of include/kzprecode.h
 KZ_OK, KZ_NOT_CONVERGED, KZ_ERR_INVALID_ARG, KZ_ERR_NUMERIC, KZ_ERR_CUDA, KZ_ERR_NOMEM, KZ_ERR_UNSUPPORTED = range(7)
-KZ_STATUS_BIT_NOT_CONVERGED, KZ_STATUS_BIT_NUMERIC = 1, 2
+KZ_STATUS_BIT_NOT_CONVERGED, KZ_STATUS_BIT_NUMERIC, KZ_STATUS_BIT_TIMEOUT = 1, 2, 4
 ALGOS = {"rk_energy": 0, "rk_uniform": 1, "grk": 2, "ahk": 3, "vr_ogrk": 4, "vr_oahk": 5}
 SELECT = {"paper": 0, "baiwu": 1, "argmax": 2}
 PREC = {"c64": 0, "bf16": 1}
@@ -51,7 +51,7 @@ EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy
            "kz_batch_query",
            "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
-KERNELS = {"auto": 0, "resident": 1, "tc": 3}
+KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4}
 
 
 def library_path() -> str:
@@ -395,6 +395,8 @@ def precode(plan: Plan, S, xi, algo="vr_oahk", sel="paper", tol=1e-6, max_iter=1
     if sync:
         torch.cuda.synchronize(dev)
         st = int(status.item())
+        if st & KZ_STATUS_BIT_TIMEOUT:
+            raise KzError(KZ_ERR_CUDA, "a bounded device wait expired")
         if st & KZ_STATUS_BIT_NUMERIC:
             raise KzError(KZ_ERR_NUMERIC, "NaN or Inf in a residual")
         out["converged"] = not (st & KZ_STATUS_BIT_NOT_CONVERGED)
