@@ -224,6 +224,17 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
  * batch->n entries, free to reuse on return. */
 kz_status kz_batch_rebind(kz_batch* batch, const kz_batch_item* items, void* stream);
 
+/* A new channel for every item of a prepared batch at once (step A0 over
+ * step A8): H_cat (device, 8-byte aligned) holds the items' packed channels
+ * (layout of kz_plan_create) concatenated in item order, item b's at
+ * sum_{c<b} sum(vr_len of item c).  Every item's plan is updated as
+ * kz_plan_update would (packing, row norms, inner products of overlapping
+ * rows), in three kernel launches for the whole batch, asynchronously on
+ * `stream` (the first call also uploads a small row table owned by the
+ * batch, synchronously).  The items must name distinct plans
+ * (KZ_ERR_INVALID_ARG otherwise).  The batch's queue order is kept. */
+kz_status kz_batch_update(kz_batch* batch, const kz_cf32* H_cat, void* stream);
+
 /* Run a prepared batch: one kernel launch after an 8-byte memset of the
  * queue counters (two launches, the second on a stream forked from `stream`
  * and joined back, when a tensor-core batch holds channels whose columns per
@@ -327,6 +338,22 @@ typedef struct {
  * owned by the batch. */
 kz_status kz_precode_adjoint_batched(kz_batch* batch, const kz_adjoint_item* items, double tol,
                                      int32_t max_iter, int32_t* status, void* stream);
+
+/* Precoder matrix from the auxiliary matrix V by the subarray-wise form
+ * (Sec. IV-B, eq. (precoding2)): the array is cut into S subarrays of
+ * consecutive antennas (subarray s = antennas [s Nt / S, (s + 1) Nt / S)),
+ * Q_s is the set of users whose VR meets subarray s, and the rows of F on
+ * subarray s are [H_s]_{Q_s} [V]_{Q_s}, i.e. F[n, :] = sum_{k in Q_s}
+ * conj(H[k, n]) V[k, :] -- the product H^H V at O(Nt |Q| ncols) instead of
+ * O(Nt K ncols).  V: device K x ncols column-major (the v of a solve with
+ * identity right-hand sides gives the RZF precoder); F: device Nt x ncols
+ * column-major (output).  normalise != 0: F is scaled by beta = 1 / ||F||_F
+ * (eq. (power) with equality) and beta (device float) receives it; else F =
+ * H^H V and beta may be NULL.  FP32 products and sums; the norm in FP64, in
+ * a fixed order.  The plan caches Q_s for the last S used and a small partial
+ * buffer (allocated on first use).  Asynchronous on `stream`. */
+kz_status kz_precoder_matrix(kz_plan* plan, const kz_cf32* V, int32_t ncols, int32_t S, int32_t normalise,
+                             kz_cf32* F, float* beta, void* stream);
 
 /* Per-user SINR and spectral efficiency of the precoder (eq. (rate)):
  * F = beta X with beta = 1 / ||X||_F (the power budget ||F||_F^2 <= 1 of

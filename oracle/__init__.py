@@ -18,9 +18,10 @@ cites the part of the paper it follows:
 * ``rng``        the SplitMix64 counter-based generator used for random row
                  selection (the paper does not name one).
 * ``sinr``       per-user SINR and spectral efficiency (eq. (rate)).
+* ``precoder``   subarray-wise precoder assembly (eq. (precoding2)) and beta.
 
 Parity unpinned: ``kaczmarz.vr_oahk``'s a-priori rate of Theorem 5 (the
 statement is iterate-dependent and garbled); only the Lemma 3 identities,
 monotone error decrease and convergence to RZF are pinned.
 """
-from . import rng, sets, rzf, kaczmarz, sinr  # noqa: F401
+from . import rng, sets, rzf, kaczmarz, sinr, precoder  # noqa: F401

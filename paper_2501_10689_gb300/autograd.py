@@ -68,7 +68,7 @@ class BatchedPrecoder:
     The VR layout of every channel (vr_offset, vr_len, Nt) and the number of
     columns are fixed at construction; the plans (packed-row layout, X sets,
     tile covering lists) are built once and each call only re-packs the new
-    channel into them (kz_plan_update).  Forward: one kz_precode_batched over
+    channel into them (kz_batch_update).  Forward: one kz_precode_batched over
     all channels (VR-OAHK, step A8).  Backward: one kz_precode_adjoint_batched
     (step A10 over A8): right-hand sides, adjoint solves and gradient
     contractions for all channels in four launches.
@@ -131,10 +131,10 @@ class BatchedPrecoder:
         return kp.kz_batch_prepare(items, self.nrhs, "vr_oahk")
 
     def load(self, H_cat):
-        """Re-pack H_cat into the plans (asynchronous, on the current stream)."""
+        """Re-pack H_cat into the plans (asynchronous, on the current stream;
+        one kz_batch_update for all channels)."""
         H_cat = H_cat.detach().reshape(-1).contiguous()
-        for c in range(self.n):
-            kp.kz_plan_update(self.plans[c], H_cat[int(self.h_off[c]):int(self.h_off[c + 1])])
+        kp.kz_batch_update(self._fwd, H_cat)
         self.version += 1
         return self.version
 

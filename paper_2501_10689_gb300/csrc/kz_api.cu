@@ -100,6 +100,11 @@ struct kz_plan {
     int sms = 1;
     std::vector<int> vr_off, vr_len;  // the caller's VRs
     GrpPlan grp;
+    // kz_precoder_matrix: Q_s of the last subarray count used, and partial sums
+    int q_S = 0;
+    int *d_qptr = nullptr, *d_qidx = nullptr;
+    double* d_qpart = nullptr;
+    size_t qpart_n = 0;
 
     ~kz_plan() {
         void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
@@ -107,6 +112,9 @@ struct kz_plan {
         for (void* p : ps)
             if (p) cudaFree(p);
         grp.release();
+        void* qs[] = {d_qptr, d_qidx, d_qpart};
+        for (void* p : qs)
+            if (p) cudaFree(p);
     }
 
     KzInst inst() const {
@@ -151,6 +159,9 @@ struct kz_batch {
     int2* d_items = nullptr;
     int* d_queue = nullptr;
     KzAdjItem* d_adj = nullptr;  // adjoint item table (allocated on first use)
+    int2* d_rowmap = nullptr;    // kz_batch_update: {item, row} of every row of every item
+    long long* d_hoff = nullptr; // kz_batch_update: item b's offset in the concatenated channels
+    int n_rows = 0;
     bool all_v = true;           // every item has a v buffer
     std::vector<const kz_plan*> plans;  // the items' plans, fixed at preparation
     std::vector<KzInst> h_insts;        // host copy of the instance table
@@ -168,6 +179,8 @@ struct kz_batch {
         if (aux) cudaStreamDestroy(aux);
         if (d_items2) cudaFree(d_items2);
         if (d_adj) cudaFree(d_adj);
+        if (d_rowmap) cudaFree(d_rowmap);
+        if (d_hoff) cudaFree(d_hoff);
         if (d_insts) cudaFree(d_insts);
         if (d_items) cudaFree(d_items);
         if (d_queue) cudaFree(d_queue);
@@ -432,11 +445,11 @@ kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo
     const int AB = G.AB, sms = P->sms;
     const bool cluster = AB <= 16;
     const int rpc = (P->K + AB - 1) / AB;
-    const size_t smem_limit = 227 * 1024 - 12 * 1024;  // the kernel's static shared memory is below 12 KiB
+    const size_t smem_limit = 227 * 1024 - 16 * 1024;  // the kernel's static shared memory is below 16 KiB
     int NC = 0;
     for (int nc : {16, 32, 64}) {
         if (rhs_per_cta && nc != rhs_per_cta) continue;
-        if ((G.rtmax + 2) * 2 * nc > 512 || kz_grp_smem(nc, G.rtmax, rpc) > smem_limit) continue;
+        if ((G.rtmax + 2) * 2 * nc > 512 || kz_grp_smem(nc, G.rtmax, rpc, AB) > smem_limit) continue;
         NC = nc;
         if (rhs_per_cta || (long)AB * ((nrhs + nc - 1) / nc) <= sms) break;  // smallest width that fills the GPU once
     }
@@ -451,7 +464,7 @@ kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo
     // must never share its SM (a second CTA's allocation would wait for the
     // first, which may wait for it at a group barrier): its shared memory is
     // padded past half of the SM's 228 KiB.
-    const size_t smem = std::max(kz_grp_smem(NC, G.rtmax, rpc), tcols > 256 ? (size_t)120 * 1024 : (size_t)0);
+    const size_t smem = std::max(kz_grp_smem(NC, G.rtmax, rpc, AB), tcols > 256 ? (size_t)120 * 1024 : (size_t)0);
     const int CG_all = (nrhs + NC - 1) / NC;
     const int CG = cluster ? CG_all : std::min(CG_all, sms / AB);
     if (CG < 1 || !kz_grp_fits(AB, cluster ? 1 : CG, cluster, smem)) {
@@ -1270,6 +1283,57 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
     return check_launch(e, "kz_batch_set_launch");
 }
 
+kz_status kz_batch_update(kz_batch* B, const kz_cf32* H_cat, void* stream) {
+    g_err.clear();
+    if (!B || !H_cat || !aligned(H_cat, 8)) {
+        kz_set_error("kz_batch_update: need a batch and an 8-byte aligned H_cat");
+        return KZ_ERR_INVALID_ARG;
+    }
+    for (int b = 0; b < B->n; ++b)
+        for (int c = 0; c < b; ++c)
+            if (B->plans[b] == B->plans[c]) {
+                kz_set_error("kz_batch_update: items %d and %d name the same plan", c, b);
+                return KZ_ERR_INVALID_ARG;
+            }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (!B->d_rowmap) {
+        std::vector<int2> rm;
+        std::vector<long long> hoff(B->n);
+        long long acc = 0;
+        for (int b = 0; b < B->n; ++b) {
+            hoff[b] = acc;
+            acc += B->plans[b]->sumL;
+            for (int k = 0; k < B->plans[b]->K; ++k) rm.push_back(make_int2(b, k));
+        }
+        e = upload(&B->d_rowmap, rm, st);
+        if (e == cudaSuccess) e = upload(&B->d_hoff, hoff, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+        if (e != cudaSuccess) {
+            if (B->d_rowmap) cudaFree(B->d_rowmap);
+            if (B->d_hoff) cudaFree(B->d_hoff);
+            B->d_rowmap = nullptr;
+            B->d_hoff = nullptr;
+            return check_launch(e, "kz_batch_update set-up");
+        }
+        B->n_rows = (int)rm.size();
+    }
+    e = kz_batch_update_rows(B->d_insts, B->d_rowmap, B->n_rows, B->d_hoff, reinterpret_cast<const float2*>(H_cat), st);
+    if (e != cudaSuccess) return check_launch(e, "kz_batch_update");
+    long long off = 0;
+    for (int b = 0; b < B->n; ++b) {  // a plan that also serves the group kernel keeps its tiles current
+        kz_plan* P = const_cast<kz_plan*>(B->plans[b]);
+        if (P->grp.built) {
+            e = kz_grp_prepare(grp_chan(P), P->d_Hc, P->total2, P->d_rows, P->d_rptr, P->d_nrm, P->grp.d_stat,
+                               P->grp.fmt, st);
+            if (e != cudaSuccess) return check_launch(e, "kz_batch_update");
+        }
+        off += P->sumL;
+    }
+    (void)off;
+    return KZ_OK;
+}
+
 kz_status kz_precode_adjoint_batched(kz_batch* B, const kz_adjoint_item* items, double tol, int32_t max_iter,
                                      int32_t* status, void* stream) {
     g_err.clear();
@@ -1311,6 +1375,52 @@ kz_status kz_precode_adjoint_batched(kz_batch* B, const kz_adjoint_item* items, 
     if (rc != KZ_OK) return rc;
     e = kz_adjoint_contract_batched(B->d_insts, B->d_adj, B->n, B->K_max, B->nrhs, st);
     return check_launch(e, "kz_precode_adjoint_batched contraction");
+}
+
+kz_status kz_precoder_matrix(kz_plan* P, const kz_cf32* V, int32_t ncols, int32_t S, int32_t normalise, kz_cf32* F,
+                             float* beta, void* stream) {
+    g_err.clear();
+    if (!P || !V || !F || ncols < 1 || S < 1 || S > P->Nt || (normalise && !beta) || !aligned(V, 8) ||
+        !aligned(F, 8) || (beta && !aligned(beta, 4))) {
+        kz_set_error("kz_precoder_matrix: need a plan, V and F (8-byte aligned), ncols >= 1, 1 <= S <= Nt, and beta "
+                     "when normalising");
+        return KZ_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaError_t e = cudaSuccess;
+    if (P->q_S != S) {  // Q_s: users whose VR meets subarray s
+        std::vector<int> qptr(S + 1, 0), qidx;
+        for (int s = 0; s < S; ++s) {
+            const long n0 = (long)s * P->Nt / S, n1 = (long)(s + 1) * P->Nt / S;
+            for (int k = 0; k < P->K; ++k)
+                if (P->vr_off[k] < n1 && P->vr_off[k] + P->vr_len[k] > n0) qidx.push_back(k);
+            qptr[s + 1] = (int)qidx.size();
+        }
+        if (P->d_qptr) cudaFree(P->d_qptr);
+        if (P->d_qidx) cudaFree(P->d_qidx);
+        P->d_qptr = P->d_qidx = nullptr;
+        P->q_S = 0;
+        e = upload(&P->d_qptr, qptr, st);
+        if (e == cudaSuccess) e = upload(&P->d_qidx, qidx, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
+        if (e != cudaSuccess) return check_launch(e, "kz_precoder_matrix set-up");
+        P->q_S = S;
+    }
+    const size_t need = (size_t)S * ((ncols + 31) / 32);
+    if (P->qpart_n < need) {
+        if (P->d_qpart) cudaFree(P->d_qpart);
+        P->d_qpart = nullptr;
+        P->qpart_n = 0;
+        e = cudaMalloc((void**)&P->d_qpart, need * sizeof(double));
+        if (e != cudaSuccess) {
+            kz_set_error("kz_precoder_matrix: %s", cudaGetErrorString(e));
+            return KZ_ERR_NOMEM;
+        }
+        P->qpart_n = need;
+    }
+    e = kz_subarray_precoder(P->inst(), P->d_qptr, P->d_qidx, S, reinterpret_cast<const float2*>(V), ncols,
+                             reinterpret_cast<float2*>(F), P->d_qpart, normalise ? beta : nullptr, st);
+    return check_launch(e, "kz_precoder_matrix");
 }
 
 kz_status kz_sum_rate(const kz_plan* plan, const kz_cf32* X, double snr_lin, double* sinr, double* rate,

@@ -1,3 +1,4 @@
+#include <algorithm>
 // Set-up kernels (step A0), the adjoint contractions (step A10) and the
 // per-user SINR / sum rate of the precoder (eq. (rate)).
 #include "kz_device.cuh"
@@ -107,6 +108,153 @@ __global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restric
             cy = (cy + rcy) + t;
         }
         if (lane == 0) G[e] = make_float2(sx + cx, sy + cy);
+    }
+}
+
+// Batched set-up (kz_batch_update): block i handles row rowmap[i].y of item
+// rowmap[i].x of the instance table, whose packed channel starts at
+// H_cat + hoff[item].  phase 0 packs the row (as pack_rows_kernel), phase 1
+// forms its norm (as row_norms_kernel), phase 2 its inner products with the
+// overlapping rows (as gram_kernel); the phases are separate launches.
+__global__ void batch_update_kernel(const KzInst* __restrict__ insts, const int2* __restrict__ rowmap,
+                                    const long long* __restrict__ hoff, const float2* __restrict__ H_cat, int phase) {
+    const int2 ir = rowmap[blockIdx.x];
+    const KzInst& I = insts[ir.x];
+    const int k = ir.y;
+    const int4 rd = I.rows[k];  // {a, len2, o, e}
+    if (phase == 0) {
+        const float2* src = H_cat + hoff[ir.x] + I.in_off[k];
+        float2* Hc = const_cast<float2*>(I.Hc) + I.rptr[k];
+        __nv_bfloat162* Hb = I.Hb ? const_cast<__nv_bfloat162*>(I.Hb) + I.rptr[k] : nullptr;
+        for (int p = threadIdx.x; p < rd.y; p += blockDim.x) {
+            const int n = rd.x + p;
+            const float2 h = (n >= rd.z && n < rd.w) ? src[n - rd.z] : make_float2(0.f, 0.f);
+            Hc[p] = h;
+            if (Hb) Hb[p] = __float22bfloat162_rn(h);
+        }
+    } else if (phase == 1) {
+        __shared__ double part[32];
+        const float2* hk = I.Hc + I.rptr[k];
+        double a = 0.0;
+        for (int p = threadIdx.x; p < rd.y; p += blockDim.x) {
+            const float2 h = hk[p];
+            a += (double)h.x * h.x + (double)h.y * h.y;
+        }
+        a = warp_sum_d(a);
+        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+            const_cast<double*>(I.nrmd)[k] = t;
+            const_cast<float*>(I.nrm)[k] = (float)t;
+        }
+    } else {
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+        const float2* hk = I.Hc + I.rptr[k] - rd.x;
+        for (int e = I.xptr[k] + warp; e < I.xptr[k + 1]; e += nw) {
+            const int l = I.xidx[e];
+            const int4 rl = I.rows[l];
+            const float2* hl = I.Hc + I.rptr[l] - rl.x;
+            const int lo = max(rd.z, rl.z), hi = min(rd.w, rl.w);
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int n = lo + lane; n < hi; n += 32) {
+                const float2 a = hk[n], b = hl[n];
+                dot2_add(a.x, b.x, sx, cx);
+                dot2_add(a.y, b.y, sx, cx);
+                dot2_add(a.y, b.x, sy, cy);
+                dot2_add(-a.x, b.y, sy, cy);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                const float rsx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
+                const float rsy = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
+                float t;
+                two_sum(sx, rsx, sx, t);
+                cx = (cx + rcx) + t;
+                two_sum(sy, rsy, sy, t);
+                cy = (cy + rcy) + t;
+            }
+            if (lane == 0) const_cast<float2*>(I.G)[e] = make_float2(sx + cx, sy + cy);
+        }
+    }
+}
+
+// Subarray-wise precoder (eq. (precoding2)): for the antennas n of subarray s
+// (n in [s Nt / S, (s + 1) Nt / S)), F[n, j] = sum_{k in Q_s} conj(H[k, n]) V[k, j],
+// Q_s the users whose VR meets the subarray.  Block (s, column chunk of 32):
+// V's rows of Q_s staged in shared memory 64 at a time, one thread per
+// antenna; the block's sum of |F|^2 goes to part[] for the normalisation.
+__global__ void subarray_precoder_kernel(const __grid_constant__ KzInst I, const int* __restrict__ qptr,
+                                         const int* __restrict__ qidx, int S, const float2* __restrict__ V, int ncols,
+                                         float2* __restrict__ F, double* __restrict__ part) {
+    __shared__ float2 sv[64 * 32];
+    __shared__ int sk[64];
+    __shared__ double red[32];
+    const int s = blockIdx.x, c0 = blockIdx.y * 32, nc = min(32, ncols - c0);
+    const int K = I.K, Nt = I.Nt;
+    const int n0 = (int)((long long)s * Nt / S), n1 = (int)((long long)(s + 1) * Nt / S);
+    const int q0 = qptr[s], q1 = qptr[s + 1];
+    double ss = 0.0;
+    for (int nb = n0; nb < n1; nb += blockDim.x) {
+        const int n = nb + threadIdx.x;
+        float2 acc[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) acc[j] = make_float2(0.f, 0.f);
+        for (int qb = q0; qb < q1; qb += 64) {
+            const int nq = min(64, q1 - qb);
+            __syncthreads();
+            for (int e = threadIdx.x; e < nq * 32; e += blockDim.x) {
+                const int r = e % nq, j = e / nq;
+                sv[r * 32 + j] = j < nc ? V[(size_t)(c0 + j) * K + qidx[qb + r]] : make_float2(0.f, 0.f);
+            }
+            for (int r = threadIdx.x; r < nq; r += blockDim.x) sk[r] = qidx[qb + r];
+            __syncthreads();
+            if (n < n1) {
+                for (int r = 0; r < nq; ++r) {
+                    const int k = sk[r];
+                    const int4 rd = I.rows[k];  // {a, len2, o, e}
+                    if (n < rd.z || n >= rd.w) continue;
+                    const float2 h = I.Hc[I.rptr[k] + (n - rd.x)];
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float2 v = sv[r * 32 + j];
+                        acc[j].x = fmaf(h.x, v.x, fmaf(h.y, v.y, acc[j].x));
+                        acc[j].y = fmaf(h.x, v.y, fmaf(-h.y, v.x, acc[j].y));
+                    }
+                }
+            }
+        }
+        if (n < n1) {
+            for (int j = 0; j < nc; ++j) {
+                F[(size_t)(c0 + j) * Nt + n] = acc[j];
+                ss += (double)acc[j].x * acc[j].x + (double)acc[j].y * acc[j].y;
+            }
+        }
+    }
+    ss = warp_sum_d(ss);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = ss;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+        part[blockIdx.x * gridDim.y + blockIdx.y] = t;
+    }
+}
+
+// beta = 1 / sqrt(sum of the blocks' partial sums, in block order).
+__global__ void precoder_beta_kernel(const double* __restrict__ part, int n, float* __restrict__ beta) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < n; ++i) t += part[i];
+        *beta = t > 0.0 ? (float)(1.0 / sqrt(t)) : 0.f;
+    }
+}
+
+__global__ void scale_kernel(float2* __restrict__ F, long long n, const float* __restrict__ beta) {
+    const float b = *beta;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float2 f = F[i];
+        F[i] = make_float2(f.x * b, f.y * b);
     }
 }
 
@@ -425,6 +573,30 @@ cudaError_t kz_coupling(const KzInst* insts, int n, float* mu, cudaStream_t st) 
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st) {
     gram_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, xptr, xidx, G);
+    return cudaGetLastError();
+}
+
+cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nrows, const long long* hoff,
+                                 const float2* H_cat, cudaStream_t st) {
+    for (int phase = 0; phase < 3; ++phase) {
+        batch_update_kernel<<<nrows, 256, 0, st>>>(insts, rowmap, hoff, H_cat, phase);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t kz_subarray_precoder(const KzInst& I, const int* qptr, const int* qidx, int S, const float2* V, int ncols,
+                                 float2* F, double* part, float* beta, cudaStream_t st) {
+    const dim3 grid(S, (ncols + 31) / 32);
+    subarray_precoder_kernel<<<grid, 128, 0, st>>>(I, qptr, qidx, S, V, ncols, F, part);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !beta) return e;
+    precoder_beta_kernel<<<1, 32, 0, st>>>(part, (int)(grid.x * grid.y), beta);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const long long n = (long long)I.Nt * ncols;
+    scale_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(F, n, beta);
     return cudaGetLastError();
 }
 

@@ -205,7 +205,8 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     __shared__ uint64_t bar_ld, bar_mma;
     __shared__ uint32_t s_tmem;
     __shared__ int s_abort, s_refresh;
-    __shared__ double c_sn2[GNCMAX], c_rt2[GNCMAX], c_sum[NQ * GNCMAX], c_tmp[GT];
+    __shared__ double c_sn2[GNCMAX], c_rt2[GNCMAX], c_sum[3 * GNCMAX];
+    __shared__ float c_tmp[3 * GNCMAX * 8];  // chunk sums of sum_partials (AB <= 128)
     __shared__ float c_kap[GNCMAX], c_sig[GNCMAX], c_isig[GNCMAX], c_tau[GNCMAX], c_gam[GNCMAX], c_coef[GNCMAX];
     __shared__ int c_act[GNCMAX], c_wait[GNCMAX], c_iters[GNCMAX];
     __shared__ float c_numv[GNCMAX], c_phinv[GNCMAX];
@@ -237,6 +238,8 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     float2* o_phi = o_q + rpc * NC;
     float* ubuf = reinterpret_cast<float*>(o_phi + rpc * NC);   // [3][rpc][NC] per-unit values
     int* s_slot = reinterpret_cast<int*>(ubuf + 3 * rpc * NC);   // [rtrows]
+    int* s_cidx = s_slot + rtrows;                               // [rpc * AB] partial slots of the owned rows
+    int* s_cptr = s_cidx + rpc * AB;                             // [rpc + 1], relative to the owned rows' first
 
     const int PSH = RT * 256;           // tile plane bytes
     const int Tn = NC * 16;             // operand stride between 8-row groups along K
@@ -259,6 +262,12 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     }
     if (warp == 0) kz5::tmem_alloc(&s_tmem, (uint32_t)L.tmem_cols);
     for (int r = tid; r < rtrows; r += GT) s_slot[r] = (r < RT) ? C.slot_row[b * 256 + r] : -1;
+    {
+        const int c0 = nown ? C.cptr[k0] : 0;
+        for (int i = tid; i <= nown; i += GT) s_cptr[i] = C.cptr[k0 + i] - c0;
+        const int nc = nown ? C.cptr[k0 + nown] - c0 : 0;
+        for (int i = tid; i < nc; i += GT) s_cidx[i] = C.cidx[c0 + i];
+    }
     kz5::fence_async_smem();
     kz5::fence_before();
     __syncthreads();
@@ -288,43 +297,52 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
         ubuf[rpc * NC + u] = a2 * C.nrm[k] / (d * d);
     }
     __syncthreads();
-    float* cp = L.colpart + (size_t)g * NQ * AB * NC;  // this group's partials [NQ][AB][NC]
+    float* cp = L.colpart + (size_t)g * NQ * AB * NC;  // this group's partials [NQ][NC][AB]
     auto put_partial = [&](int q, int which) {         // column sums over the owned rows, in row order
         if (tid < NC) {
             float a = 0.f;
             for (int kk = 0; kk < nown; ++kk) a += ubuf[which * rpc * NC + kk * NC + tid];
-            cp[((size_t)q * AB + b) * NC + tid] = a;
+            cp[((size_t)q * NC + tid) * AB + b] = a;
         }
     };
     put_partial(Q_SN2, 0);
     put_partial(Q_KAP, 1);
 
     // fixed-order sums of partials over the group's AB CTAs into c_sum[qi * NC + j]
-    // (nq * NC <= GT); each (quantity, column) pair is split over `per` threads
-    // that add contiguous ranges of CTAs, and the ranges are added in order
+    // (nq <= 3): every (quantity, column) pair's AB partials (contiguous) are
+    // cut into chunks of 16 added by one thread each (four 16-byte loads), then
+    // the chunk sums are added in chunk order.  With the abort word read here
+    // too, this is where every CTA learns of a failure (at the same barrier).
     auto sum_partials = [&](const int* qs, int nq) {
-        const int pairs = nq * NC;
-        const int per = (GT / pairs) >= 4 ? 4 : ((GT / pairs) >= 2 ? 2 : 1);
-        if (tid < pairs * per) {
-            const int pr = tid / per, sub = tid % per, q = qs[pr / NC], j = pr % NC;
-            const int b0 = sub * AB / per, b1 = (sub + 1) * AB / per;
-            double a = 0.0;
-            for (int bb = b0; bb < b1; ++bb) a += (double)__ldcg(cp + ((size_t)q * AB + bb) * NC + j);
-            c_tmp[tid] = a;
-        }
-        __syncthreads();
-        if (tid < pairs) {
-            double a = 0.0;
-            for (int sub = 0; sub < per; ++sub) a += c_tmp[tid * per + sub];
-            c_sum[tid] = a;
-        }
-        __syncthreads();
-    };
-    auto sync = [&]() {
-        group_sync<CLUSTER>(L, gen, nctas, abort_word);
+        const int pairs = nq * NC, nch = (AB + 15) / 16, tasks = pairs * nch;
         if (tid == 0) s_abort = (__ldcg(abort_word) <= gen) ? 1 : 0;
+#pragma unroll 2
+        for (int tk = tid; tk < tasks; tk += GT) {
+            const int p = tk / nch, c = tk % nch;
+            const float* src = cp + ((size_t)qs[p / NC] * NC + (p % NC)) * AB + 16 * c;
+            const int n = min(16, AB - 16 * c);
+            double a = 0.0;
+            if (n == 16 && (AB & 3) == 0) {
+                const float4 x0 = __ldcg(reinterpret_cast<const float4*>(src));
+                const float4 x1 = __ldcg(reinterpret_cast<const float4*>(src) + 1);
+                const float4 x2 = __ldcg(reinterpret_cast<const float4*>(src) + 2);
+                const float4 x3 = __ldcg(reinterpret_cast<const float4*>(src) + 3);
+                a = (((double)x0.x + x0.y) + ((double)x0.z + x0.w)) + (((double)x1.x + x1.y) + ((double)x1.z + x1.w)) +
+                    (((double)x2.x + x2.y) + ((double)x2.z + x2.w)) + (((double)x3.x + x3.y) + ((double)x3.z + x3.w));
+            } else {
+                for (int i = 0; i < n; ++i) a += (double)__ldcg(src + i);
+            }
+            c_tmp[tk] = (float)a;
+        }
+        __syncthreads();
+        for (int p = tid; p < pairs; p += GT) {
+            double a = 0.0;
+            for (int c = 0; c < nch; ++c) a += (double)c_tmp[p * nch + c];
+            c_sum[p] = a;
+        }
         __syncthreads();
     };
+    auto sync = [&]() { group_sync<CLUSTER>(L, gen, nctas, abort_word); };
     auto fail_later = [&]() {  // acted on by every CTA after the next barrier
         flag(L.status, KZ_STATUS_BIT_TIMEOUT);
         atomicMin(abort_word, gen + 1);
@@ -460,7 +478,7 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
         if (tid < NC) {
             const float sc = sigH * c_tau[tid];
             const float a = ((red[0][tid] + red[1][tid]) + (red[2][tid] + red[3][tid])) * sc * sc;
-            cp[((size_t)Q_U2 * AB + b) * NC + tid] = a;
+            cp[((size_t)Q_U2 * NC + tid) * AB + b] = a;
         }
     };
     // dM += coef_j U (FP32 master in tensor memory), then the 16-bit operand dM / sigma_j
@@ -518,12 +536,18 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
         float2 r = o_rref[u];
         if (dirty) {
             const float2* pp = L.Ppart + (size_t)g * C.n_slots * NC + j;
-            const int e0 = C.cptr[k], e1 = C.cptr[k + 1];
+            const int e0 = s_cptr[kk], e1 = s_cptr[kk + 1];
             float px = 0.f, py = 0.f;
-            for (int e = e0; e < e1; ++e) {
-                const float2 v = __ldcg(pp + (size_t)C.cidx[e] * NC);
-                px += v.x;
-                py += v.y;
+            for (int e = e0; e < e1; e += 8) {  // eight loads in flight, added in order
+                float2 v[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i)
+                    v[i] = (e + i < e1) ? __ldcg(pp + (size_t)s_cidx[e + i] * NC) : make_float2(0.f, 0.f);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    px += v[i].x;
+                    py += v[i].y;
+                }
             }
             r.x -= px;
             r.y -= py;
@@ -561,17 +585,25 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             qg[(size_t)k * NC + j] = o_q[u];
         }
         sync();
-        if (s_abort) return 2;
         for (int u = tid; u < nown * NC; u += GT) {
             const int kk = u / NC, j = u % NC, k = k0 + kk;
             float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
-            for (int e = C.xptr[k]; e < C.xptr[k + 1]; ++e) {
-                const float2 gk = __ldg(C.G + e);
-                const float2 ql = __ldcg(qg + (size_t)C.xidx[e] * NC + j);
-                two_prod_acc(gk.x, ql.x, hx, lx);
-                two_prod_acc(-gk.y, ql.y, hx, lx);
-                two_prod_acc(gk.x, ql.y, hy, ly);
-                two_prod_acc(gk.y, ql.x, hy, ly);
+            const int e1 = C.xptr[k + 1];
+            for (int e = C.xptr[k]; e < e1; e += 8) {  // eight entries' loads in flight
+                float2 gk[8], ql[8];
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const bool in = e + i < e1;
+                    gk[i] = in ? __ldg(C.G + e + i) : make_float2(0.f, 0.f);
+                    ql[i] = in ? __ldcg(qg + (size_t)__ldg(C.xidx + e + i) * NC + j) : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    two_prod_acc(gk[i].x, ql[i].x, hx, lx);
+                    two_prod_acc(-gk[i].y, ql[i].y, hx, lx);
+                    two_prod_acc(gk[i].x, ql[i].y, hy, ly);
+                    two_prod_acc(gk[i].y, ql[i].x, hy, ly);
+                }
             }
             const float2 sv = o_s[u], qv = o_q[u];
             float2 r;
@@ -583,11 +615,11 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
         __syncthreads();
         put_partial(Q_RT2, 0);
         sync();
-        if (s_abort) return 2;
         {
             const int qs[1] = {Q_RT2};
             sum_partials(qs, 1);
         }
+        if (s_abort) return 2;
         if (tid < NC) {
             const int j = tid;
             if (c_act[j]) {
@@ -640,7 +672,6 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
                     if (dirty) {
                         gemm_p();
                         sync();
-                        if (s_abort) break;
                     }
                     for (int u = tid; u < nown * NC; u += GT) {
                         const int kk = u / NC, j = u % NC, k = k0 + kk;
@@ -655,7 +686,6 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
                         put_phi(kk, j, ph);
                     }
                     sync();
-                    if (s_abort) break;
                     if (tid < NC) c_coef[tid] = (c_act[tid] && !c_wait[tid]) ? sigH * c_tau[tid] : 0.f;
                     gemm_u();
                     dm_update();
@@ -671,7 +701,6 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             if (dirty) {
                 gemm_p();
                 sync();
-                if (s_abort) break;
             }
             for (int u = tid; u < nown * NC; u += GT) {
                 const int kk = u / NC, j = u % NC, k = k0 + kk;
@@ -698,11 +727,11 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             put_partial(Q_NUM, 1);
             put_partial(Q_PHIN, 2);
             sync();
-            if (s_abort) break;
             {
                 const int qs[3] = {Q_RV2, Q_NUM, Q_PHIN};
                 sum_partials(qs, 3);
             }
+            if (s_abort) break;
             // tentative stopping test on the running residual
             if (tid < NC) {
                 const int j = tid;
@@ -739,11 +768,11 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             gemm_u();
             u_norms();
             sync();
-            if (s_abort) break;
             {
                 const int qs[1] = {Q_U2};
                 sum_partials(qs, 1);
             }
+            if (s_abort) break;
             // gamma = Re(phi_V^H r_V) / (||u||^2 + xi ||phi_V||^2) (eq. (coefficient)); 0 skips the step
             if (tid < NC) {
                 const int j = tid;
@@ -834,11 +863,11 @@ cudaError_t kz_grp_prepare(const KzGrpChan& C, const float2* Hc, long long total
     return cudaGetLastError();
 }
 
-size_t kz_grp_smem(int NC, int rtmax, int rpc) {
+size_t kz_grp_smem(int NC, int rtmax, int rpc, int AB) {
     const int rtrows = 128 * rtmax;
     const size_t szop = (size_t)std::max(512 * NC, 4 * NC * rtrows);
     return (size_t)2 * rtrows * 256 + szop + (size_t)5 * rpc * NC * sizeof(float2) + (size_t)3 * rpc * NC * sizeof(float) +
-           (size_t)rtrows * sizeof(int);
+           (size_t)(rtrows + rpc * AB + rpc + 1) * sizeof(int);
 }
 
 // Whether AB x CG CTAs can run: cluster mode needs one resident cluster of AB

@@ -102,6 +102,15 @@ cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, in
                          float* out_f, cudaStream_t st);
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st);
+// Re-pack every item of a batch from H_cat (item b's packed channel at
+// H_cat + hoff[b]): packing, row norms and inner products of overlapping rows,
+// one launch each over all (item, row) pairs of rowmap.
+cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nrows, const long long* hoff,
+                                 const float2* H_cat, cudaStream_t st);
+// Subarray-wise precoder F = H^H V over S subarrays (Q_s in CSR qptr / qidx);
+// with beta non-NULL, F is scaled by beta = 1 / ||F||_F (part: S x ceil(ncols / 32) doubles).
+cudaError_t kz_subarray_precoder(const KzInst& I, const int* qptr, const int* qidx, int S, const float2* V, int ncols,
+                                 float2* F, double* part, float* beta, cudaStream_t st);
 // Coupling of every channel of a batch: mu[b] = max_k sum_{l in X_k, l != k}
 // |G_kl|^2 / (d_k d_l), d = ||h||^2 + xi (the largest squared off-diagonal
 // row mass of the row-normalised system), one block per channel.
@@ -183,7 +192,7 @@ struct KzGrpLaunch {
 
 cudaError_t kz_grp_prepare(const KzGrpChan& C, const float2* Hc, long long total2, const int4* rows, const int* rptr,
                            const float* nrm, float* stat, int fmt, cudaStream_t st);
-size_t kz_grp_smem(int NC, int rtmax, int rpc);
+size_t kz_grp_smem(int NC, int rtmax, int rpc, int AB);
 bool kz_grp_fits(int AB, int CG, bool cluster, size_t smem);
 cudaError_t kz_launch_grp(const KzGrpLaunch& L, bool cluster, size_t smem, cudaStream_t st);
 

@@ -49,8 +49,8 @@ class KzBatchItem(ctypes.Structure):
 EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_query",
-           "kz_batch_rebind", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
-           "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
+           "kz_batch_rebind", "kz_batch_update", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
+           "kz_precoder_matrix", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4}
 
 
@@ -73,12 +73,16 @@ def load():
     lib.kz_plan_create.restype = I32
     lib.kz_plan_dense.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_dense.restype = I32
+    lib.kz_precoder_matrix.argtypes = [P, P, I32, I32, I32, P, P, P]
+    lib.kz_precoder_matrix.restype = I32
     lib.kz_sum_rate.argtypes = [P, P, F64, P, P, P]
     lib.kz_sum_rate.restype = I32
     lib.kz_sum_rate_batched.argtypes = [P, F64, P, P, P]
     lib.kz_sum_rate_batched.restype = I32
     lib.kz_batch_rebind.argtypes = [P, P, P]
     lib.kz_batch_rebind.restype = I32
+    lib.kz_batch_update.argtypes = [P, P, P]
+    lib.kz_batch_update.restype = I32
     lib.kz_plan_update.argtypes = [P, P, P]
     lib.kz_plan_update.restype = I32
     lib.kz_precode_adjoint_batched.argtypes = [P, P, F64, I32, P, P]
@@ -281,6 +285,15 @@ def kz_batch_rebind(batch: Batch, items, stream=None):
     batch.keep = list(items)
 
 
+def kz_batch_update(batch: Batch, H_cat, stream=None):
+    """Re-pack every item's plan from H_cat (complex64 CUDA tensor: the items'
+    packed channels concatenated in item order)."""
+    lib = load()
+    n = sum(it["plan"].sum_len for it in batch.keep)
+    _check_c64(H_cat, (n,), "H_cat")
+    return _check(lib.kz_batch_update(batch.handle, _ptr(H_cat), _stream(stream)))
+
+
 def kz_precode_batched(batch: Batch, sel, tol, max_iter, seed, refresh=0, status=None, stream=None):
     lib = load()
     return _check(lib.kz_precode_batched(batch.handle, SELECT[sel] if isinstance(sel, str) else sel, float(tol),
@@ -346,6 +359,19 @@ def kz_precode_adjoint_batched(batch: Batch, items, tol, max_iter, status=None, 
                                it["grad_H"].data_ptr(), it["grad_xi"].data_ptr())
     return _check(lib.kz_precode_adjoint_batched(batch.handle, ctypes.cast(arr, ctypes.c_void_p), float(tol),
                                                  int(max_iter), _ptr(status), _stream(stream)))
+
+
+def kz_precoder_matrix(plan: Plan, V, S, F, normalise=False, beta=None, stream=None):
+    """F (ncols, Nt) from V (ncols, K) by the subarray form over S subarrays
+    (both complex64 CUDA tensors, one row per column); beta: float32 (1,)."""
+    lib = load()
+    ncols = V.shape[0]
+    _check_c64(V, (ncols, plan.K), "V")
+    _check_c64(F, (ncols, plan.Nt), "F")
+    if beta is not None and (beta.dtype != torch.float32 or tuple(beta.shape) != (1,)):
+        raise ValueError("beta: expected float32 tensor of shape (1,)")
+    return _check(lib.kz_precoder_matrix(plan.handle, _ptr(V), int(ncols), int(S), int(bool(normalise)), _ptr(F),
+                                         _ptr(beta), _stream(stream)))
 
 
 def kz_sum_rate(plan: Plan, X, snr_lin, sinr=None, rate=None, stream=None):

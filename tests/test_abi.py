@@ -116,3 +116,10 @@ def test_plan_dense_rejects_bad_input(lib):
     rc, msg = dense(2, 8, [0, 1], [3, 4], H=None)
     assert rc == KZ_ERR_INVALID_ARG and "H_dense" in msg
     assert dense(2, 8, [0, 1], [3, 4], H=ctypes.c_void_p(0x10004))[0] == KZ_ERR_INVALID_ARG  # misaligned
+
+
+def test_precoder_matrix_rejects_bad_input(lib):
+    from paper_2501_10689_gb300.kzprecode import KZ_ERR_INVALID_ARG
+    P = ctypes.c_void_p
+    assert lib.kz_precoder_matrix(None, FAKE, 4, 2, 0, FAKE, None, None) == KZ_ERR_INVALID_ARG
+    assert "kz_precoder_matrix" in lib.kz_last_error().decode()
