@@ -62,18 +62,24 @@ typedef enum {
 #define KZ_STATUS_BIT_TIMEOUT 4  /* a bounded device wait expired (the call's outputs are not valid) */
 
 /* Methods.  RK_ENERGY / RK_UNIFORM: Alg. 1 with p_i = ||b_i||^2/||B||_F^2 or 1/K
- * (Sec. III-A).  GRK: greedy selection with every residual recomputed
- * (Sec. IV-A).  VR_OGRK: Alg. 2, residuals recomputed only on X_{i(t-1)}.
- * AHK: aggregation-hyperplane step on all rows (eqs. (update4),
- * (coefficient)).  VR_OAHK: Alg. 3, unit step on the orthogonal set F
- * (Prop. 1) followed by an AHK step on the rest V. */
+ * (Sec. III-A; RK_UNIFORM is the URK of Table I).  GRK: greedy selection
+ * with every residual recomputed (Sec. IV-A).  VR_OGRK: Alg. 2, residuals
+ * recomputed only on X_{i(t-1)}.  AHK: aggregation-hyperplane step on all
+ * rows (eqs. (update4), (coefficient)).  VR_OAHK: Alg. 3, unit step on the
+ * orthogonal set F (Prop. 1) followed by an AHK step on the rest V.
+ * RK_SWOR (SWOR-ERK of Table I): energy weights, each sweep of K steps
+ * drawing rows without replacement (p_i proportional to ||b_i||^2 over the
+ * rows not yet drawn in the sweep).  GK (Table I): GRK with the maximal-
+ * residual rule, i.e. KZ_SEL_ARGMAX whatever `sel` says. */
 typedef enum {
     KZ_RK_ENERGY = 0,
     KZ_RK_UNIFORM = 1,
     KZ_GRK = 2,
     KZ_AHK = 3,
     KZ_VR_OGRK = 4,
-    KZ_VR_OAHK = 5
+    KZ_VR_OAHK = 5,
+    KZ_RK_SWOR = 6,
+    KZ_GK = 7
 } kz_algo;
 
 /* Row selection for GRK / VR_OGRK.  PAPER: sample p_i = |r_i|^2/||r||^2
@@ -354,6 +360,18 @@ kz_status kz_precode_adjoint_batched(kz_batch* batch, const kz_adjoint_item* ite
  * buffer (allocated on first use).  Asynchronous on `stream`. */
 kz_status kz_precoder_matrix(kz_plan* plan, const kz_cf32* V, int32_t ncols, int32_t S, int32_t normalise,
                              kz_cf32* F, float* beta, void* stream);
+
+/* The paper's computational complexity in FLOPs (Table I) for this plan:
+ * scheme -1 is RZF; KZ_RK_UNIFORM (URK), KZ_RK_SWOR (SWOR-ERK), KZ_GK,
+ * KZ_VR_OGRK and KZ_VR_OAHK are the table's other rows (the precoder-matrix
+ * setup plus T times the per-iteration cost; T: the iteration count, e.g.
+ * the mean of a solve's iters).  The table's per-user set sizes are means
+ * over the plan's users: |Q| over S subarrays (as in kz_precoder_matrix),
+ * |M| the VR length |Gamma_k| (the table's |M| in the VR rows is read as
+ * |Gamma|), |X| the size of X_k without k, |F| and |V| the orthogonal set
+ * and its complement.  Host only; KZ_ERR_UNSUPPORTED for a method the table
+ * does not list. */
+kz_status kz_plan_flops(const kz_plan* plan, int32_t scheme, int32_t S, double T, double* flops);
 
 /* Per-user SINR and spectral efficiency of the precoder (eq. (rate)):
  * F = beta X with beta = 1 / ||X||_F (the power budget ||F||_F^2 <= 1 of

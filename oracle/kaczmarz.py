@@ -132,23 +132,33 @@ def _trace_state(trace, **kw):
         trace.append({k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in kw.items()})
 
 
-def rk(sys, s, *, energy=True, tol=1e-6, max_iter=10000, seed=0, instance=0, rhs=0, trace=None):
-    """Alg. 1: rows drawn with p_i = d_i / sum(d) (energy) or 1/K (uniform)."""
+def rk(sys, s, *, energy=True, swor=False, tol=1e-6, max_iter=10000, seed=0, instance=0, rhs=0, trace=None):
+    """Alg. 1: rows drawn with p_i = d_i / sum(d) (energy) or 1/K (uniform).
+
+    ``swor=True`` (the SWOR-ERK comparison method of Table I): energy weights,
+    but within each sweep of K consecutive steps (t = cK .. cK + K - 1) a row
+    is drawn at most once -- each draw takes p_i proportional to d_i over the
+    rows not yet drawn in the sweep (sampling without replacement), so every
+    sweep visits every row once."""
     s = np.asarray(s, dtype=np.complex128)
     m = np.zeros(sys.Nt, dtype=np.complex128)
     q = np.zeros(sys.K, dtype=np.complex128)
-    w = sys.d if energy else np.ones(sys.K)
+    w = sys.d if (energy or swor) else np.ones(sys.K)
+    drawn = np.zeros(sys.K, dtype=bool)
     sn = np.linalg.norm(s)
     t = 0
     conv = False
     while True:
         if t % sys.K == 0:
+            drawn[:] = False
             if np.linalg.norm(sys.residual(s, m, q)) <= tol * sn:
                 conv = True
                 break
         if t >= max_iter:
             break
-        i = pick(w, _rng.uniform(seed, instance, rhs, t))
+        weights = np.where(drawn, 0.0, w) if swor else w
+        i = pick(weights, _rng.uniform(seed, instance, rhs, t))
+        drawn[i] = True
         r_i = sys.residual_row(i, s, m, q)
         gamma = r_i / sys.d[i]
         sys.project_row(i, gamma, m, q)
@@ -279,7 +289,7 @@ def vr_oahk(sys, s, *, F=None, V=None, tol=1e-6, max_iter=1000, trace=None, f_un
     return m, q, t, conv
 
 
-ALGOS = ("rk_energy", "rk_uniform", "grk", "ahk", "vr_ogrk", "vr_oahk")
+ALGOS = ("rk_energy", "rk_uniform", "grk", "ahk", "vr_ogrk", "vr_oahk", "rk_swor", "gk")
 
 
 def solve(inst_or_sys, S, algo, *, rule="paper", tol=1e-6, max_iter=10000, seed=0, instance=0,
@@ -299,12 +309,12 @@ def solve(inst_or_sys, S, algo, *, rule="paper", tol=1e-6, max_iter=10000, seed=
     F, V = _sets.split_fv(sys.off, sys.len) if algo == "vr_oahk" else (None, None)
     for j in range(nrhs):
         s = S[:, j]
-        if algo in ("rk_energy", "rk_uniform"):
-            m, q, t, c = rk(sys, s, energy=(algo == "rk_energy"), tol=tol, max_iter=max_iter,
-                            seed=seed, instance=instance, rhs=j)
-        elif algo == "grk":
-            m, q, t, c = grk(sys, s, rule=rule, tol=tol, max_iter=max_iter, seed=seed,
-                             instance=instance, rhs=j)
+        if algo in ("rk_energy", "rk_uniform", "rk_swor"):
+            m, q, t, c = rk(sys, s, energy=(algo != "rk_uniform"), swor=(algo == "rk_swor"), tol=tol,
+                            max_iter=max_iter, seed=seed, instance=instance, rhs=j)
+        elif algo in ("grk", "gk"):  # GK: the greedy (maximal-residual) rule
+            m, q, t, c = grk(sys, s, rule="argmax" if algo == "gk" else rule, tol=tol, max_iter=max_iter,
+                             seed=seed, instance=instance, rhs=j)
         elif algo == "vr_ogrk":
             m, q, t, c = vr_ogrk(sys, s, rule=rule, tol=tol, max_iter=max_iter, seed=seed,
                                  instance=instance, rhs=j, X=xsets)

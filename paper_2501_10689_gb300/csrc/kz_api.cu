@@ -163,6 +163,7 @@ struct kz_batch {
     long long* d_hoff = nullptr; // kz_batch_update: item b's offset in the concatenated channels
     int n_rows = 0;
     bool all_v = true;           // every item has a v buffer
+    bool gk = false;             // prepared as KZ_GK: GRK with the argmax rule
     std::vector<const kz_plan*> plans;  // the items' plans, fixed at preparation
     std::vector<KzInst> h_insts;        // host copy of the instance table
     // Tensor-core kernel at J = 8 over channels of both widths: the 4-column
@@ -191,7 +192,7 @@ namespace {
 
 bool is_ahk_family(kz_algo a) { return a == KZ_AHK || a == KZ_VR_OAHK; }
 
-bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_VR_OAHK; }
+bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_GK; }
 
 // Refresh period: the drift correction of C64, the correction-form refresh
 // of BF16_MIXED and of the tensor-core kernel (whose TF32 inner products
@@ -865,6 +866,10 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         kz_set_error("kz_precode: misaligned output or input pointer");
         return KZ_ERR_INVALID_ARG;
     }
+    if (algo == KZ_GK) {  // GK is GRK with the maximal-residual rule
+        algo = KZ_GRK;
+        sel = KZ_SEL_ARGMAX;
+    }
     const kz_prec prec = plan->prec;
     const bool bf = (prec == KZ_BF16_MIXED);
     if (bf && !is_ahk_family(algo)) {
@@ -987,7 +992,8 @@ kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n
     kz_batch* B = new kz_batch();
     B->n = n;
     B->nrhs = nrhs;
-    B->algo = algo;
+    B->gk = (algo == KZ_GK);
+    B->algo = B->gk ? KZ_GRK : algo;
     B->prec = prec;
     B->Ntp_max = Ntp_max;
     B->K_max = K_max;
@@ -1103,6 +1109,7 @@ kz_status kz_precode_batched(kz_batch* B, kz_select sel, double tol, int32_t max
         kz_set_error("kz_precode_batched: bad selection rule, tol, max_iter or refresh");
         return KZ_ERR_INVALID_ARG;
     }
+    if (B->gk) sel = KZ_SEL_ARGMAX;
     KzLaunch L;
     memset(&L, 0, sizeof(L));
     L.insts = B->d_insts;
@@ -1421,6 +1428,39 @@ kz_status kz_precoder_matrix(kz_plan* P, const kz_cf32* V, int32_t ncols, int32_
     e = kz_subarray_precoder(P->inst(), P->d_qptr, P->d_qidx, S, reinterpret_cast<const float2*>(V), ncols,
                              reinterpret_cast<float2*>(F), P->d_qpart, normalise ? beta : nullptr, st);
     return check_launch(e, "kz_precoder_matrix");
+}
+
+kz_status kz_plan_flops(const kz_plan* P, int32_t scheme, int32_t S, double T, double* flops) {
+    g_err.clear();
+    if (!P || !flops || S < 1 || S > (P ? P->Nt : 1) || !(T >= 0.0)) {
+        kz_set_error("kz_plan_flops: need a plan, flops, 1 <= S <= Nt and T >= 0");
+        return KZ_ERR_INVALID_ARG;
+    }
+    const double K = P->K, Nt = P->Nt;
+    const double M = (double)P->sumL / K;                           // mean |Gamma_k|
+    const double X = (double)P->xidx.size() / K - 1.0;              // mean |X_k| without k itself
+    const double F = P->nF, V = K - P->nF;
+    double Qsum = 0.0;                                              // mean |Q_s| over the S subarrays
+    for (int s = 0; s < S; ++s) {
+        const long n0 = (long)s * P->Nt / S, n1 = (long)(s + 1) * P->Nt / S;
+        for (int k = 0; k < P->K; ++k)
+            if (P->vr_off[k] < n1 && P->vr_off[k] + P->vr_len[k] > n0) Qsum += 1.0;
+    }
+    const double Q = Qsum / S;
+    double f;
+    switch (scheme) {
+        case -1: f = 8 * K * K * K + 9 * K * K + 12 * Nt * K * K - 3 * K; break;
+        case KZ_RK_UNIFORM: f = 8 * Nt * K * K + 4 * Nt * K + T * (16 * Nt - 4); break;
+        case KZ_RK_SWOR: f = 8 * Nt * K * K + 4 * Nt * K + K - 1 + T * (16 * Nt + K + 8); break;
+        case KZ_GK: f = 8 * Nt * K * K + 4 * Nt * K - K + T * (8 * Nt * (K + 1) + K - 5); break;
+        case KZ_VR_OGRK: f = 8 * Nt * K * (Q + 0.5) - K + T * (8 * M * (X + 1) + K - 5); break;
+        case KZ_VR_OAHK: f = 8 * Nt * K * (Q + 0.5) + T * (8 * M * (2 * V + F + 2) + 24 * V + 14 * Nt + 5); break;
+        default:
+            kz_set_error("kz_plan_flops: Table I has no row for scheme %d", scheme);
+            return KZ_ERR_UNSUPPORTED;
+    }
+    *flops = f;
+    return KZ_OK;
 }
 
 kz_status kz_sum_rate(const kz_plan* plan, const kz_cf32* X, double snr_lin, double* sinr, double* rate,

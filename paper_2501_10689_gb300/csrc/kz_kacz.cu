@@ -9,6 +9,8 @@
 //              Theorem 2), starting from r = s;  RK: only the drawn row, plus
 //              every row each K steps for the stopping test;
 //   selection  one warp per column: RK draws p_i = d_i / sum d or 1/K;
+//              SWOR-ERK draws p_i proportional to d_i over the rows not yet
+//              drawn in the current sweep of K steps (without replacement);
 //              GRK / VR-OGRK use the PAPER, BAIWU or ARGMAX rule;
 //   projection gamma = r_i / d_i,  m[Gamma_i] += gamma conj(h_i),  q_i += gamma
 //              (Alg. 1 steps 9-11).
@@ -42,8 +44,9 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
     float2* r_s = q_s + (size_t)L.K_max * J;
     float* d_s = reinterpret_cast<float*>(r_s + (size_t)L.K_max * J);
     int* stamp = reinterpret_cast<int*>(d_s + L.K_max);
+    int* swor = stamp + L.K_max;  // [K][J]: the sweep in which (row, column) was last drawn
     const int algo = L.algo;
-    const bool is_rk = (algo == KZ_RK_ENERGY || algo == KZ_RK_UNIFORM);
+    const bool is_rk = (algo == KZ_RK_ENERGY || algo == KZ_RK_UNIFORM || algo == KZ_RK_SWOR);
     const bool ogrk = (algo == KZ_VR_OGRK);
 
     int static_item = blockIdx.x;
@@ -80,6 +83,7 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
             d_s[i] = I.nrm[i] + xi;
             stamp[i] = -1;
         }
+        for (int e = tid; e < K * J; e += NT) swor[e] = -1;
         __syncthreads();
         if (warp < J) {
             double a = 0.0;
@@ -231,10 +235,17 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                         const double u = kz_uniform(L.seed, I.inst, col0 + j, t);
                         float2 r;
                         if (is_rk) {
-                            if (algo == KZ_RK_ENERGY)
+                            if (algo == KZ_RK_ENERGY) {
                                 sel = warp_pick(K, u, [&](int i) { return (double)d_s[i]; });
-                            else
+                            } else if (algo == KZ_RK_SWOR) {
+                                const int sweep = t / K;
+                                sel = warp_pick(K, u, [&](int i) {
+                                    return swor[i * J + j] == sweep ? 0.0 : (double)d_s[i];
+                                });
+                                if (lane == 0 && sel >= 0) swor[sel * J + j] = sweep;
+                            } else {
                                 sel = warp_pick(K, u, [&](int i) { return 1.0; });
+                            }
                             // no positive weight (every d_i NaN): sel < 0 stops the column below
                             const int4 rd = sel >= 0 ? I.rows[sel] : make_int4(0, 0, 0, 0);
                             const int base = sel >= 0 ? I.rptr[sel] : 0;
@@ -427,7 +438,7 @@ int occ_j(int J, size_t smem) {
 
 size_t kz_smem_kacz(int J, int Ntp, int K) {
     return (size_t)J * Ntp * sizeof(float2) + 3 * (size_t)K * J * sizeof(float2) + (size_t)K * sizeof(float) +
-           (size_t)K * sizeof(int) + 16;
+           (size_t)K * sizeof(int) + (size_t)K * J * sizeof(int) + 16;
 }
 
 cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st) {

@@ -22,7 +22,7 @@ from . import _build
 # enums of include/kzprecode.h
 KZ_OK, KZ_NOT_CONVERGED, KZ_ERR_INVALID_ARG, KZ_ERR_NUMERIC, KZ_ERR_CUDA, KZ_ERR_NOMEM, KZ_ERR_UNSUPPORTED = range(7)
 KZ_STATUS_BIT_NOT_CONVERGED, KZ_STATUS_BIT_NUMERIC, KZ_STATUS_BIT_TIMEOUT = 1, 2, 4
-ALGOS = {"rk_energy": 0, "rk_uniform": 1, "grk": 2, "ahk": 3, "vr_ogrk": 4, "vr_oahk": 5}
+ALGOS = {"rk_energy": 0, "rk_uniform": 1, "grk": 2, "ahk": 3, "vr_ogrk": 4, "vr_oahk": 5, "rk_swor": 6, "gk": 7}
 SELECT = {"paper": 0, "baiwu": 1, "argmax": 2}
 PREC = {"c64": 0, "bf16": 1}
 
@@ -50,7 +50,7 @@ EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_query",
            "kz_batch_rebind", "kz_batch_update", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
-           "kz_precoder_matrix", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
+           "kz_precoder_matrix", "kz_plan_flops", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4}
 
 
@@ -73,6 +73,8 @@ def load():
     lib.kz_plan_create.restype = I32
     lib.kz_plan_dense.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_dense.restype = I32
+    lib.kz_plan_flops.argtypes = [P, I32, I32, F64, P]
+    lib.kz_plan_flops.restype = I32
     lib.kz_precoder_matrix.argtypes = [P, P, I32, I32, I32, P, P, P]
     lib.kz_precoder_matrix.restype = I32
     lib.kz_sum_rate.argtypes = [P, P, F64, P, P, P]
@@ -372,6 +374,15 @@ def kz_precoder_matrix(plan: Plan, V, S, F, normalise=False, beta=None, stream=N
         raise ValueError("beta: expected float32 tensor of shape (1,)")
     return _check(lib.kz_precoder_matrix(plan.handle, _ptr(V), int(ncols), int(S), int(bool(normalise)), _ptr(F),
                                          _ptr(beta), _stream(stream)))
+
+
+def kz_plan_flops(plan: Plan, scheme, S, T):
+    """Table I's FLOPs for the plan: scheme "rzf" or a method name (urk is rk_uniform)."""
+    lib = load()
+    code = -1 if scheme == "rzf" else (ALGOS["rk_uniform"] if scheme == "urk" else ALGOS[scheme])
+    out = ctypes.c_double()
+    _check(lib.kz_plan_flops(plan.handle, code, int(S), float(T), ctypes.byref(out)))
+    return out.value
 
 
 def kz_sum_rate(plan: Plan, X, snr_lin, sinr=None, rate=None, stream=None):

@@ -256,3 +256,50 @@ def test_loss_pin_catches_transposed_interference():
         return -torch.sum(torch.log2(1.0 + sig / (tot - sig + 1.0 / snr_lin)))
     inst = kzgen.make_instance(1, 7, 64, vr_len_range=(20, 50), nrhs=7, rhs="identity")
     assert not loss_matches_sinr(planted, inst, 10.0, X=general_precoder(inst, 1))
+
+
+# ---------------------------------------------------------------- SWOR-ERK (Table I's comparison method)
+def swor_rows(inst, steps, rk_fn=None, seed=5):
+    sys = kz.System.from_instance(inst)
+    tr = []
+    (rk_fn or kz.rk)(sys, inst.S[:, 0], swor=True, tol=0.0, max_iter=steps, seed=seed, trace=tr)
+    return sys, np.array([t["row"] for t in tr])
+
+
+def test_swor_every_sweep_is_a_permutation(uneven_inst):
+    sys, rows = swor_rows(uneven_inst, 5 * 400)
+    for c in range(400):
+        assert sorted(rows[5 * c:5 * c + 5].tolist()) == list(range(5))
+
+
+def test_swor_draws_follow_sampling_without_replacement(uneven_inst):
+    """First draw of a sweep: d_i / D.  Pair (first, second): d_i/D * d_j/(D - d_i)."""
+    n_sweeps = 6000
+    sys, rows = swor_rows(uneven_inst, 5 * n_sweeps)
+    d = sys.d
+    D = d.sum()
+    first = rows[0::5]
+    second = rows[1::5]
+    assert chi2_ok(np.bincount(first, minlength=5) / n_sweeps, d / D, n_sweeps)
+    pair = np.zeros((5, 5))
+    for a, c in zip(first, second):
+        pair[a, c] += 1
+    p = np.array([[0.0 if i == j else d[i] / D * d[j] / (D - d[i]) for j in range(5)] for i in range(5)])
+    mask = p > 0
+    stat = n_sweeps * np.sum((pair[mask] / n_sweeps - p[mask]) ** 2 / p[mask])
+    assert stat < 60.0  # 19 dof, far tail
+
+
+def test_swor_pin_catches_replacement(uneven_inst):
+    """Drawing with replacement (plain energy RK) breaks the permutation pin."""
+    def planted(sys, s, *, swor=True, **kw):
+        return kz.rk(sys, s, energy=True, swor=False, **kw)
+    sys, rows = swor_rows(uneven_inst, 5 * 200, rk_fn=planted)
+    assert any(sorted(rows[5 * c:5 * c + 5].tolist()) != list(range(5)) for c in range(200))
+
+
+def test_gk_is_the_argmax_rule():
+    inst = kzgen.make_instance(8, 9, 72, vr_len_range=(8, 40), nrhs=2)
+    a = kz.solve(inst, inst.S, "gk", tol=1e-10, max_iter=5000)
+    b = kz.solve(inst, inst.S, "grk", rule="argmax", tol=1e-10, max_iter=5000)
+    assert np.array_equal(a["x"], b["x"]) and np.array_equal(a["iters"], b["iters"])
