@@ -195,6 +195,42 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
                         kz_cf32* v, int32_t* iters, double* resid, int32_t* status, kz_kernel kernel,
                         int32_t rhs_per_cta, int32_t refresh, void* stream);
 
+/* A fixed number of iterations of a row-action method (RK_ENERGY,
+ * RK_UNIFORM, RK_SWOR, GRK, GK, VR_OGRK) -- the fixed-T precoders of the
+ * paper's spectral-efficiency comparisons (Sec. VII, T = 15) -- recording
+ * the selected-row history for kz_unrolled_adjoint: hist_row (device
+ * int32[T * nrhs]) and hist_gam (device kz_cf32[T * nrhs]) receive the row
+ * and the step gamma of step t of column c at t * nrhs + c (row -1: the
+ * column had stopped; a column stops early only when its residual is
+ * exactly zero).  The solve takes T row projections per column (tol = 0),
+ * so the status word receives KZ_STATUS_BIT_NOT_CONVERGED by design; x, v,
+ * iters (the projections taken) and resid are those of kz_precode, v is
+ * required.  C64 plans only.  The history is all the reverse pass keeps:
+ * O(T) per column instead of the T iterates. */
+kz_status kz_precode_record(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
+                            kz_select sel, int32_t T, uint64_t seed, kz_cf32* x, kz_cf32* v,
+                            int32_t* iters, double* resid, int32_t* hist_row, kz_cf32* hist_gam,
+                            int32_t* status, void* stream);
+
+/* Gradient of a real loss through a recorded fixed-iteration solve (the
+ * unrolled adjoint; the paper has no gradient).  Given x, v and the history of
+ * kz_precode_record and the loss's gradients G_X (Nt x nrhs) and / or G_V
+ * (K x nrhs) (PyTorch's convention: dL = Re sum conj(G) dZ; either may be
+ * NULL, not both), it replays the steps in reverse -- each iterate before a
+ * step is rebuilt from the one after it and the recorded gamma, so no iterate
+ * is stored -- and writes dL/dH (grad_H_packed, packed like H_packed), dL/dxi
+ * (grad_xi, one float) and dL/ds (grad_s, K x nrhs), treating the selected
+ * rows as fixed (the selection is piecewise constant in H).  All pointers are
+ * device memory.  One CTA per column holds m and its adjoint: needs
+ * (2 Nt + 3 K) * 8 bytes of shared memory (KZ_ERR_UNSUPPORTED beyond 219
+ * KiB).  The H gradient is accumulated with atomic additions, so its last
+ * bits may vary between calls.  The first call allocates 8 bytes owned by
+ * the plan. */
+kz_status kz_unrolled_adjoint(kz_plan* plan, int32_t nrhs, float xi, int32_t T, const int32_t* iters,
+                              const int32_t* hist_row, const kz_cf32* hist_gam, const kz_cf32* x,
+                              const kz_cf32* v, const kz_cf32* G_X, const kz_cf32* G_V,
+                              kz_cf32* grad_H_packed, float* grad_xi, kz_cf32* grad_s, void* stream);
+
 /* One item of a batch: a plan with its own right-hand sides and outputs
  * (layouts as in kz_precode, all device pointers, nrhs columns each). */
 typedef struct {

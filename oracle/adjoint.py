@@ -11,6 +11,11 @@ for the RZF precoder built from the auxiliary matrix V (Remark 2):
 dense solve, no Kaczmarz), so torch.autograd gives the FP64 reference
 gradient with respect to H (on the VR entries, packed) and xi.
 ``central_difference`` perturbs one real coordinate at a time.
+
+``unrolled`` is the fixed-iteration precoder instead: T single-row Kaczmarz
+steps (eq. (update); Alg. 1 steps 8-11) on a GIVEN row sequence, written
+out in complex128 PyTorch ops, so torch.autograd differentiates through the
+steps with the selection held fixed (the reference of the unrolled adjoint).
 """
 import numpy as np
 import torch
@@ -77,3 +82,31 @@ def central_difference(inst, coords, h=1e-4, snr_lin=None):
             d[c[1]] = h if c[0] == "re" else 1j * h
             out.append((f(base + d, inst.xi) - f(base - d, inst.xi)) / (2 * h))
     return np.array(out)
+
+
+def unrolled(Hp, xi, S, rows, vr_offset, vr_len, Nt):
+    """(X, V) after the row steps rows[t][j] (-1: no step) of every column j
+    of S (K x nrhs), from m = 0, q = 0: gamma = (s_i - h_i m - xi q_i) /
+    (||h_i||^2 + xi), m += gamma conj(h_i), q_i += gamma."""
+    H = dense_from_packed_t(Hp, vr_offset, vr_len, Nt)
+    K = H.shape[0]
+    d = torch.sum(torch.abs(H) ** 2, dim=1) + xi
+    Xc, Vc = [], []
+    for j in range(S.shape[1]):
+        m = torch.zeros(Nt, dtype=H.dtype)
+        q = torch.zeros(K, dtype=H.dtype)
+        for t in range(len(rows)):
+            i = int(rows[t][j])
+            if i < 0:
+                continue
+            g = (S[i, j] - H[i] @ m - xi * q[i]) / d[i]
+            m = m + g * H[i].conj()
+            q = q + g * torch.nn.functional.one_hot(torch.tensor(i), K).to(H.dtype)
+        Xc.append(m)
+        Vc.append(q)
+    return torch.stack(Xc, dim=1), torch.stack(Vc, dim=1)
+
+
+def unrolled_loss(Hp, xi, S, rows, vr_offset, vr_len, Nt, snr_lin):
+    X, V = unrolled(Hp, xi, S, rows, vr_offset, vr_len, Nt)
+    return loss_from_VX(dense_from_packed_t(Hp, vr_offset, vr_len, Nt), V, X, snr_lin)

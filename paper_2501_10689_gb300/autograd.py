@@ -219,6 +219,58 @@ class _BatchedFn(torch.autograd.Function):
         return None, gH.view(hs), (gxi if ctx.xi_is_tensor else None), lam.view(ss)
 
 
+class KzUnrolledFn(torch.autograd.Function):
+    """Fixed-iteration row-action precoder (T projections per column, e.g. the
+    T = 15 precoders of the paper's spectral-efficiency comparisons) with the
+    unrolled adjoint: the forward keeps only the selected-row history
+    (kz_precode_record), the backward replays the steps in reverse
+    (kz_unrolled_adjoint); the row selection is held fixed."""
+
+    @staticmethod
+    def forward(ctx, H_packed, xi, S, vr_offset, vr_len, Nt, algo, sel, T, seed):
+        K = len(vr_len)
+        nrhs = S.shape[0]
+        dev = S.device
+        plan = kp.kz_plan_create(K, Nt, vr_offset, vr_len, H_packed.detach().contiguous())
+        x = torch.empty((nrhs, Nt), dtype=torch.complex64, device=dev)
+        v = torch.empty((nrhs, K), dtype=torch.complex64, device=dev)
+        iters = torch.empty(nrhs, dtype=torch.int32, device=dev)
+        resid = torch.empty(nrhs, dtype=torch.float64, device=dev)
+        hist_row = torch.empty((T, nrhs), dtype=torch.int32, device=dev)
+        hist_gam = torch.empty((T, nrhs), dtype=torch.complex64, device=dev)
+        status = torch.zeros(1, dtype=torch.int32, device=dev)
+        kp.kz_precode_record(plan, S.detach().contiguous(), nrhs, float(xi), algo, sel, T, seed, x, v, iters, resid,
+                             hist_row, hist_gam, status)
+        if int(status.item()) & kp.KZ_STATUS_BIT_NUMERIC:
+            raise kp.KzError(kp.KZ_ERR_NUMERIC, "fixed-iteration solve: NaN or Inf in a residual")
+        ctx.plan, ctx.xi, ctx.T = plan, float(xi), int(T)
+        ctx.xi_is_tensor = isinstance(xi, torch.Tensor)
+        ctx.save_for_backward(x, v, iters, hist_row, hist_gam)
+        return x, v
+
+    @staticmethod
+    def backward(ctx, gX, gV):
+        x, v, iters, hist_row, hist_gam = ctx.saved_tensors
+        plan = ctx.plan
+        nrhs = v.shape[0]
+        dev = v.device
+        if gX is None and gV is None:
+            return (None,) * 10
+        gH = torch.empty(plan.sum_len, dtype=torch.complex64, device=dev)
+        gxi = torch.empty(1, dtype=torch.float32, device=dev)
+        gS = torch.empty_like(v)
+        kp.kz_unrolled_adjoint(plan, nrhs, ctx.xi, ctx.T, iters, hist_row, hist_gam, x, v,
+                               gX.contiguous() if gX is not None else None,
+                               gV.contiguous() if gV is not None else None, gH, gxi, gS)
+        return (gH, gxi.reshape(()) if ctx.xi_is_tensor else None, gS) + (None,) * 7
+
+
+def precode_fixed(H_packed, xi, S, vr_offset, vr_len, Nt, algo="vr_ogrk", sel="paper", T=15, seed=0):
+    """Differentiable (X, V) after T row projections per column (unrolled adjoint)."""
+    return KzUnrolledFn.apply(H_packed, xi, S, np.asarray(vr_offset, np.int32), np.asarray(vr_len, np.int32), int(Nt),
+                              algo, sel, int(T), int(seed))
+
+
 def sum_rate_loss_batched(H_dense, X, snr_lin):
     """Sum over channels of sum_rate_loss: H_dense (n, K, Nt), X (n, K, Nt)."""
     F = X.transpose(1, 2) / torch.linalg.norm(X.reshape(X.shape[0], -1), dim=1)[:, None, None]

@@ -836,10 +836,14 @@ kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz
                          KZ_KERNEL_AUTO, rhs_per_cta, refresh, stream);
 }
 
-kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
-                        double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
-                        double* resid, int32_t* status, kz_kernel kernel, int32_t rhs_per_cta, int32_t refresh,
-                        void* stream) {
+}  // extern "C"
+
+// kz_precode_ex, optionally recording the selected-row history of a row-action
+// method (hist_row / hist_gam: T x nrhs, step t of column c at t * nrhs + c).
+static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
+                              double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
+                              double* resid, int32_t* status, kz_kernel kernel, int32_t rhs_per_cta, int32_t refresh,
+                              void* stream, int32_t* hist_row, kz_cf32* hist_gam, int32_t hist_T) {
     g_err.clear();
     if (kernel == KZ_KERNEL_TC) {
         if (rhs_per_cta != 0 && rhs_per_cta != 4 && rhs_per_cta != 8) {
@@ -934,6 +938,10 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
     L.status = status;
     L.Ntp_max = plan->Ntp;
     L.K_max = plan->K;
+    L.hist_row = hist_row;
+    L.hist_gam = reinterpret_cast<float2*>(hist_gam);
+    L.hist_ld = nrhs;
+    L.hist_T = hist_T;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e;
     if (kernel == KZ_KERNEL_TC) {
@@ -947,6 +955,79 @@ kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi,
         e = is_ahk_family(algo) ? kz_launch_ahk(L, J, nw, grid, smem, st) : kz_launch_kacz(L, J, nw, grid, smem, st);
     }
     return check_launch(e, "kz_precode launch");
+}
+
+extern "C" {
+
+kz_status kz_precode_ex(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
+                        double tol, int32_t max_iter, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters,
+                        double* resid, int32_t* status, kz_kernel kernel, int32_t rhs_per_cta, int32_t refresh,
+                        void* stream) {
+    return precode_impl(plan, s, nrhs, xi, algo, sel, tol, max_iter, seed, x, v, iters, resid, status, kernel,
+                        rhs_per_cta, refresh, stream, nullptr, nullptr, 0);
+}
+
+kz_status kz_precode_record(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo, kz_select sel,
+                            int32_t T, uint64_t seed, kz_cf32* x, kz_cf32* v, int32_t* iters, double* resid,
+                            int32_t* hist_row, kz_cf32* hist_gam, int32_t* status, void* stream) {
+    g_err.clear();
+    if (is_ahk_family(algo) || !valid_algo(algo)) {
+        kz_set_error("kz_precode_record: records the row-action methods (RK, GRK, GK, VR_OGRK, SWOR-ERK)");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    if (T < 1 || !hist_row || !hist_gam || !v || !aligned(hist_gam, 8) || !aligned(hist_row, 4)) {
+        kz_set_error("kz_precode_record: need T >= 1, v and the history buffers");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (plan && plan->prec != KZ_C64) {
+        kz_set_error("kz_precode_record: needs a C64 plan");
+        return KZ_ERR_UNSUPPORTED;
+    }
+    // refresh T + 1: m is never rebuilt from q inside the T steps
+    return precode_impl(plan, s, nrhs, xi, algo, sel, 0.0, T, seed, x, v, iters, resid, status, KZ_KERNEL_AUTO, 0,
+                        T + 1, stream, hist_row, hist_gam, T);
+}
+
+kz_status kz_unrolled_adjoint(kz_plan* plan, int32_t nrhs, float xi, int32_t T, const int32_t* iters,
+                              const int32_t* hist_row, const kz_cf32* hist_gam, const kz_cf32* x, const kz_cf32* v,
+                              const kz_cf32* G_X, const kz_cf32* G_V, kz_cf32* grad_H_packed, float* grad_xi,
+                              kz_cf32* grad_s, void* stream) {
+    g_err.clear();
+    if (!plan || nrhs < 1 || T < 1 || !(xi > 0.f) || !iters || !hist_row || !hist_gam || !x || !v || (!G_X && !G_V) ||
+        !grad_H_packed || !grad_xi || !grad_s) {
+        kz_set_error("kz_unrolled_adjoint: need a plan, nrhs >= 1, T >= 1, xi > 0, the history, x, v, one of "
+                     "G_X / G_V and the gradient outputs");
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (kz_smem_unrolled(plan->Nt, plan->K) > kSmemLimit) {
+        kz_set_error("kz_unrolled_adjoint: Nt = %d, K = %d do not fit one CTA's shared memory", plan->Nt, plan->K);
+        return KZ_ERR_UNSUPPORTED;
+    }
+    if (!plan->d_scratch || plan->scratch_elems < 1) {  // one double for the xi gradient
+        if (plan->d_scratch) cudaFree(plan->d_scratch);
+        plan->d_scratch = nullptr;
+        plan->scratch_elems = 0;
+        cudaError_t e = cudaMalloc((void**)&plan->d_scratch, sizeof(float2));
+        if (e != cudaSuccess) {
+            kz_set_error("kz_unrolled_adjoint: %s", cudaGetErrorString(e));
+            return KZ_ERR_NOMEM;
+        }
+        plan->scratch_elems = 1;
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    KzInst I = plan->inst();
+    I.xi = xi;
+    I.ld = nrhs;
+    double* acc = reinterpret_cast<double*>(plan->d_scratch);
+    cudaError_t e = cudaMemsetAsync(grad_H_packed, 0, (size_t)plan->sumL * sizeof(kz_cf32), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, sizeof(double), st);
+    if (e == cudaSuccess)
+        e = kz_unrolled_adjoint(I, nrhs, T, iters, hist_row, reinterpret_cast<const float2*>(hist_gam),
+                                reinterpret_cast<const float2*>(x), reinterpret_cast<const float2*>(v),
+                                reinterpret_cast<const float2*>(G_X), reinterpret_cast<const float2*>(G_V),
+                                reinterpret_cast<float2*>(grad_H_packed), acc, reinterpret_cast<float2*>(grad_s),
+                                grad_xi, st);
+    return check_launch(e, "kz_unrolled_adjoint");
 }
 
 kz_status kz_batch_prepare(kz_batch** out, const kz_batch_item* items, int32_t n, int32_t nrhs, kz_algo algo,

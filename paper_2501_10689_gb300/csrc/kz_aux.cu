@@ -258,6 +258,108 @@ __global__ void scale_kernel(float2* __restrict__ F, long long n, const float* _
     }
 }
 
+// Reverse pass through T recorded row steps (the unrolled adjoint of a
+// fixed-iteration RK / GRK / VR-OGRK solve; only the selected rows and step
+// lengths were kept).  Forward step t of a column: i = row, gamma = (s_i -
+// h_i m - xi q_i) / d_i with d_i = ||h_i||^2 + xi, m += gamma conj(h_i),
+// q_i += gamma.  With adjoints mb, qb of the state after the step (PyTorch's
+// convention: dL = Re sum conj(G) dz), the step's reverse is
+//   gb = sum_n mb_n h_in + qb_i                      (adjoint of gamma)
+//   dL/dh_in += gamma conj(mb_n) - gb conj(m_n) / d_i - (2 / d_i) Re(conj(gb) gamma) h_in
+//   mb_n -= gb conj(h_in) / d_i,   qb_i -= xi gb / d_i,   sb_i += gb / d_i,
+//   dL/dxi += -Re(conj(gb) (q_i + gamma)) / d_i
+// where m_n, q_i are the state BEFORE the step, rebuilt from the state after
+// it (m -= gamma conj(h_i), q_i -= gamma) starting from the solve's x and v.
+// One CTA per column: m, mb (Nt) and q, qb, sb (K) in shared memory; the H
+// gradient is added with atomics (its summation order over columns varies).
+__global__ void unrolled_adjoint_kernel(const __grid_constant__ KzInst I, int nrhs, int T, const int* __restrict__ iters,
+                                        const int* __restrict__ hrow, const float2* __restrict__ hgam,
+                                        const float2* __restrict__ X, const float2* __restrict__ Vq,
+                                        const float2* __restrict__ GX, const float2* __restrict__ GV,
+                                        float2* __restrict__ gH, double* __restrict__ gxi, float2* __restrict__ gS) {
+    extern __shared__ __align__(16) unsigned char ua_smem[];
+    const int K = I.K, Nt = I.Nt, j = blockIdx.x;
+    float2* m = reinterpret_cast<float2*>(ua_smem);
+    float2* mb = m + Nt;
+    float2* q = mb + Nt;
+    float2* qb = q + K;
+    float2* sb = qb + K;
+    __shared__ float2 red[32];
+    __shared__ float2 s_gb;
+    const float xi = I.xi;
+    for (int n = threadIdx.x; n < Nt; n += blockDim.x) {
+        m[n] = X[(size_t)j * Nt + n];
+        mb[n] = GX ? GX[(size_t)j * Nt + n] : make_float2(0.f, 0.f);
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        q[k] = Vq[(size_t)j * K + k];
+        qb[k] = GV ? GV[(size_t)j * K + k] : make_float2(0.f, 0.f);
+        sb[k] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
+    double gx = 0.0;
+    const int steps = min(iters[j], T);
+    for (int t = steps - 1; t >= 0; --t) {
+        const int i = hrow[(size_t)t * nrhs + j];
+        if (i < 0) continue;
+        const float2 g = hgam[(size_t)t * nrhs + j];
+        const int4 rd = I.rows[i];  // {a, len2, o, e}
+        const float2* h = I.Hc + I.rptr[i] - rd.x;
+        const float d = I.nrm[i] + xi;
+        // rebuild m before the step; gb = sum mb h (+ qb_i)
+        float ax = 0.f, ay = 0.f;
+        for (int n = rd.z + threadIdx.x; n < rd.w; n += blockDim.x) {
+            const float2 hn = h[n];
+            float2 mn = m[n];
+            mn.x -= g.x * hn.x + g.y * hn.y;
+            mn.y -= g.y * hn.x - g.x * hn.y;
+            m[n] = mn;
+            const float2 b = mb[n];
+            ax = fmaf(b.x, hn.x, fmaf(-b.y, hn.y, ax));
+            ay = fmaf(b.x, hn.y, fmaf(b.y, hn.x, ay));
+        }
+        ax = warp_sum(ax);
+        ay = warp_sum(ay);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(ax, ay);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            float2 a = qb[i];
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+                a.x += red[w].x;
+                a.y += red[w].y;
+            }
+            s_gb = a;
+        }
+        __syncthreads();
+        const float2 gb = s_gb;
+        const float id = 1.f / d;
+        const float c2 = 2.f * id * (gb.x * g.x + gb.y * g.y);
+        float2* gh = gH + I.in_off[i] - rd.z;
+        for (int n = rd.z + threadIdx.x; n < rd.w; n += blockDim.x) {
+            const float2 hn = h[n], mn = m[n], b = mb[n];
+            const float2 dh = make_float2((g.x * b.x + g.y * b.y) - id * (gb.x * mn.x + gb.y * mn.y) - c2 * hn.x,
+                                          (g.y * b.x - g.x * b.y) - id * (gb.y * mn.x - gb.x * mn.y) - c2 * hn.y);
+            atomicAdd(&gh[n].x, dh.x);
+            atomicAdd(&gh[n].y, dh.y);
+            mb[n] = make_float2(b.x - id * (gb.x * hn.x + gb.y * hn.y), b.y - id * (gb.y * hn.x - gb.x * hn.y));
+        }
+        if (threadIdx.x == 0) {
+            const float2 qp = make_float2(q[i].x - g.x, q[i].y - g.y);
+            gx -= ((double)gb.x * (qp.x + g.x) + (double)gb.y * (qp.y + g.y)) / d;
+            sb[i].x += gb.x * id;
+            sb[i].y += gb.y * id;
+            qb[i].x -= xi * gb.x * id;
+            qb[i].y -= xi * gb.y * id;
+            q[i] = qp;
+        }
+        __syncthreads();
+    }
+    for (int k = threadIdx.x; k < K; k += blockDim.x) gS[(size_t)j * K + k] = sb[k];
+    if (threadIdx.x == 0) atomicAdd(gxi, gx);
+}
+
+__global__ void double_to_float_kernel(const double* a, float* b) { *b = (float)*a; }
+
 // Gt[:, j] = G_Q[:, j] + H G_X[:, j]   (one block per row, one warp per column).
 __global__ void adjoint_rhs_kernel(const __grid_constant__ KzInst I, int nrhs, const float2* __restrict__ G_Q,
                                    const float2* __restrict__ G_X, float2* __restrict__ Gt) {
@@ -597,6 +699,21 @@ cudaError_t kz_subarray_precoder(const KzInst& I, const int* qptr, const int* qi
     if (e != cudaSuccess) return e;
     const long long n = (long long)I.Nt * ncols;
     scale_kernel<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, st>>>(F, n, beta);
+    return cudaGetLastError();
+}
+
+size_t kz_smem_unrolled(int Nt, int K) { return (size_t)(2 * Nt + 3 * K) * sizeof(float2); }
+
+cudaError_t kz_unrolled_adjoint(const KzInst& I, int nrhs, int T, const int* iters, const int* hrow, const float2* hgam,
+                                const float2* X, const float2* Vq, const float2* GX, const float2* GV, float2* gH,
+                                double* gxi, float2* gS, float* gxi_out, cudaStream_t st) {
+    const size_t smem = kz_smem_unrolled(I.Nt, I.K);
+    cudaError_t e = cudaFuncSetAttribute(unrolled_adjoint_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    unrolled_adjoint_kernel<<<nrhs, 256, smem, st>>>(I, nrhs, T, iters, hrow, hgam, X, Vq, GX, GV, gH, gxi, gS);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    double_to_float_kernel<<<1, 1, 0, st>>>(gxi, gxi_out);
     return cudaGetLastError();
 }
 

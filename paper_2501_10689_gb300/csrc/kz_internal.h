@@ -74,6 +74,11 @@ struct KzLaunch {
     int tc;               // resident kernel: tensor-core inner products (correction form)
     int m_elems;          // resident kernel: shared iterate entries per CTA (0: J x (Ntp_max + pad))
     int trow_max;         // tensor-core kernel: covering-list entries staged in shared memory (0: none)
+    // row kernel: selected-row history (row index and step gamma of step t of
+    // column c at [t * hist_ld + c], t < hist_T), or nullptr
+    int* hist_row;
+    float2* hist_gam;
+    int hist_ld, hist_T;
 };
 
 // Work item {instance, first column | (columns << 24)}: the column count of
@@ -111,6 +116,13 @@ cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nr
 // with beta non-NULL, F is scaled by beta = 1 / ||F||_F (part: S x ceil(ncols / 32) doubles).
 cudaError_t kz_subarray_precoder(const KzInst& I, const int* qptr, const int* qidx, int S, const float2* V, int ncols,
                                  float2* F, double* part, float* beta, cudaStream_t st);
+// Reverse pass through a recorded row-action solve (kz_aux.cu): one CTA per
+// column; gradients with respect to the packed H (accumulated, caller zeroes
+// it), xi (accumulated into *gxi) and s.
+cudaError_t kz_unrolled_adjoint(const KzInst& I, int nrhs, int T, const int* iters, const int* hrow, const float2* hgam,
+                                const float2* X, const float2* Vq, const float2* GX, const float2* GV, float2* gH,
+                                double* gxi, float2* gS, float* gxi_out, cudaStream_t st);
+size_t kz_smem_unrolled(int Nt, int K);
 // Coupling of every channel of a batch: mu[b] = max_k sum_{l in X_k, l != k}
 // |G_kl|^2 / (d_k d_l), d = ||h||^2 + xi (the largest squared off-diagonal
 // row mass of the row-normalised system), one block per channel.

@@ -312,6 +312,10 @@ __global__ void __launch_bounds__(NW * 32) kz_kacz_kernel(const __grid_constant_
                 if (lane == 0) {
                     s_sel[j] = sel;
                     s_gam[j] = gam;
+                    if (L.hist_row && t < L.hist_T) {  // the selected-row history (step t, this column)
+                        L.hist_row[(size_t)t * L.hist_ld + col0 + j] = sel;
+                        L.hist_gam[(size_t)t * L.hist_ld + col0 + j] = gam;
+                    }
                 }
             }
             __syncthreads();

@@ -50,7 +50,7 @@ EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_query",
            "kz_batch_rebind", "kz_batch_update", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
-           "kz_precoder_matrix", "kz_plan_flops", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
+           "kz_precode_record", "kz_unrolled_adjoint", "kz_precoder_matrix", "kz_plan_flops", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4}
 
 
@@ -73,6 +73,10 @@ def load():
     lib.kz_plan_create.restype = I32
     lib.kz_plan_dense.argtypes = [ctypes.POINTER(P), I32, I32, P, P, P, I32, P]
     lib.kz_plan_dense.restype = I32
+    lib.kz_precode_record.argtypes = [P, P, I32, F32, I32, I32, I32, U64, P, P, P, P, P, P, P, P]
+    lib.kz_precode_record.restype = I32
+    lib.kz_unrolled_adjoint.argtypes = [P, I32, F32, I32, P, P, P, P, P, P, P, P, P, P, P]
+    lib.kz_unrolled_adjoint.restype = I32
     lib.kz_plan_flops.argtypes = [P, I32, I32, F64, P]
     lib.kz_plan_flops.restype = I32
     lib.kz_precoder_matrix.argtypes = [P, P, I32, I32, I32, P, P, P]
@@ -374,6 +378,32 @@ def kz_precoder_matrix(plan: Plan, V, S, F, normalise=False, beta=None, stream=N
         raise ValueError("beta: expected float32 tensor of shape (1,)")
     return _check(lib.kz_precoder_matrix(plan.handle, _ptr(V), int(ncols), int(S), int(bool(normalise)), _ptr(F),
                                          _ptr(beta), _stream(stream)))
+
+
+def kz_precode_record(plan: Plan, s, nrhs, xi, algo, sel, T, seed, x, v, iters, resid, hist_row, hist_gam,
+                      status=None, stream=None):
+    """T row projections per column with the selected-row history: hist_row
+    int32 (T, nrhs), hist_gam complex64 (T, nrhs)."""
+    lib = load()
+    _check_c64(s, (nrhs, plan.K), "s")
+    _check_c64(x, (nrhs, plan.Nt), "x")
+    _check_c64(v, (nrhs, plan.K), "v")
+    _check_c64(hist_gam, (T, nrhs), "hist_gam")
+    if hist_row.dtype != torch.int32 or tuple(hist_row.shape) != (T, nrhs):
+        raise ValueError("hist_row: expected int32 tensor of shape (T, nrhs)")
+    return _check(lib.kz_precode_record(plan.handle, _ptr(s), int(nrhs), float(xi),
+                                        ALGOS[algo] if isinstance(algo, str) else algo,
+                                        SELECT[sel] if isinstance(sel, str) else sel, int(T), int(seed), _ptr(x),
+                                        _ptr(v), _ptr(iters), _ptr(resid), _ptr(hist_row), _ptr(hist_gam),
+                                        _ptr(status), _stream(stream)))
+
+
+def kz_unrolled_adjoint(plan: Plan, nrhs, xi, T, iters, hist_row, hist_gam, x, v, G_X, G_V, grad_H, grad_xi, grad_s,
+                        stream=None):
+    lib = load()
+    return _check(lib.kz_unrolled_adjoint(plan.handle, int(nrhs), float(xi), int(T), _ptr(iters), _ptr(hist_row),
+                                          _ptr(hist_gam), _ptr(x), _ptr(v), _ptr(G_X), _ptr(G_V), _ptr(grad_H),
+                                          _ptr(grad_xi), _ptr(grad_s), _stream(stream)))
 
 
 def kz_plan_flops(plan: Plan, scheme, S, T):
