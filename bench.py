@@ -78,6 +78,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=6.0, help="seconds per CPU-baseline leg")
     ap.add_argument("--configs", action="store_true",
                     help="measure the other workloads (configs 1, 2, 4, 5) instead of the benchmark line")
+    ap.add_argument("--sweep", action="store_true",
+                    help="fixed-T (T = 15) sum rates on the paper's scenario versus SNR and Nt (Figs. 3-4)")
     return ap.parse_args(argv)
 
 
@@ -735,10 +737,52 @@ def run_configs(args):
                   "(right-hand sides, solve, contractions), host clock, mean of 5"})
 
 
+def run_sweep(args, T=15, seeds=4):
+    """Sum rate (bits/s/Hz, eq. (rate)) of each method's precoder after T
+    iterations on the paper's scenario (multipath, Bernoulli subarray VRs,
+    K = 30, S = 20), versus SNR at Nt = 2000 and versus Nt at 10 dB; the RZF
+    curve is the library's converged VR-OAHK (tol 1e-7).  Mean over `seeds`
+    channels.  One JSON line per point."""
+    import torch
+
+    import __graft_entry__
+    import kzgen
+    from paper_2501_10689_gb300 import kzprecode as kp
+    __graft_entry__.build()
+    methods = (("vr_oahk", "paper"), ("vr_ogrk", "paper"), ("gk", "paper"), ("rk_swor", "paper"),
+               ("rk_uniform", "paper"))
+
+    def point(Nt, snr_db):
+        acc = {}
+        for seed in range(seeds):
+            inst = kzgen.paper_scenario(500 + seed, Nt=Nt, snr_db=snr_db)
+            plan = kp.plan_from_instance(inst)
+            S = kp.rhs_tensor(inst.S)
+            snr = 1.0 / inst.xi
+            runs = [("rzf", "vr_oahk", "paper", 1e-7, 5000)] + [(a, a, s_, 0.0, T) for a, s_ in methods]
+            for name, algo, sel, tol, it in runs:
+                out = kp.precode(plan, S, inst.xi, algo=algo, sel=sel, tol=tol, max_iter=it, seed=seed)
+                r = torch.empty(1, dtype=torch.float64, device="cuda")
+                kp.kz_sum_rate(plan, out["x"], snr, rate=r)
+                torch.cuda.synchronize()
+                acc[name] = acc.get(name, 0.0) + float(r.item()) / seeds
+        return acc
+
+    for snr_db in (-10.0, 0.0, 10.0, 20.0, 30.0):
+        print(json.dumps({"sweep": "snr", "Nt": 2000, "K": 30, "snr_db": snr_db, "T": T, "seeds": seeds,
+                          "sum_rate": point(2000, snr_db)}), flush=True)
+    for Nt in (1000, 2000, 4000, 8000):
+        print(json.dumps({"sweep": "Nt", "Nt": Nt, "K": 30, "snr_db": 10.0, "T": T, "seeds": seeds,
+                          "sum_rate": point(Nt, 10.0)}), flush=True)
+
+
 def main():
     args = parse()
     if args.configs:
         run_configs(args)
+        return
+    if args.sweep:
+        run_sweep(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -173,3 +173,61 @@ def config5_instance(i: int, rhs: str = "identity", nrhs: int = 128, snr_db: flo
     """Channel ``i`` of the gradient batch: Nt=2048, K=128, VR 256-1024."""
     return make_instance(BASE_SEED + 4000 + i, 128, 2048, vr_len_range=(256, 1024), snr_db=snr_db,
                          nrhs=nrhs, rhs=rhs)
+
+
+def paper_scenario(seed: int, *, Nt: int = 2000, K: int = 30, S: int = 20, p: float = 0.35, L: int = 5,
+                   fc: float = 100e9, snr_db: float = 0.0, r_range=(1.0, 50.0),
+                   theta_deg_range=(30.0, 150.0)) -> Instance:
+    """The paper's simulation scenario (Sec. II eqs. (1)-(5), Sec. VII): an
+    Nt-antenna half-wavelength ULA cut into S subarrays of Nt / S antennas,
+    K users with L paths each (line of sight from the user, L - 1 from
+    scatterers), every subarray visible to a user with probability p.
+
+    Readings of what the paper leaves open: users and scatterers at distance
+    U[r_range] and angle U[theta_deg_range] measured from the array axis (the
+    paper places a point at (d cos(theta), d sin(theta))); path gains
+    beta ~ CN(0, 1); an empty visibility set is replaced by one subarray drawn
+    uniformly; every user's channel is scaled to ||h_k|| = 1 (equal per-user
+    SNR_k = rho ||h_k||^2 / sigma^2 under power control), so the
+    regularisation is the paper's xi = 1 / SNR; identity right-hand sides (the
+    precoder matrix).
+
+    The library takes one contiguous interval per user: each VR is stored as
+    its hull (first to last visible subarray) with exact zeros on the invisible
+    subarrays in between.  meta["M"] lists each user's visible subarrays.
+    """
+    if Nt % S:
+        raise ValueError("Nt / S must be an integer")
+    rng = np.random.default_rng(seed)
+    lam = C_LIGHT / fc
+    d = lam / 2.0
+    xs = (np.arange(Nt, dtype=np.float64) - (Nt - 1) / 2.0) * d
+    sub = Nt // S
+    rows, offs, lens, Ms = [], [], [], []
+    for k in range(K):
+        dist = rng.uniform(r_range[0], r_range[1], size=L)
+        th = np.deg2rad(rng.uniform(theta_deg_range[0], theta_deg_range[1], size=L))
+        beta = (rng.normal(size=L) + 1j * rng.normal(size=L)) / np.sqrt(2.0)
+        h = np.zeros(Nt, dtype=np.complex128)
+        for l in range(L):
+            dn = np.sqrt(dist[l] ** 2 + xs ** 2 - 2.0 * xs * dist[l] * np.cos(th[l]))
+            h += beta[l] * np.exp(-2j * np.pi * (dn - dist[l]) / lam) / np.sqrt(Nt)
+        h *= np.sqrt(Nt / L)
+        vis = rng.random(S) < p
+        if not vis.any():
+            vis[int(rng.integers(0, S))] = True
+        M = np.nonzero(vis)[0]
+        mask = np.repeat(vis, sub)
+        h = h * mask
+        h /= np.linalg.norm(h)
+        o, e = int(M[0]) * sub, (int(M[-1]) + 1) * sub
+        rows.append(h[o:e])
+        offs.append(o)
+        lens.append(e - o)
+        Ms.append([int(s_) for s_ in M])
+    Hp = np.concatenate(rows).astype(np.complex64)
+    S_ = np.eye(K, dtype=np.complex64)
+    xi = 10.0 ** (-snr_db / 10.0)
+    return Instance(K=K, Nt=Nt, vr_offset=np.array(offs, dtype=np.int32), vr_len=np.array(lens, dtype=np.int32),
+                    H_packed=Hp, S=S_, xi=float(xi), snr_db=float(snr_db), seed=int(seed),
+                    meta={"M": Ms, "S": S, "p": p, "L": L, "fc": fc})

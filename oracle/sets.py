@@ -71,3 +71,57 @@ def split_fv(vr_offset, vr_len):
     fs = set(F)
     V = [k for k in range(len(vr_len)) if k not in fs]
     return F, V
+
+
+# ---------------------------------------------------------------------------
+# Subarray VRs (Sec. II eq. (5), Sec. VII): user k sees the subarrays M_k.
+# Two users' rows are orthogonal when they share no subarray (Lemma 1), so the
+# overlap graph joins users with a common subarray; it is a general graph, and
+# F is found by a near-maximum independent-set heuristic (the paper cites a
+# linear-time near-MIS method): repeatedly take a vertex of least degree in
+# the remaining graph and delete it with its neighbours.
+
+
+def subarray_adjacency(M):
+    K = len(M)
+    sets = [set(m) for m in M]
+    A = np.zeros((K, K), dtype=bool)
+    for i in range(K):
+        for j in range(K):
+            if i != j and sets[i] & sets[j]:
+                A[i, j] = True
+    return A
+
+
+def x_sets_graph(A):
+    """X_k (k included) from an adjacency matrix."""
+    return [sorted(set(np.nonzero(A[k])[0].tolist()) | {k}) for k in range(A.shape[0])]
+
+
+def mis_min_degree(A):
+    """Near-maximum independent set: least remaining degree first (ties: lower index)."""
+    alive = set(range(A.shape[0]))
+    F = []
+    while alive:
+        k = min(alive, key=lambda v: (sum(1 for u in alive if A[v, u]), v))
+        F.append(k)
+        alive -= {k} | {u for u in alive if A[k, u]}
+    return sorted(F)
+
+
+def mis_bruteforce_graph(A) -> int:
+    K = A.shape[0]
+    for size in range(K, 0, -1):
+        for sub in combinations(range(K), size):
+            if not any(A[i, j] for i in sub for j in sub if i < j):
+                return size
+    return 0
+
+
+def is_independent_graph(F, A) -> bool:
+    return not any(A[i, j] for i in F for j in F if i != j)
+
+
+def is_maximal_graph(F, A) -> bool:
+    fs = set(F)
+    return all(any(A[v, u] for u in fs) for v in range(A.shape[0]) if v not in fs)

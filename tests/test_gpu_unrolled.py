@@ -78,7 +78,7 @@ def test_unrolled_gradient_vs_fp64_autograd(kp, algo, sel):
     Lr = oadj.unrolled_loss(Hr, xr, torch.tensor(inst.S.astype(np.complex128)), rows, inst.vr_offset, inst.vr_len,
                             inst.Nt, snr)
     Lr.backward()
-    assert abs(float(L) - float(Lr)) <= 1e-5 * abs(float(Lr))
+    assert abs(float(L.detach()) - float(Lr.detach())) <= 1e-5 * abs(float(Lr.detach()))
     gH, gHr = Hp.grad.cpu().numpy(), Hr.grad.numpy()
     assert np.linalg.norm(gH - gHr) <= 1e-4 * np.linalg.norm(gHr), np.linalg.norm(gH - gHr) / np.linalg.norm(gHr)
     assert abs(float(xi.grad) - float(xr.grad)) <= 1e-4 * abs(float(xr.grad))
