@@ -603,12 +603,14 @@ def run_configs(args):
     V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
     plan = kp.plan_from_instance(inst, device=dev)
     S = kp.rhs_tensor(inst.S, device=dev)
-    for algo in ("grk", "vr_ogrk", "ahk", "vr_oahk"):
-        out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=4000)
-        err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])
-        ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, 4000))
-        emit({"workload": "config1 Nt=256 K=16 1 column SNR 10 dB", "algo": algo, "tol": 1e-6,
-              "us_per_solve": 1000 * ms, "iters": int(out["iters"][0].item()), "rel_err": err})
+    for algo in ("grk", "vr_ogrk", "gk", "ahk", "vr_oahk"):
+        for kernel in ("auto", "warp"):
+            out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=4000, kernel=kernel)
+            err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])
+            ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, 4000, kernel), reps=20)
+            it = int(out["iters"][0].item())
+            emit({"workload": "config1 Nt=256 K=16 1 column SNR 10 dB", "algo": algo, "kernel": kernel, "tol": 1e-6,
+                  "us_per_solve": 1000 * ms, "iters": it, "us_per_iter": 1000 * ms / max(it, 1), "rel_err": err})
 
     # config 2: 256 columns sharing one channel, every method, three SNRs
     for snr in (0.0, 10.0, 20.0):
@@ -617,7 +619,7 @@ def run_configs(args):
         plan = kp.plan_from_instance(inst, device=dev)
         S = kp.rhs_tensor(inst.S, device=dev)
         for algo, kernel in (("rk_energy", "auto"), ("grk", "auto"), ("vr_ogrk", "auto"), ("ahk", "auto"),
-                             ("ahk", "tc"), ("vr_oahk", "resident"), ("vr_oahk", "tc")):
+                             ("ahk", "tc"), ("vr_oahk", "resident"), ("vr_oahk", "tc"), ("vr_oahk", "group")):
             max_iter = 400000 if algo.startswith("rk") else (40000 if "grk" in algo else 4000)
             for tol in (1e-5, 3e-6, 1e-6):
                 out = kp.precode(plan, S, inst.xi, algo=algo, tol=tol, max_iter=max_iter, kernel=kernel)
@@ -633,7 +635,7 @@ def run_configs(args):
     inst = kzgen.config4()
     V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
     S = kp.rhs_tensor(inst.S, device=dev)
-    for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc")):
+    for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc"), ("c64", "group"), ("bf16", "group")):
         plan = kp.plan_from_instance(inst, prec=prec, device=dev)
         try:
             out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000, kernel=kernel)

@@ -850,6 +850,11 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
             kz_set_error("kz_precode_ex: the tensor-core kernel takes 0, 4 or 8 columns per CTA");
             return KZ_ERR_INVALID_ARG;
         }
+    } else if (kernel == KZ_KERNEL_WARP) {
+        if (rhs_per_cta != 0 && rhs_per_cta != 1 && rhs_per_cta != 4) {
+            kz_set_error("kz_precode_ex: the warp kernel takes 0, 1 or 4 columns per CTA");
+            return KZ_ERR_INVALID_ARG;
+        }
     } else if (kernel == KZ_KERNEL_GROUP) {
         if (rhs_per_cta != 0 && rhs_per_cta != 16 && rhs_per_cta != 32 && rhs_per_cta != 64) {
             kz_set_error("kz_precode_ex: the group kernel takes 0, 16, 32 or 64 columns per group");
@@ -860,7 +865,10 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         return KZ_ERR_INVALID_ARG;
     }
     kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
-                                    (kernel == KZ_KERNEL_TC || kernel == KZ_KERNEL_GROUP) ? 0 : rhs_per_cta, refresh);
+                                    (kernel == KZ_KERNEL_TC || kernel == KZ_KERNEL_GROUP || kernel == KZ_KERNEL_WARP)
+                                        ? 0
+                                        : rhs_per_cta,
+                                    refresh);
     if (rc != KZ_OK) return rc;
     if (!s || !x || !iters || !resid) {
         kz_set_error("kz_precode: s, x, iters and resid are required");
@@ -883,6 +891,38 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
     if (kernel == KZ_KERNEL_TC && !tc_ok(algo, prec)) {
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
+    }
+    if (kernel == KZ_KERNEL_WARP) {
+        if (prec != KZ_C64 || plan->K > 32 || plan->Ntp > 512 || hist_row) {
+            kz_set_error("kz_precode_ex: the warp kernel needs a C64 plan with K <= 32 and Nt <= 511");
+            return KZ_ERR_UNSUPPORTED;
+        }
+        const int nwc = rhs_per_cta ? rhs_per_cta : (nrhs >= 4 ? 4 : 1);
+        const size_t smem = kz_smem_warp(nwc, (int)plan->total2, plan->K, plan->Ntp);
+        if (smem > kSmemLimit) {
+            kz_set_error("kz_precode_ex: the channel does not fit the warp kernel's shared memory");
+            return KZ_ERR_UNSUPPORTED;
+        }
+        KzLaunch L;
+        memset(&L, 0, sizeof(L));
+        L.single = plan->inst();
+        L.single.xi = xi;
+        L.single.ld = nrhs;
+        L.single.s = reinterpret_cast<const float2*>(s);
+        L.single.x = reinterpret_cast<float2*>(x);
+        L.single.v = reinterpret_cast<float2*>(v);
+        L.single.iters = iters;
+        L.single.resid = resid;
+        L.algo = algo;
+        L.sel = sel;
+        L.prec = prec;
+        L.tol = tol;
+        L.max_iter = max_iter;
+        L.refresh = refresh ? refresh : default_refresh(algo, prec);
+        L.seed = seed;
+        L.status = status;
+        return check_launch(kz_launch_warp(L, nwc, (nrhs + nwc - 1) / nwc, smem, static_cast<cudaStream_t>(stream)),
+                            "kz_precode warp kernel");
     }
     if (kernel == KZ_KERNEL_GROUP) {
         if (!is_ahk_family(algo)) {
