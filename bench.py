@@ -604,7 +604,7 @@ def run_configs(args):
     plan = kp.plan_from_instance(inst, device=dev)
     S = kp.rhs_tensor(inst.S, device=dev)
     for algo in ("grk", "vr_ogrk", "gk", "ahk", "vr_oahk"):
-        for kernel in ("auto", "warp"):
+        for kernel in ("auto", "small"):
             out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=4000, kernel=kernel)
             err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])
             ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, 4000, kernel), reps=20)

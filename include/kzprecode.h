@@ -115,11 +115,11 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * CTAs for channels up to 2048 antennas, else every CTA of a cooperative
  * launch (then one launch serves at most SMs / blocks groups; more columns
  * take further launches).  KZ_ERR_UNSUPPORTED when a 128-antenna block is
- * seen by more than 256 users.  WARP (every method, C64, channels of at
- * most 32 users and 511 antennas whose rows fit shared memory): one warp per
- * column, lane k owning row k, the channel staged once per CTA; the
- * iteration synchronises only within the warp (rhs_per_cta 0, 1 or 4
- * columns per CTA).  AUTO: RESIDENT
+ * seen by more than 256 users.  SMALL (every method, C64, channels of at
+ * most 32 users and 511 antennas whose rows fit shared memory): one CTA of 8
+ * warps per column with the whole state in shared memory and a few short
+ * phases per step, for the latency of single small solves (rhs_per_cta 0
+ * or 1).  AUTO: RESIDENT
  * for kz_precode; the batch default is RESIDENT until kz_batch_tune or
  * kz_batch_set_launch chooses. */
 typedef enum {
@@ -127,7 +127,7 @@ typedef enum {
     KZ_KERNEL_RESIDENT = 1,
     KZ_KERNEL_TC = 3,
     KZ_KERNEL_GROUP = 4,
-    KZ_KERNEL_WARP = 5
+    KZ_KERNEL_SMALL = 5
 } kz_kernel;
 
 typedef struct kz_plan kz_plan;

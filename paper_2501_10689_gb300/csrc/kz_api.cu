@@ -850,9 +850,9 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
             kz_set_error("kz_precode_ex: the tensor-core kernel takes 0, 4 or 8 columns per CTA");
             return KZ_ERR_INVALID_ARG;
         }
-    } else if (kernel == KZ_KERNEL_WARP) {
-        if (rhs_per_cta != 0 && rhs_per_cta != 1 && rhs_per_cta != 4) {
-            kz_set_error("kz_precode_ex: the warp kernel takes 0, 1 or 4 columns per CTA");
+    } else if (kernel == KZ_KERNEL_SMALL) {
+        if (rhs_per_cta != 0 && rhs_per_cta != 1) {
+            kz_set_error("kz_precode_ex: the small-channel kernel takes 0 or 1 column per CTA");
             return KZ_ERR_INVALID_ARG;
         }
     } else if (kernel == KZ_KERNEL_GROUP) {
@@ -865,7 +865,7 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         return KZ_ERR_INVALID_ARG;
     }
     kz_status rc = check_solve_args("kz_precode", plan, nrhs, xi, algo, sel, tol, max_iter,
-                                    (kernel == KZ_KERNEL_TC || kernel == KZ_KERNEL_GROUP || kernel == KZ_KERNEL_WARP)
+                                    (kernel == KZ_KERNEL_TC || kernel == KZ_KERNEL_GROUP || kernel == KZ_KERNEL_SMALL)
                                         ? 0
                                         : rhs_per_cta,
                                     refresh);
@@ -892,15 +892,14 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
     }
-    if (kernel == KZ_KERNEL_WARP) {
+    if (kernel == KZ_KERNEL_SMALL) {
         if (prec != KZ_C64 || plan->K > 32 || plan->Ntp > 512 || hist_row) {
-            kz_set_error("kz_precode_ex: the warp kernel needs a C64 plan with K <= 32 and Nt <= 511");
+            kz_set_error("kz_precode_ex: the small-channel kernel needs a C64 plan with K <= 32 and Nt <= 511");
             return KZ_ERR_UNSUPPORTED;
         }
-        const int nwc = rhs_per_cta ? rhs_per_cta : (nrhs >= 4 ? 4 : 1);
-        const size_t smem = kz_smem_warp(nwc, (int)plan->total2, plan->K, plan->Ntp);
+        const size_t smem = kz_smem_small((int)plan->total2, plan->K, plan->Ntp);
         if (smem > kSmemLimit) {
-            kz_set_error("kz_precode_ex: the channel does not fit the warp kernel's shared memory");
+            kz_set_error("kz_precode_ex: the channel does not fit the small-channel kernel's shared memory");
             return KZ_ERR_UNSUPPORTED;
         }
         KzLaunch L;
@@ -921,8 +920,8 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         L.refresh = refresh ? refresh : default_refresh(algo, prec);
         L.seed = seed;
         L.status = status;
-        return check_launch(kz_launch_warp(L, nwc, (nrhs + nwc - 1) / nwc, smem, static_cast<cudaStream_t>(stream)),
-                            "kz_precode warp kernel");
+        return check_launch(kz_launch_small(L, nrhs, smem, static_cast<cudaStream_t>(stream)),
+                            "kz_precode small-channel kernel");
     }
     if (kernel == KZ_KERNEL_GROUP) {
         if (!is_ahk_family(algo)) {

@@ -89,10 +89,10 @@ struct KzLaunch {
 // Host-side launchers (kz_ahk.cu / kz_kacz.cu).
 cudaError_t kz_launch_ahk(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
 cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t smem, cudaStream_t st);
-// Warp kernel (kz_warp.cu): single channel with K <= 32 and Ntp <= 512, one
-// warp per column, nwc (1 or 4) columns per CTA.
-cudaError_t kz_launch_warp(const KzLaunch& L, int nwc, int grid, size_t smem, cudaStream_t st);
-size_t kz_smem_warp(int nwc, int total2, int K, int Ntp);
+// Small-channel kernel (kz_small.cu): single channel with K <= 32 and
+// Ntp <= 512, one CTA of 8 warps per column.
+cudaError_t kz_launch_small(const KzLaunch& L, int grid, size_t smem, cudaStream_t st);
+size_t kz_smem_small(int total2, int K, int Ntp);
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);

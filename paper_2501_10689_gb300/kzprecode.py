@@ -51,7 +51,7 @@ EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy
            "kz_batch_query",
            "kz_batch_rebind", "kz_batch_update", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_precode_record", "kz_unrolled_adjoint", "kz_precoder_matrix", "kz_plan_flops", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
-KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4, "warp": 5}
+KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4, "small": 5}
 
 
 def library_path() -> str:
