@@ -897,7 +897,7 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
             kz_set_error("kz_precode_ex: the small-channel kernel needs a C64 plan with K <= 32 and Nt <= 511");
             return KZ_ERR_UNSUPPORTED;
         }
-        const size_t smem = kz_smem_small((int)plan->total2, plan->K, plan->Ntp);
+        const size_t smem = kz_smem_small(plan->K, plan->Ntp);
         if (smem > kSmemLimit) {
             kz_set_error("kz_precode_ex: the channel does not fit the small-channel kernel's shared memory");
             return KZ_ERR_UNSUPPORTED;

@@ -532,7 +532,6 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     };
     // owner residual of unit u (row k0 + kk, column j): b_ref - P - xi dq
     auto owner_resid = [&](int kk, int j, int u, bool dirty) {
-        const int k = k0 + kk;
         float2 r = o_rref[u];
         if (dirty) {
             const float2* pp = L.Ppart + (size_t)g * C.n_slots * NC + j;

@@ -92,7 +92,7 @@ cudaError_t kz_launch_kacz(const KzLaunch& L, int J, int nw, int grid, size_t sm
 // Small-channel kernel (kz_small.cu): single channel with K <= 32 and
 // Ntp <= 512, one CTA of 8 warps per column.
 cudaError_t kz_launch_small(const KzLaunch& L, int grid, size_t smem, cudaStream_t st);
-size_t kz_smem_small(int total2, int K, int Ntp);
+size_t kz_smem_small(int K, int Ntp);
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec);
 size_t kz_smem_kacz(int J, int Ntp, int K);
 int kz_occupancy_ahk(int J, int nw, size_t smem, int prec);

@@ -1,19 +1,33 @@
 // Small-channel kernel: every method on one channel of at most 32 users and
 // 511 antennas, one CTA of 8 warps per right-hand side, the whole state in
-// shared memory (the channel's aligned complex64 rows, m, and r, q, d, s per
-// row).  A step is a few short phases separated by block barriers:
+// shared memory: the channel as a dense K x Ntp complex64 array (zero outside
+// each VR, so the aggregate's per-antenna sums need no index lookups), m, and
+// |r|^2, phi = r / d, q, s, 1/d per row.  Built for the latency of one solve, so a
+// step is as few short phases between block barriers as the method allows:
 //
 //   residuals   r_k = s_k - h_k m - xi q_k for the rows the method needs
 //               (Alg. 1 step 8: all rows for GRK / AHK, X_{i(t-1)} for VR-OGRK
-//               (Alg. 2 step 8), one row for RK), rows spread over the warps,
-//               each row's VR over the lanes of its warp;
-//   selection   warp 0 (lane k holds row k): inverse-CDF draws (Sec. III-A,
-//               IV-A), the Bai-Wu greedy set, argmax with the lowest index on
-//               ties; the stopping test on ||r||;
+//               (Alg. 2 step 8)), up to four rows per warp, each row's VR over
+//               the lanes, the rows' warp sums interleaved;
+//   selection   every warp on its own (lane k holds row k), so no barrier
+//               follows it: inverse-CDF draws (Sec. III-A, IV-A), the Bai-Wu
+//               greedy set, argmax with the lowest index on ties; the
+//               stopping test on ||r||;
 //   projection  m[Gamma_i] += gamma conj(h_i) over all threads (eq. (update));
-//               the orthogonal set F with each warp taking whole rows (their
-//               VRs are disjoint, Prop. 1); the aggregate u = H_V^H phi_V with
-//               one thread per antenna (eqs. (update4), (coefficient)).
+//               RK's selected row, whose residual is taken in the same phase,
+//               by warp 0 alone between the every-K-step tests; the
+//               orthogonal set F with each warp taking whole rows (their VRs
+//               are disjoint, Prop. 1); the aggregate u = H_V^H phi_V with one
+//               thread per antenna (eqs. (update4), (coefficient)).
+//
+// All per-step arithmetic is FP32 (FP64 runs at a small fraction of the FP32
+// rate on this GPU and its latency dominated a step): selection weights,
+// their running sums and the draw u (the top 24 bits of the same
+// counter-based SplitMix64 stream the other kernels use) are FP32.  Each
+// column is scaled on entry by the power of two that brings its RMS into
+// [0.5, 1); that is exact, so the iterates are exactly those of the unscaled
+// column while squared residuals cannot underflow, and the outputs are scaled
+// back exactly.
 //
 // Stopping as in the other kernels: tested where the method has its residual
 // (RK: every K projections; GRK / VR-OGRK: before every selection; AHK: before
@@ -23,42 +37,53 @@
 
 namespace {
 
-constexpr int SNT = 256, SNW = 8, SU = 2;  // threads, warps, antennas per thread (Ntp <= 512)
+constexpr int SNT = 256, SNW = 8, SU = 2, RPW = 4;  // threads, warps, antennas per thread, rows per warp
 
-// Inverse-CDF draw when lane k holds row k's weight w (lanes >= K hold 0): the
-// smallest k whose running sum (FP64, inclusive scan over the lanes) exceeds
-// u * total; the last positive weight when rounding leaves none; -1 when every
-// weight is zero.  Every lane of the warp takes part.
-__device__ __forceinline__ int lane_pick(double w, double u) {
+// Inclusive running sum over the lanes (lane k holds row k's weight).
+__device__ __forceinline__ float lane_scan(float w) {
     const int lane = threadIdx.x & 31;
-    double incl = w;
+    float incl = w;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-        const double y = __shfl_up_sync(KZ_FULL, incl, o);
+        const float y = __shfl_up_sync(KZ_FULL, incl, o);
         if (lane >= o) incl += y;
     }
-    const double total = __shfl_sync(KZ_FULL, incl, 31);
-    const unsigned hit = __ballot_sync(KZ_FULL, total > 0.0 && incl > u * total);
+    return incl;
+}
+
+// Inverse-CDF draw from a running sum: the smallest lane whose running sum
+// exceeds u * total; the last positive weight when rounding leaves none; -1
+// when every weight is zero.
+__device__ __forceinline__ int pick_scan(float incl, float w, float u) {
+    const float total = __shfl_sync(KZ_FULL, incl, 31);
+    const unsigned hit = __ballot_sync(KZ_FULL, total > 0.f && incl > u * total);
     if (hit) return __ffs(hit) - 1;
-    const unsigned pos = __ballot_sync(KZ_FULL, w > 0.0);
+    const unsigned pos = __ballot_sync(KZ_FULL, w > 0.f);
     return pos ? 31 - __clz(pos) : -1;
 }
 
-// Argmax of the lanes' values (lanes >= K pass -1), lowest lane on ties; -1 if
-// none is >= 0.  *best (if given) receives the maximum.
-__device__ __forceinline__ int lane_argmax(double v, double* best) {
+// Argmax of the lanes' values (lanes outside pass -1), lowest lane on ties;
+// -1 if none is >= 0.  *best receives the maximum.
+__device__ __forceinline__ int lane_argmax_f(float v, float* best) {
     int bi = threadIdx.x & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        const double ov = __shfl_xor_sync(KZ_FULL, v, o);
+        const float ov = __shfl_xor_sync(KZ_FULL, v, o);
         const int oi = __shfl_xor_sync(KZ_FULL, bi, o);
         if (ov > v || (ov == v && oi < bi)) {
             v = ov;
             bi = oi;
         }
     }
-    if (best) *best = v;
-    return v >= 0.0 ? bi : -1;
+    *best = v;
+    return v >= 0.f ? bi : -1;
+}
+
+// u in [0, 1): the top 24 bits of draw t of a column's SplitMix64 stream
+// (key = kz_mix64(seed + counter * golden), as in kz_uniform).
+__device__ __forceinline__ float draw24(unsigned long long key, int t) {
+    const unsigned long long z = kz_mix64(key + (unsigned long long)(t + 1) * KZ_GOLDEN);
+    return (float)(unsigned)(z >> 40) * 5.9604644775390625e-8f;
 }
 
 __device__ __forceinline__ void dot2_acc(float a, float b, float& s, float& c) {
@@ -69,142 +94,224 @@ __device__ __forceinline__ void dot2_acc(float a, float b, float& s, float& c) {
     c += pe + e;
 }
 
+__device__ __forceinline__ bool bad(float a) { return !(a == a) || isinf(a); }
+
 __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant__ KzLaunch L) {
     extern __shared__ __align__(16) unsigned char s_smem[];
-    __shared__ float2 r_s[32], q_s[32], sv_s[32], ph_s[32];
-    __shared__ float d_s[32];
-    __shared__ int drawn_s[32];
-    __shared__ double red_d[SNW];
-    __shared__ double s_a, s_num, s_pn;
-    __shared__ int s_sel;
-    __shared__ float2 s_g;
+    __shared__ float2 ph_s[32], cf_s[32], q_s[32], sv_s[32];
+    __shared__ float a2_s[32], dinv_s[32];
+    __shared__ int2 vr_s[32];
+    __shared__ unsigned xm_s[32];
+    __shared__ float red_s[SNW];
+    __shared__ double s_sn2, s_sumd;
+    __shared__ int s_stop, s_tstop;
 
     const KzInst& I = L.single;
     const int K = I.K, Nt = I.Nt, Ntp = I.Ntp;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int col = blockIdx.x;
-    const int total2 = I.rptr[K - 1] + I.rows[K - 1].y;
-    float2* Hs = reinterpret_cast<float2*>(s_smem);
-    int4* rows_s = reinterpret_cast<int4*>(Hs + ((total2 + 1) & ~1));
-    int* rptr_s = reinterpret_cast<int*>(rows_s + K);
-    float2* m = reinterpret_cast<float2*>(rptr_s + ((K + 3) & ~3));
+    float2* Hd = reinterpret_cast<float2*>(s_smem);  // Hd[k * Ntp + n]
+    float2* m = Hd + (size_t)K * Ntp;
     const float xi = I.xi;
     const int algo = L.algo;
 
-    for (int e = tid; e < total2; e += SNT) Hs[e] = I.Hc[e];
+    for (int e = tid; e < K * Ntp; e += SNT) {
+        const int k = e / Ntp, n = e - k * Ntp;
+        const int4 rk = __ldg(I.rows + k);
+        Hd[e] = (n >= rk.z && n < rk.w) ? I.Hc[__ldg(I.rptr + k) + (n - rk.x)] : make_float2(0.f, 0.f);
+    }
     for (int n = tid; n < Ntp; n += SNT) m[n] = make_float2(0.f, 0.f);
     if (tid < K) {
-        rows_s[tid] = I.rows[tid];
-        rptr_s[tid] = I.rptr[tid];
-        const float2 sv = I.s[(size_t)col * K + tid];
-        sv_s[tid] = sv;
-        r_s[tid] = sv;
+        const int4 rk = I.rows[tid];
+        vr_s[tid] = make_int2(rk.z, rk.w);
+        unsigned xm = 0u;  // X_k (k included)
+        for (int e = I.xptr[tid]; e < I.xptr[tid + 1]; ++e) xm |= 1u << I.xidx[e];
+        xm_s[tid] = xm;
+        const float dk = I.nrm[tid] + xi;
+        dinv_s[tid] = dk > 0.f ? 1.f / dk : 0.f;
         q_s[tid] = make_float2(0.f, 0.f);
-        d_s[tid] = I.nrm[tid] + xi;
-        drawn_s[tid] = -1;
+        ph_s[tid] = make_float2(0.f, 0.f);
+        cf_s[tid] = make_float2(0.f, 0.f);  // rows outside the aggregate step keep 0
     }
+    if (tid == 0) s_stop = 0;
+    if (warp == 0) {  // ||s||^2, ||B||_F^2 and the column's scale, once, in FP64
+        const float2 sv = lane < K ? I.s[(size_t)col * K + lane] : make_float2(0.f, 0.f);
+        const double a = warp_sum_d((double)sv.x * sv.x + (double)sv.y * sv.y);
+        const double b = warp_sum_d(lane < K ? I.nrmd[lane] : 0.0);
+        int ex = 0;
+        if (a > 0.0 && isfinite(a)) {
+            (void)frexp(sqrt(a / K), &ex);
+            ex = max(-120, min(120, ex));
+        }
+        const float sc = ldexpf(1.f, -ex);
+        if (lane < K) {
+            const float2 ss = make_float2(sv.x * sc, sv.y * sc);
+            sv_s[lane] = ss;
+            a2_s[lane] = ss.x * ss.x + ss.y * ss.y;
+        }
+        if (lane == 0) {
+            s_sn2 = a;
+            s_sumd = b + (double)K * xi;
+            red_s[0] = sc;
+        }
+    }
+    __syncthreads();
+    const float sc = red_s[0];
+    const float unsc = 1.f / sc;  // exact: sc is a power of two
+    const double sn2 = s_sn2;     // unscaled ||s||^2
+    const double sn2s = sn2 * (double)sc * (double)sc;
+    const float tol2f = (float)(L.tol * L.tol * sn2s);
+    const float inv_sumd = (float)(1.0 / s_sumd);
+    __syncthreads();  // red_s is reused below
+
     unsigned fmask = 0u;  // the orthogonal set F (rows of I.order[0, nF))
     for (int f = 0; f < I.nF; ++f) fmask |= 1u << I.order[f];
     const unsigned allmask = (K == 32) ? 0xffffffffu : ((1u << K) - 1u);
     const unsigned vmask = allmask & ~fmask;
-    __syncthreads();
-    double sn2 = 0.0, sumd = 0.0;  // ||s||^2 and ||B||_F^2 (warp 0 forms them, all read)
-    if (warp == 0) {
-        const float2 sv = lane < K ? sv_s[lane] : make_float2(0.f, 0.f);
-        const double a = warp_sum_d((double)sv.x * sv.x + (double)sv.y * sv.y);
-        const double b = warp_sum_d(lane < K ? I.nrmd[lane] : 0.0);
-        if (lane == 0) {
-            s_a = a;
-            s_num = b + (double)K * xi;
-        }
-    }
-    __syncthreads();
-    sn2 = s_a;
-    sumd = s_num;
-    __syncthreads();  // s_a and s_num are reused below
-    const double tol2 = L.tol * L.tol * sn2;
+    const unsigned amask = algo == KZ_VR_OAHK ? vmask : allmask;  // rows the aggregate step takes
 
-    // residuals of the rows in `mask` from the current m (plain or compensated sums)
-    auto resid = [&](unsigned mask, bool comp) {
+    // lane 0 of a warp stores row k's residual as |r_k|^2 and phi_k = r_k / d_k
+    // (cf_k = phi_k on the rows the aggregate step takes, else 0)
+    auto put_r = [&](int k, float2 r) {
+        const float di = dinv_s[k];
+        const float2 ph = make_float2(r.x * di, r.y * di);
+        a2_s[k] = r.x * r.x + r.y * r.y;
+        ph_s[k] = ph;
+        cf_s[k] = ((amask >> k) & 1u) ? ph : make_float2(0.f, 0.f);
+    };
+    // r for the rows of `mask` from the current m (plain FP32 sums): a warp's
+    // rows (up to four) advance together over their VRs, so their chains and
+    // then their warp sums interleave
+    auto resid = [&](unsigned mask) {
+        float2 acc[RPW];
+        int2 vr[RPW];
+        int imax = 0;
+#pragma unroll
+        for (int j = 0; j < RPW; ++j) {
+            acc[j] = make_float2(0.f, 0.f);
+            const int k = warp + SNW * j;
+            vr[j] = (k < K && ((mask >> k) & 1u)) ? vr_s[k] : make_int2(0, 0);
+            imax = max(imax, (vr[j].y - vr[j].x + 31) >> 5);
+        }
+        for (int i = 0; i < imax; ++i) {
+#pragma unroll
+            for (int j = 0; j < RPW; ++j) {
+                const int n = vr[j].x + lane + 32 * i;
+                if (n < vr[j].y) {
+                    const float2 hh = Hd[(size_t)(warp + SNW * j) * Ntp + n], vv = m[n];
+                    acc[j].x = fmaf(hh.x, vv.x, fmaf(-hh.y, vv.y, acc[j].x));
+                    acc[j].y = fmaf(hh.x, vv.y, fmaf(hh.y, vv.x, acc[j].y));
+                }
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+            for (int j = 0; j < RPW; ++j) {
+                if (warp + SNW * j >= K) continue;
+                acc[j].x += __shfl_xor_sync(KZ_FULL, acc[j].x, o);
+                acc[j].y += __shfl_xor_sync(KZ_FULL, acc[j].y, o);
+            }
+        }
+        if (lane == 0) {
+#pragma unroll
+            for (int j = 0; j < RPW; ++j) {
+                const int k = warp + SNW * j;
+                if (k >= K || !((mask >> k) & 1u)) continue;
+                const float2 sv = sv_s[k], qv = q_s[k];
+                put_r(k, make_float2(sv.x - acc[j].x - xi * qv.x, sv.y - acc[j].y - xi * qv.y));
+            }
+        }
+        __syncthreads();
+    };
+    // the true residual of every row (compensated sums), for confirmation
+    auto resid_true = [&]() {
         for (int k = warp; k < K; k += SNW) {
-            if (!((mask >> k) & 1u)) continue;
-            const int4 rk = rows_s[k];
-            const float2* h = Hs + rptr_s[k];
-            const float2* v = m + rk.x;
-            if (!comp) {
-                float ax = 0.f, ay = 0.f;
-                for (int p = lane; p < rk.y; p += 32) {
-                    const float2 hh = h[p], vv = v[p];
-                    ax = fmaf(hh.x, vv.x, fmaf(-hh.y, vv.y, ax));
-                    ay = fmaf(hh.x, vv.y, fmaf(hh.y, vv.x, ay));
+            const int2 vr = vr_s[k];
+            const float2* h = Hd + (size_t)k * Ntp;
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int n = vr.x + lane; n < vr.y; n += 32) {
+                const float2 hh = h[n], vv = m[n];
+                dot2_acc(hh.x, vv.x, sx, cx);
+                dot2_acc(-hh.y, vv.y, sx, cx);
+                dot2_acc(hh.x, vv.y, sy, cy);
+                dot2_acc(hh.y, vv.x, sy, cy);
+            }
+            float hx, lx, hy, ly;
+            warp_sum_c(sx, hx, lx);
+            warp_sum_c(sy, hy, ly);
+            lx += warp_sum(cx);
+            ly += warp_sum(cy);
+            if (lane == 0) put_r(k, true_resid(sv_s[k], make_float2(hx, hy), make_float2(lx, ly), q_s[k], xi));
+        }
+        __syncthreads();
+    };
+    // ||r||^2 over the rows of `mask`, every warp on its own
+    auto wnorm = [&](unsigned mask) -> float {
+        return warp_sum((lane < K && ((mask >> lane) & 1u)) ? a2_s[lane] : 0.f);
+    };
+    // sum over all rows of conj(h_k[n]) c_k for this thread's antennas (rows
+    // in two interleaved partial sums; zero coefficients drop rows out)
+    auto gather = [&](const float2* c, float2 (&u)[SU]) {
+        float2 ua[SU], ub[SU];
+#pragma unroll
+        for (int a = 0; a < SU; ++a) ua[a] = ub[a] = make_float2(0.f, 0.f);
+        int k = 0;
+#pragma unroll 2
+        for (; k + 1 < K; k += 2) {
+            const float2 c0 = c[k], c1 = c[k + 1];
+            const float2* h0 = Hd + (size_t)k * Ntp;
+            const float2* h1 = h0 + Ntp;
+#pragma unroll
+            for (int a = 0; a < SU; ++a) {
+                const int n = tid + a * SNT;
+                if (n < Ntp) {
+                    const float2 x0 = h0[n], x1 = h1[n];
+                    ua[a].x = fmaf(x0.x, c0.x, fmaf(x0.y, c0.y, ua[a].x));
+                    ua[a].y = fmaf(x0.x, c0.y, fmaf(-x0.y, c0.x, ua[a].y));
+                    ub[a].x = fmaf(x1.x, c1.x, fmaf(x1.y, c1.y, ub[a].x));
+                    ub[a].y = fmaf(x1.x, c1.y, fmaf(-x1.y, c1.x, ub[a].y));
                 }
-                ax = warp_sum(ax);
-                ay = warp_sum(ay);
-                if (lane == 0) {
-                    const float2 sv = sv_s[k], qv = q_s[k];
-                    r_s[k] = make_float2(sv.x - ax - xi * qv.x, sv.y - ay - xi * qv.y);
-                }
-            } else {
-                float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-                for (int p = lane; p < rk.y; p += 32) {
-                    const float2 hh = h[p], vv = v[p];
-                    dot2_acc(hh.x, vv.x, sx, cx);
-                    dot2_acc(-hh.y, vv.y, sx, cx);
-                    dot2_acc(hh.x, vv.y, sy, cy);
-                    dot2_acc(hh.y, vv.x, sy, cy);
-                }
-                float hx, lx, hy, ly;
-                warp_sum_c(sx, hx, lx);
-                warp_sum_c(sy, hy, ly);
-                lx += warp_sum(cx);
-                ly += warp_sum(cy);
-                if (lane == 0) r_s[k] = true_resid(sv_s[k], make_float2(hx, hy), make_float2(lx, ly), q_s[k], xi);
             }
         }
-        __syncthreads();
-    };
-    // ||r||^2 over the rows of `mask` (warp 0), every thread gets it
-    auto norm2 = [&](unsigned mask) -> double {
-        if (warp == 0) {
-            const float2 rv = lane < K ? r_s[lane] : make_float2(0.f, 0.f);
-            const double a = warp_sum_d(((mask >> lane) & 1u) ? (double)rv.x * rv.x + (double)rv.y * rv.y : 0.0);
-            if (lane == 0) s_a = a;
+        if (k < K) {
+            const float2 c0 = c[k];
+            const float2* h0 = Hd + (size_t)k * Ntp;
+#pragma unroll
+            for (int a = 0; a < SU; ++a) {
+                const int n = tid + a * SNT;
+                if (n < Ntp) {
+                    const float2 x0 = h0[n];
+                    ua[a].x = fmaf(x0.x, c0.x, fmaf(x0.y, c0.y, ua[a].x));
+                    ua[a].y = fmaf(x0.x, c0.y, fmaf(-x0.y, c0.x, ua[a].y));
+                }
+            }
         }
-        __syncthreads();
-        const double a = s_a;
-        __syncthreads();
-        return a;
+#pragma unroll
+        for (int a = 0; a < SU; ++a) u[a] = make_float2(ua[a].x + ub[a].x, ua[a].y + ub[a].y);
     };
-    // m = H^H q, one thread per antenna
+    // m = H^H q
     auto rebuild = [&]() {
-        for (int c = 0; c < SU; ++c) {
-            const int n = tid + c * SNT;
-            if (n >= Ntp) continue;
-            float2 acc = make_float2(0.f, 0.f);
-            for (int k = 0; k < K; ++k) {
-                const int4 rk = rows_s[k];
-                if (n < rk.x || n >= rk.x + rk.y) continue;
-                const float2 h = Hs[rptr_s[k] + (n - rk.x)], qk = q_s[k];
-                acc.x = fmaf(h.x, qk.x, fmaf(h.y, qk.y, acc.x));
-                acc.y = fmaf(h.x, qk.y, fmaf(-h.y, qk.x, acc.y));
-            }
-            m[n] = acc;
+        float2 u[SU];
+        gather(q_s, u);
+#pragma unroll
+        for (int a = 0; a < SU; ++a) {
+            const int n = tid + a * SNT;
+            if (n < Ntp) m[n] = u[a];
         }
         __syncthreads();
     };
-    auto confirm = [&]() -> double {
+    auto confirm = [&]() -> float {
         rebuild();
-        resid(allmask, true);
-        return norm2(allmask);
+        resid_true();
+        return wnorm(allmask);
     };
-    // m[Gamma_i] += g conj(h_i) on row i's true VR, all threads
+    // m[Gamma_i] += g conj(h_i) on row i's VR, all threads
     auto project = [&](int i, float2 g) {
-        const int4 ri = rows_s[i];
-        const float2* h = Hs + rptr_s[i];
-        for (int p = tid; p < ri.y; p += SNT) {
-            const int n = ri.x + p;
-            if (n < ri.z || n >= ri.w) continue;
-            const float2 hh = h[p];
+        const int2 vr = vr_s[i];
+        const float2* h = Hd + (size_t)i * Ntp;
+        for (int n = vr.x + tid; n < vr.y; n += SNT) {
+            const float2 hh = h[n];
             float2 v = m[n];
             v.x = fmaf(g.x, hh.x, fmaf(g.y, hh.y, v.x));
             v.y = fmaf(g.y, hh.x, fmaf(-g.x, hh.y, v.y));
@@ -212,58 +319,67 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
         }
         __syncthreads();
     };
-    // aggregate step on the rows of `mask` (eq. (update4)) with phi = r / d
+    // one warp: row i's residual over its VR, the step g = r_i / d_i, and the
+    // projection on the lanes' own entries; returns g
+    auto warp_row_step = [&](int i) -> float2 {
+        const int2 vr = vr_s[i];
+        const float2* h = Hd + (size_t)i * Ntp;
+        float ax = 0.f, ay = 0.f;
+#pragma unroll 4
+        for (int n = vr.x + lane; n < vr.y; n += 32) {
+            const float2 hh = h[n], vv = m[n];
+            ax = fmaf(hh.x, vv.x, fmaf(-hh.y, vv.y, ax));
+            ay = fmaf(hh.x, vv.y, fmaf(hh.y, vv.x, ay));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(KZ_FULL, ax, o);
+            ay += __shfl_xor_sync(KZ_FULL, ay, o);
+        }
+        const float2 sv = sv_s[i], qv = q_s[i];
+        const float di = dinv_s[i];
+        const float2 g = make_float2((sv.x - ax - xi * qv.x) * di, (sv.y - ay - xi * qv.y) * di);
+#pragma unroll 4
+        for (int n = vr.x + lane; n < vr.y; n += 32) {
+            const float2 hh = h[n];
+            float2 v = m[n];
+            v.x = fmaf(g.x, hh.x, fmaf(g.y, hh.y, v.x));
+            v.y = fmaf(g.y, hh.x, fmaf(-g.x, hh.y, v.y));
+            m[n] = v;
+        }
+        return g;
+    };
+    // aggregate step on the rows of `mask` (eq. (update4)), phi = r / d:
+    // gamma = phi^H r / (||H^H phi||^2 + xi ||phi||^2)
     auto aggregate = [&](unsigned mask) {
-        if (warp == 0) {
-            const bool in = lane < K && ((mask >> lane) & 1u);
-            const float2 rv = in ? r_s[lane] : make_float2(0.f, 0.f);
-            const float dk = lane < K ? d_s[lane] : 1.f;
-            const float2 ph = in ? make_float2(rv.x / dk, rv.y / dk) : make_float2(0.f, 0.f);
-            if (lane < K) ph_s[lane] = ph;
-            const double num = warp_sum_d(in ? ((double)rv.x * rv.x + (double)rv.y * rv.y) / dk : 0.0);
-            const double pn = warp_sum_d((double)ph.x * ph.x + (double)ph.y * ph.y);
-            if (lane == 0) {
-                s_num = num;
-                s_pn = pn;
-            }
-        }
-        __syncthreads();
         float2 u[SU];
-        double un = 0.0;
+        gather(cf_s, u);
+        float un = 0.f;
 #pragma unroll
-        for (int c = 0; c < SU; ++c) {
-            const int n = tid + c * SNT;
-            float2 acc = make_float2(0.f, 0.f);
-            if (n < Ntp) {
-                for (int k = 0; k < K; ++k) {
-                    if (!((mask >> k) & 1u)) continue;
-                    const int4 rk = rows_s[k];
-                    if (n < rk.x || n >= rk.x + rk.y) continue;
-                    const float2 h = Hs[rptr_s[k] + (n - rk.x)], pk = ph_s[k];
-                    acc.x = fmaf(h.x, pk.x, fmaf(h.y, pk.y, acc.x));
-                    acc.y = fmaf(h.x, pk.y, fmaf(-h.y, pk.x, acc.y));
-                }
-            }
-            u[c] = acc;
-            un += (double)acc.x * acc.x + (double)acc.y * acc.y;
-        }
-        un = warp_sum_d(un);
-        if (lane == 0) red_d[warp] = un;
-        __syncthreads();
-        if (tid == 0) {
-            double a = 0.0;
-            for (int w = 0; w < SNW; ++w) a += red_d[w];
-            const double den = a + (double)xi * s_pn;
-            s_g = make_float2((s_num > 0.0 && den > 0.0) ? (float)(s_num / den) : 0.f, 0.f);
-        }
-        __syncthreads();
-        const float g = s_g.x;
+        for (int a = 0; a < SU; ++a) un += u[a].x * u[a].x + u[a].y * u[a].y;
+        // phi^H r = sum |r_k|^2 / d_k and ||phi||^2, lane k holding row k
+        const bool in = lane < K && ((mask >> lane) & 1u);
+        const float dl = in ? dinv_s[lane] : 0.f, al = in ? a2_s[lane] * dl : 0.f;
+        float num = al, pn = al * dl;
 #pragma unroll
-        for (int c = 0; c < SU; ++c) {
-            const int n = tid + c * SNT;
+        for (int o = 16; o > 0; o >>= 1) {
+            un += __shfl_xor_sync(KZ_FULL, un, o);
+            num += __shfl_xor_sync(KZ_FULL, num, o);
+            pn += __shfl_xor_sync(KZ_FULL, pn, o);
+        }
+        if (lane == 0) red_s[warp] = un;
+        __syncthreads();
+        float ut = 0.f;
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) ut += red_s[w];
+        const float den = ut + xi * pn;
+        const float g = (num > 0.f && den > 0.f) ? num / den : 0.f;
+#pragma unroll
+        for (int a = 0; a < SU; ++a) {
+            const int n = tid + a * SNT;
             if (n < Ntp) {
-                m[n].x = fmaf(g, u[c].x, m[n].x);
-                m[n].y = fmaf(g, u[c].y, m[n].y);
+                m[n].x = fmaf(g, u[a].x, m[n].x);
+                m[n].y = fmaf(g, u[a].y, m[n].y);
             }
         }
         if (tid < K && ((mask >> tid) & 1u)) {
@@ -273,6 +389,9 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
         __syncthreads();
     };
 
+    const unsigned long long key =
+        kz_mix64(L.seed + (((unsigned long long)(unsigned)I.inst << 32) + (unsigned long long)(unsigned)col + 1ull) *
+                              KZ_GOLDEN);
     int t = 0, since = 0;
     bool conv = false, numeric = false;
     const bool zero = !(sn2 > 0.0);
@@ -283,64 +402,62 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
     if (zero || numeric) {
         conv = zero && !numeric;
     } else if (is_rk) {
+        // fixed weights: their running sum once; SWOR-ERK re-scans each draw
+        const float wl = lane < K ? (algo == KZ_RK_UNIFORM ? 1.f : I.nrm[lane] + xi) : 0.f;
+        const float incl = lane_scan(wl);
+        int drawn = -1;  // SWOR: the sweep in which this lane's row was last drawn (warp 0)
         while (true) {
             if (t % K == 0) {
-                resid(allmask, false);
-                const double a = norm2(allmask);
-                if (!(a == a) || isinf(a)) {
+                resid(allmask);
+                const float a = wnorm(allmask);
+                if (bad(a)) {
                     numeric = true;
                     break;
                 }
-                if (a <= tol2 && confirm() <= tol2) {
+                if (a <= tol2f && confirm() <= tol2f) {
                     conv = true;
                     break;
                 }
             }
             if (t >= L.max_iter) break;
-            if (warp == 0) {  // draw a row, then its residual (lanes over its VR)
-                const double uu = kz_uniform(L.seed, I.inst, col, t);
-                const int sweep = t / K;
-                const double dk = lane < K ? (double)d_s[lane] : 0.0;
-                int sel;
-                if (algo == KZ_RK_ENERGY)
-                    sel = lane_pick(dk, uu);
-                else if (algo == KZ_RK_SWOR)
-                    sel = lane_pick(lane < K && drawn_s[lane] != sweep ? dk : 0.0, uu);
-                else
-                    sel = lane_pick(lane < K ? 1.0 : 0.0, uu);
-                float2 g = make_float2(0.f, 0.f);
-                if (sel >= 0) {
-                    const int4 ri = rows_s[sel];
-                    const float2* h = Hs + rptr_s[sel];
-                    float ax = 0.f, ay = 0.f;
-                    for (int p = lane; p < ri.y; p += 32) {
-                        const float2 hh = h[p], vv = m[ri.x + p];
-                        ax = fmaf(hh.x, vv.x, fmaf(-hh.y, vv.y, ax));
-                        ay = fmaf(hh.x, vv.y, fmaf(hh.y, vv.x, ay));
+            const int seg = min(min(K - t % K, L.max_iter - t), refresh - since);
+            if (warp == 0) {  // seg projections by warp 0 alone
+                for (int st = 0; st < seg; ++st) {
+                    const int tt = t + st;
+                    const float u = draw24(key, tt);
+                    int sel;
+                    if (algo == KZ_RK_SWOR) {
+                        const int sweep = tt / K;
+                        const float w = drawn != sweep ? wl : 0.f;
+                        sel = pick_scan(lane_scan(w), w, u);
+                        if (lane == sel) drawn = sweep;
+                    } else {
+                        sel = pick_scan(incl, wl, u);
                     }
-                    ax = warp_sum(ax);
-                    ay = warp_sum(ay);
-                    const float2 sv = sv_s[sel], qv = q_s[sel];
-                    const float ds = d_s[sel];
-                    g = make_float2((sv.x - ax - xi * qv.x) / ds, (sv.y - ay - xi * qv.y) / ds);
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    s_sel = sel;
-                    s_g = g;
-                    if (sel >= 0) {
-                        drawn_s[sel] = sweep;
+                    if (sel < 0) {
+                        if (lane == 0) {
+                            s_stop = 1;
+                            s_tstop = tt;
+                        }
+                        break;
+                    }
+                    const float2 g = warp_row_step(sel);
+                    __syncwarp();
+                    if (lane == 0) {
                         q_s[sel].x += g.x;
                         q_s[sel].y += g.y;
                     }
+                    __syncwarp();
                 }
             }
             __syncthreads();
-            const int sel = s_sel;
-            if (sel < 0) break;
-            project(sel, s_g);
-            ++t;
-            if (++since >= refresh) {
+            if (s_stop) {  // every weight is zero: nothing left to project
+                t = s_tstop;
+                break;
+            }
+            t += seg;
+            since += seg;
+            if (since >= refresh) {
                 since = 0;
                 rebuild();
             }
@@ -349,60 +466,50 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
         int prev = -1;
         bool full = true;
         while (true) {
-            unsigned mask = allmask;
-            if (ogrk && !full) {
-                mask = 0u;
-                if (prev >= 0)
-                    for (int e = I.xptr[prev]; e < I.xptr[prev + 1]; ++e) mask |= 1u << I.xidx[e];
-            }
+            const unsigned mask = (ogrk && !full) ? xm_s[prev] : allmask;
             full = false;
-            if (mask) resid(mask, false);
-            const double a = norm2(allmask);
-            if (!(a == a) || isinf(a)) {
+            const float u = draw24(key, t);  // ahead of the residual phase, off the selection's path
+            resid(mask);
+            float a = wnorm(allmask);
+            if (bad(a)) {
                 numeric = true;
                 break;
             }
-            if (a <= tol2 && confirm() <= tol2) {
-                conv = true;
-                break;
+            if (a <= tol2f) {
+                const float ac = confirm();
+                if (ac <= tol2f) {
+                    conv = true;
+                    break;
+                }
+                a = ac;
             }
             if (t >= L.max_iter) break;
-            if (warp == 0) {
-                const double uu = kz_uniform(L.seed, I.inst, col, t);
-                const float2 rv = lane < K ? r_s[lane] : make_float2(0.f, 0.f);
-                const double a2 = (double)rv.x * rv.x + (double)rv.y * rv.y;
-                const double ratio = lane < K ? a2 / (double)d_s[lane] : -1.0;
-                int sel;
-                if (L.sel == KZ_SEL_ARGMAX) {
-                    sel = lane_argmax(ratio, nullptr);
-                } else if (L.sel == KZ_SEL_PAPER) {
-                    sel = lane_pick(a2, uu);
-                } else {
-                    double mx = 0.0;
-                    (void)lane_argmax(ratio, &mx);
-                    const double tot = warp_sum_d(a2);
-                    const double thr = 0.5 * (mx + fmin(tot / sumd, mx));
-                    sel = lane_pick(lane < K && ratio >= thr ? a2 : 0.0, uu);
-                }
-                if (lane == 0) {
-                    s_sel = sel;
-                    if (sel >= 0) {
-                        const float2 rs = r_s[sel];
-                        const float ds = d_s[sel];
-                        const float2 g = make_float2(rs.x / ds, rs.y / ds);
-                        s_g = g;
-                        q_s[sel].x += g.x;
-                        q_s[sel].y += g.y;
-                    }
-                }
+            // selection, every warp on its own
+            const float a2 = lane < K ? a2_s[lane] : 0.f;
+            const float ratio = lane < K ? a2 * dinv_s[lane] : -1.f;
+            int sel;
+            if (L.sel == KZ_SEL_ARGMAX) {
+                float mx;
+                sel = lane_argmax_f(ratio, &mx);
+            } else if (L.sel == KZ_SEL_PAPER) {
+                sel = pick_scan(lane_scan(a2), a2, u);
+            } else {  // Bai-Wu: rows with |r_k|^2 / d_k >= (max + ||r||^2 / ||B||_F^2) / 2
+                float mx;
+                (void)lane_argmax_f(ratio, &mx);
+                const float thr = 0.5f * (mx + fminf(a * inv_sumd, mx));
+                const float w = (lane < K && ratio >= thr) ? a2 : 0.f;
+                sel = pick_scan(lane_scan(w), w, u);
             }
-            __syncthreads();
-            const int sel = s_sel;
             if (sel < 0) {
                 conv = true;  // every residual is exactly zero
                 break;
             }
-            project(sel, s_g);
+            const float2 g = ph_s[sel];
+            if (tid == 0) {
+                q_s[sel].x += g.x;
+                q_s[sel].y += g.y;
+            }
+            project(sel, g);
             prev = sel;
             ++t;
             if (++since >= refresh) {
@@ -413,13 +520,13 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
         }
     } else if (ahk) {
         while (true) {
-            resid(allmask, false);
-            const double a = norm2(allmask);
-            if (!(a == a) || isinf(a)) {
+            resid(allmask);
+            const float a = wnorm(allmask);
+            if (bad(a)) {
                 numeric = true;
                 break;
             }
-            if (a <= tol2 && confirm() <= tol2) {
+            if (a <= tol2f && confirm() <= tol2f) {
                 conv = true;
                 break;
             }
@@ -434,27 +541,14 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
     } else {  // VR-OAHK
         while (t < L.max_iter) {
             ++t;
-            // orthogonal half-step: each warp projects whole rows of F (disjoint VRs)
+            // orthogonal half-step: each warp takes whole rows of F (disjoint
+            // VRs: a row's residual and projection touch only its own entries)
             if (fmask) {
-                resid(fmask, false);
                 int idx = 0;
                 for (unsigned fm = fmask; fm; fm &= fm - 1, ++idx) {
                     if (idx % SNW != warp) continue;
                     const int f = __ffs(fm) - 1;
-                    const float2 rf = r_s[f];
-                    const float df = d_s[f];
-                    const float2 g = make_float2(rf.x / df, rf.y / df);
-                    const int4 ri = rows_s[f];
-                    const float2* h = Hs + rptr_s[f];
-                    for (int p = lane; p < ri.y; p += 32) {
-                        const int n = ri.x + p;
-                        if (n < ri.z || n >= ri.w) continue;
-                        const float2 hh = h[p];
-                        float2 v = m[n];
-                        v.x = fmaf(g.x, hh.x, fmaf(g.y, hh.y, v.x));
-                        v.y = fmaf(g.y, hh.x, fmaf(-g.x, hh.y, v.y));
-                        m[n] = v;
-                    }
+                    const float2 g = warp_row_step(f);
                     if (lane == 0) {
                         q_s[f].x += g.x;
                         q_s[f].y += g.y;
@@ -462,13 +556,13 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
                 }
                 __syncthreads();
             }
-            if (vmask) resid(vmask, false);
-            const double a = norm2(vmask);
-            if (!(a == a) || isinf(a)) {
+            if (vmask) resid(vmask);
+            const float a = wnorm(vmask);
+            if (bad(a)) {
                 numeric = true;
                 break;
             }
-            if (a <= tol2 && confirm() <= tol2) {
+            if (a <= tol2f && confirm() <= tol2f) {
                 conv = true;
                 break;
             }
@@ -479,24 +573,24 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
             }
         }
     }
-    // outputs: x = H^H q, the true residual, v = q
-    const double rn2 = (zero || numeric) ? 0.0 : confirm();
-    for (int n = tid; n < Nt; n += SNT) I.x[(size_t)col * Nt + n] = zero ? make_float2(0.f, 0.f) : m[n];
-    if (I.v && tid < K) I.v[(size_t)col * K + tid] = q_s[tid];
+    // outputs: x = H^H q, the true residual, v = q (scaled back exactly)
+    const float rn2 = (zero || numeric) ? 0.f : confirm();
+    for (int n = tid; n < Nt; n += SNT) {
+        const float2 v = m[n];
+        I.x[(size_t)col * Nt + n] = zero ? make_float2(0.f, 0.f) : make_float2(v.x * unsc, v.y * unsc);
+    }
+    if (I.v && tid < K) I.v[(size_t)col * K + tid] = make_float2(q_s[tid].x * unsc, q_s[tid].y * unsc);
     if (tid == 0) {
         I.iters[col] = t;
-        I.resid[col] = zero ? 0.0 : (numeric ? (double)NAN : sqrt(rn2 / sn2));
-        if (numeric || !(rn2 == rn2)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+        I.resid[col] = zero ? 0.0 : (numeric ? (double)NAN : sqrt((double)rn2 / sn2s));
+        if (numeric || bad(rn2)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
         else if (!conv) kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
     }
 }
 
 }  // namespace
 
-size_t kz_smem_small(int total2, int K, int Ntp) {
-    return (size_t)((total2 + 1) & ~1) * sizeof(float2) + (size_t)K * sizeof(int4) + (size_t)((K + 3) & ~3) * sizeof(int) +
-           (size_t)Ntp * sizeof(float2);
-}
+size_t kz_smem_small(int K, int Ntp) { return (size_t)(K + 1) * Ntp * sizeof(float2); }
 
 cudaError_t kz_launch_small(const KzLaunch& L, int grid, size_t smem, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(kz_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
