@@ -588,13 +588,423 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_kernel(const __grid_constant_
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Register-resident variant for every method but RK on channels with
+// K <= KMAX (16 or 32) and Ntp <= 256 AU: thread n keeps antenna n's column of
+// H (and of m) in registers, so
+//
+//   residuals   each thread forms h_k[n] m[n] for all rows at once; a warp
+//               reduces the 2 KMAX partial sums by recursive halving (31
+//               shuffles for 32 values, every lane ending with one row
+//               component), the 8 warps' sums meet in shared memory across
+//               one block barrier, and every warp then finishes r_k, |r_k|^2,
+//               phi_k for all rows on its own (lane k holds row k; r, q and
+//               phi are replicated per warp, computed identically);
+//   aggregate   u[n] = sum_k conj(h_k[n]) c_k from the warp's own copy of the
+//               coefficients, ||u||^2 over one more barrier, then m[n] and q_k
+//               update in registers;
+//   projection  m[n] += g conj(h_i[n]) from the dense shared-memory copy of
+//               row i, no barrier (GRK); the orthogonal set F as one gather
+//               with coefficients r_f / d_f (disjoint VRs: one term per
+//               antenna).
+//
+// Block barriers per step: GRK / VR-OGRK 1, AHK 2, VR-OAHK 3.  The
+// confirmation stages m in shared memory and takes the rows' true residuals
+// with compensated sums, as in the shared-memory kernel above.
+// Recursive halving: v[32] per lane -> this lane's value of index `lane`
+// summed over the warp (fixed order).
+__device__ __forceinline__ float halving_sum32(float (&v)[32]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 16, w = 16; o > 0; o >>= 1, w >>= 1) {
+        const bool hi = lane & o;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if (i >= w) break;
+            const float send = hi ? v[i] : v[i + w];
+            const float keep = hi ? v[i + w] : v[i];
+            v[i] = keep + __shfl_xor_sync(KZ_FULL, send, o);
+        }
+    }
+    return v[0];
+}
+
+template <int KMAX, int AU>
+__global__ void __launch_bounds__(SNT, 1) kz_small_reg_kernel(const __grid_constant__ KzLaunch L) {
+    constexpr int NB = (2 * KMAX) / 32;  // banks of 32 partial sums: re parts, then im parts
+    extern __shared__ __align__(16) unsigned char s_smem[];
+    __shared__ float part_s[2][SNW][2 * KMAX];
+    __shared__ float red_s[2][SNW];
+    __shared__ float2 cw_s[SNW][KMAX];
+    __shared__ float2 rt_s[32];
+    __shared__ unsigned xm_s[32];
+    __shared__ int2 vr_s[32];
+    __shared__ double s_sn2, s_sumd;
+    __shared__ float s_sc;
+
+    const KzInst& I = L.single;
+    const int K = I.K, Nt = I.Nt, Ntp = I.Ntp;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int col = blockIdx.x;
+    float2* Hd = reinterpret_cast<float2*>(s_smem);  // Hd[k * Ntp + n], zero outside each VR
+    float2* m_s = Hd + (size_t)K * Ntp;                // m staged for the confirmation
+    const float xi = I.xi;
+    const int algo = L.algo;
+
+    for (int e = tid; e < K * Ntp; e += SNT) {
+        const int k = e / Ntp, n = e - k * Ntp;
+        const int4 rk = __ldg(I.rows + k);
+        Hd[e] = (n >= rk.z && n < rk.w) ? I.Hc[__ldg(I.rptr + k) + (n - rk.x)] : make_float2(0.f, 0.f);
+    }
+    if (tid < K) {
+        const int4 rk = I.rows[tid];
+        vr_s[tid] = make_int2(rk.z, rk.w);
+        unsigned xm = 0u;  // X_k (k included)
+        for (int e = I.xptr[tid]; e < I.xptr[tid + 1]; ++e) xm |= 1u << I.xidx[e];
+        xm_s[tid] = xm;
+    }
+    if (warp == 0) {  // ||s||^2, ||B||_F^2 and the column's scale, once, in FP64
+        const float2 sv = lane < K ? I.s[(size_t)col * K + lane] : make_float2(0.f, 0.f);
+        const double a = warp_sum_d((double)sv.x * sv.x + (double)sv.y * sv.y);
+        const double b = warp_sum_d(lane < K ? I.nrmd[lane] : 0.0);
+        int ex = 0;
+        if (a > 0.0 && isfinite(a)) {
+            (void)frexp(sqrt(a / K), &ex);
+            ex = max(-120, min(120, ex));
+        }
+        if (lane == 0) {
+            s_sn2 = a;
+            s_sumd = b + (double)K * xi;
+            s_sc = ldexpf(1.f, -ex);
+        }
+    }
+    __syncthreads();
+    const float sc = s_sc, unsc = 1.f / sc;  // exact: sc is a power of two
+    const double sn2 = s_sn2;
+    const double sn2s = sn2 * (double)sc * (double)sc;
+    const float tol2f = (float)(L.tol * L.tol * sn2s);
+    const float inv_sumd = (float)(1.0 / s_sumd);
+
+    // this thread's antennas: H column and m in registers
+    float2 h[AU][KMAX], m[AU];
+#pragma unroll
+    for (int a = 0; a < AU; ++a) {
+        const int n = tid + a * SNT;
+        m[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) h[a][k] = (k < K && n < Ntp) ? Hd[(size_t)k * Ntp + n] : make_float2(0.f, 0.f);
+    }
+    // lane k's row (replicated in every warp)
+    const bool own = lane < K;
+    const float2 sv = own ? make_float2(I.s[(size_t)col * K + lane].x * sc, I.s[(size_t)col * K + lane].y * sc)
+                          : make_float2(0.f, 0.f);
+    const float dk = own ? I.nrm[lane] + xi : 0.f;
+    const float dinv = dk > 0.f ? 1.f / dk : 0.f;
+    float2 q = make_float2(0.f, 0.f), ph = make_float2(0.f, 0.f);
+    float a2 = sv.x * sv.x + sv.y * sv.y;
+
+    unsigned fmask = 0u;
+    for (int f = 0; f < I.nF; ++f) fmask |= 1u << I.order[f];
+    const unsigned allmask = (K == 32) ? 0xffffffffu : ((1u << K) - 1u);
+    const unsigned vmask = allmask & ~fmask;
+
+    int pp = 0, rp = 0;  // parities of the double-buffered partial sums
+    auto set_r = [&](float2 r) {
+        a2 = r.x * r.x + r.y * r.y;
+        ph = make_float2(r.x * dinv, r.y * dinv);
+    };
+    // r for the rows of `mask` (others keep theirs)
+    auto resid = [&](unsigned mask) {
+        float v[NB][32];
+#pragma unroll
+        for (int k = 0; k < KMAX; ++k) {
+            float px = 0.f, py = 0.f;
+            if ((mask >> k) & 1u) {
+#pragma unroll
+                for (int a = 0; a < AU; ++a) {
+                    px = fmaf(h[a][k].x, m[a].x, fmaf(-h[a][k].y, m[a].y, px));
+                    py = fmaf(h[a][k].x, m[a].y, fmaf(h[a][k].y, m[a].x, py));
+                }
+            }
+            v[k / 32][k % 32] = px;
+            v[(KMAX + k) / 32][(KMAX + k) % 32] = py;
+        }
+        float* ps = part_s[pp][warp];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) ps[b * 32 + lane] = halving_sum32(v[b]);
+        __syncthreads();
+        if (own && ((mask >> lane) & 1u)) {
+            float hx = 0.f, hy = 0.f;
+#pragma unroll
+            for (int w = 0; w < SNW; ++w) {
+                hx += part_s[pp][w][lane];
+                hy += part_s[pp][w][KMAX + lane];
+            }
+            set_r(make_float2(sv.x - hx - xi * q.x, sv.y - hy - xi * q.y));
+        }
+        pp ^= 1;
+    };
+    auto rnorm = [&](unsigned mask) -> float { return warp_sum((own && ((mask >> lane) & 1u)) ? a2 : 0.f); };
+    // u[a] = sum_k conj(h_k[n]) c_k with c from lane k of this warp
+    auto gather = [&](float2 c, float2 (&u)[AU]) {
+        __syncwarp();
+        if (lane < KMAX) cw_s[warp][lane] = own ? c : make_float2(0.f, 0.f);
+        __syncwarp();
+        float2 ua[AU], ub[AU];
+#pragma unroll
+        for (int a = 0; a < AU; ++a) ua[a] = ub[a] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int k = 0; k < KMAX; k += 2) {
+            const float2 c0 = cw_s[warp][k], c1 = cw_s[warp][k + 1];
+#pragma unroll
+            for (int a = 0; a < AU; ++a) {
+                ua[a].x = fmaf(h[a][k].x, c0.x, fmaf(h[a][k].y, c0.y, ua[a].x));
+                ua[a].y = fmaf(h[a][k].x, c0.y, fmaf(-h[a][k].y, c0.x, ua[a].y));
+                ub[a].x = fmaf(h[a][k + 1].x, c1.x, fmaf(h[a][k + 1].y, c1.y, ub[a].x));
+                ub[a].y = fmaf(h[a][k + 1].x, c1.y, fmaf(-h[a][k + 1].y, c1.x, ub[a].y));
+            }
+        }
+#pragma unroll
+        for (int a = 0; a < AU; ++a) u[a] = make_float2(ua[a].x + ub[a].x, ua[a].y + ub[a].y);
+    };
+    auto rebuild = [&]() {  // m = H^H q
+        float2 u[AU];
+        gather(q, u);
+#pragma unroll
+        for (int a = 0; a < AU; ++a) m[a] = u[a];
+    };
+    // the true residual of every row: m rebuilt, staged, compensated row sums
+    auto confirm = [&]() -> float {
+        rebuild();
+#pragma unroll
+        for (int a = 0; a < AU; ++a) {
+            const int n = tid + a * SNT;
+            if (n < Ntp) m_s[n] = m[a];
+        }
+        __syncthreads();
+        for (int k = warp; k < K; k += SNW) {
+            const int2 vr = vr_s[k];
+            const float2* hk = Hd + (size_t)k * Ntp;
+            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
+            for (int n = vr.x + lane; n < vr.y; n += 32) {
+                const float2 hh = hk[n], vv = m_s[n];
+                dot2_acc(hh.x, vv.x, sx, cx);
+                dot2_acc(-hh.y, vv.y, sx, cx);
+                dot2_acc(hh.x, vv.y, sy, cy);
+                dot2_acc(hh.y, vv.x, sy, cy);
+            }
+            float hx, lx, hy, ly;
+            warp_sum_c(sx, hx, lx);
+            warp_sum_c(sy, hy, ly);
+            lx += warp_sum(cx);
+            ly += warp_sum(cy);
+            const float2 sk = make_float2(__shfl_sync(KZ_FULL, sv.x, k), __shfl_sync(KZ_FULL, sv.y, k));
+            const float2 qk = make_float2(__shfl_sync(KZ_FULL, q.x, k), __shfl_sync(KZ_FULL, q.y, k));
+            if (lane == 0) rt_s[k] = true_resid(sk, make_float2(hx, hy), make_float2(lx, ly), qk, xi);
+        }
+        __syncthreads();
+        if (own) set_r(rt_s[lane]);
+        __syncthreads();  // rt_s and m_s are rewritten by the next confirmation only after this
+        return rnorm(allmask);
+    };
+    // aggregate step on the rows of `mask` (eq. (update4))
+    auto aggregate = [&](unsigned mask) {
+        const bool in = own && ((mask >> lane) & 1u);
+        float2 u[AU];
+        gather(in ? ph : make_float2(0.f, 0.f), u);
+        float un = 0.f;
+#pragma unroll
+        for (int a = 0; a < AU; ++a) un += u[a].x * u[a].x + u[a].y * u[a].y;
+        const float al = in ? a2 * dinv : 0.f;
+        float num = al, pn = al * dinv;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            un += __shfl_xor_sync(KZ_FULL, un, o);
+            num += __shfl_xor_sync(KZ_FULL, num, o);
+            pn += __shfl_xor_sync(KZ_FULL, pn, o);
+        }
+        if (lane == 0) red_s[rp][warp] = un;
+        __syncthreads();
+        float ut = 0.f;
+#pragma unroll
+        for (int w = 0; w < SNW; ++w) ut += red_s[rp][w];
+        rp ^= 1;
+        const float den = ut + xi * pn;
+        const float g = (num > 0.f && den > 0.f) ? num / den : 0.f;
+#pragma unroll
+        for (int a = 0; a < AU; ++a) {
+            m[a].x = fmaf(g, u[a].x, m[a].x);
+            m[a].y = fmaf(g, u[a].y, m[a].y);
+        }
+        if (in) {
+            q.x = fmaf(g, ph.x, q.x);
+            q.y = fmaf(g, ph.y, q.y);
+        }
+    };
+
+    const unsigned long long key =
+        kz_mix64(L.seed + (((unsigned long long)(unsigned)I.inst << 32) + (unsigned long long)(unsigned)col + 1ull) *
+                              KZ_GOLDEN);
+    int t = 0, since = 0;
+    bool conv = false, numeric = false;
+    const bool zero = !(sn2 > 0.0);
+    if (!(sn2 == sn2) || isinf(sn2)) numeric = true;
+    const bool oahk = (algo == KZ_VR_OAHK), ahk = (algo == KZ_AHK), ogrk = (algo == KZ_VR_OGRK);
+    const int refresh = L.refresh;
+    if (zero || numeric) {
+        conv = zero && !numeric;
+    } else if (!ahk && !oahk) {  // GRK / VR-OGRK (GK arrives as GRK with argmax)
+        int prev = -1;
+        bool full = true;
+        while (true) {
+            const unsigned mask = (ogrk && !full) ? xm_s[prev] : allmask;
+            full = false;
+            const float u = draw24(key, t);
+            resid(mask);
+            float a = rnorm(allmask);
+            if (bad(a)) {
+                numeric = true;
+                break;
+            }
+            if (a <= tol2f) {
+                const float ac = confirm();
+                if (ac <= tol2f) {
+                    conv = true;
+                    break;
+                }
+                a = ac;
+            }
+            if (t >= L.max_iter) break;
+            const float w2 = own ? a2 : 0.f;
+            const float ratio = own ? a2 * dinv : -1.f;
+            int sel;
+            if (L.sel == KZ_SEL_ARGMAX) {
+                float mx;
+                sel = lane_argmax_f(ratio, &mx);
+            } else if (L.sel == KZ_SEL_PAPER) {
+                sel = pick_scan(lane_scan(w2), w2, u);
+            } else {  // Bai-Wu
+                float mx;
+                (void)lane_argmax_f(ratio, &mx);
+                const float thr = 0.5f * (mx + fminf(a * inv_sumd, mx));
+                const float w = (own && ratio >= thr) ? a2 : 0.f;
+                sel = pick_scan(lane_scan(w), w, u);
+            }
+            if (sel < 0) {
+                conv = true;  // every residual is exactly zero
+                break;
+            }
+            const float2 g = make_float2(__shfl_sync(KZ_FULL, ph.x, sel), __shfl_sync(KZ_FULL, ph.y, sel));
+            if (lane == sel) {
+                q.x += g.x;
+                q.y += g.y;
+            }
+            const float2* hs = Hd + (size_t)sel * Ntp;
+#pragma unroll
+            for (int a = 0; a < AU; ++a) {
+                const int n = tid + a * SNT;
+                if (n < Ntp) {
+                    const float2 hh = hs[n];
+                    m[a].x = fmaf(g.x, hh.x, fmaf(g.y, hh.y, m[a].x));
+                    m[a].y = fmaf(g.y, hh.x, fmaf(-g.x, hh.y, m[a].y));
+                }
+            }
+            prev = sel;
+            ++t;
+            if (++since >= refresh) {
+                since = 0;
+                rebuild();
+                full = ogrk;  // carried residuals refer to the old m
+            }
+        }
+    } else if (ahk) {
+        while (true) {
+            resid(allmask);
+            const float a = rnorm(allmask);
+            if (bad(a)) {
+                numeric = true;
+                break;
+            }
+            if (a <= tol2f && confirm() <= tol2f) {
+                conv = true;
+                break;
+            }
+            if (t >= L.max_iter) break;
+            aggregate(allmask);
+            ++t;
+            if (++since >= refresh) {
+                since = 0;
+                rebuild();
+            }
+        }
+    } else {  // VR-OAHK
+        while (t < L.max_iter) {
+            ++t;
+            if (fmask) {  // orthogonal half-step: unit steps on F, one gather (disjoint VRs)
+                resid(fmask);
+                const bool inF = own && ((fmask >> lane) & 1u);
+                const float2 g = inF ? ph : make_float2(0.f, 0.f);
+                if (inF) {
+                    q.x += g.x;
+                    q.y += g.y;
+                }
+                float2 u[AU];
+                gather(g, u);
+#pragma unroll
+                for (int a = 0; a < AU; ++a) {
+                    m[a].x += u[a].x;
+                    m[a].y += u[a].y;
+                }
+            }
+            if (vmask) resid(vmask);
+            const float a = rnorm(vmask);
+            if (bad(a)) {
+                numeric = true;
+                break;
+            }
+            if (a <= tol2f && confirm() <= tol2f) {
+                conv = true;
+                break;
+            }
+            if (vmask) aggregate(vmask);
+            if (++since >= refresh) {
+                since = 0;
+                rebuild();
+            }
+        }
+    }
+    // outputs: x = H^H q, the true residual, v = q (scaled back exactly)
+    const float rn2 = (zero || numeric) ? 0.f : confirm();
+#pragma unroll
+    for (int a = 0; a < AU; ++a) {
+        const int n = tid + a * SNT;
+        if (n < Nt) I.x[(size_t)col * Nt + n] = zero ? make_float2(0.f, 0.f) : make_float2(m[a].x * unsc, m[a].y * unsc);
+    }
+    if (I.v && warp == 0 && own) I.v[(size_t)col * K + lane] = make_float2(q.x * unsc, q.y * unsc);
+    if (tid == 0) {
+        I.iters[col] = t;
+        I.resid[col] = zero ? 0.0 : (numeric ? (double)NAN : sqrt((double)rn2 / sn2s));
+        if (numeric || bad(rn2)) kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
+        else if (!conv) kz_flag(L.status, KZ_STATUS_BIT_NOT_CONVERGED);
+    }
+}
+
 }  // namespace
 
 size_t kz_smem_small(int K, int Ntp) { return (size_t)(K + 1) * Ntp * sizeof(float2); }
 
 cudaError_t kz_launch_small(const KzLaunch& L, int grid, size_t smem, cudaStream_t st) {
-    cudaError_t e = cudaFuncSetAttribute(kz_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    kz_small_kernel<<<grid, SNT, smem, st>>>(L);
-    return cudaGetLastError();
+    auto go = [&](auto kern) -> cudaError_t {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        kern<<<grid, SNT, smem, st>>>(L);
+        return cudaGetLastError();
+    };
+    const int K = L.single.K, Ntp = L.single.Ntp;
+    const bool rk = (L.algo == KZ_RK_ENERGY || L.algo == KZ_RK_UNIFORM || L.algo == KZ_RK_SWOR);
+    if (!rk && K <= 16 && Ntp <= SNT) return go(kz_small_reg_kernel<16, 1>);
+    if (!rk && K <= 16 && Ntp <= 2 * SNT) return go(kz_small_reg_kernel<16, 2>);
+    if (!rk && K <= 32 && Ntp <= SNT) return go(kz_small_reg_kernel<32, 1>);
+    return go(kz_small_kernel);
 }
