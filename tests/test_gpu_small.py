@@ -2,7 +2,12 @@
 oracle (GB300, through the C ABI): converged x against the closed-form RZF
 (eq. (precoding)) for every method, fixed-iteration iterates against the
 oracle's literal iterates (deterministic rules, and RK / SWOR-ERK whose draws
-depend only on the row norms), and the edge cases."""
+depend only on the row norms), and the edge cases.
+
+The shapes reach each of the kernel's forms: the register-resident one with
+16 rows and one antenna per thread (config 1: 16 users, 256 antennas), with
+two antennas per thread (12 users, 400 antennas) and with 32 rows (28 users,
+200 antennas), and the shared-memory one (20 users, 301 antennas; RK always)."""
 import numpy as np
 import pytest
 
@@ -39,10 +44,20 @@ def ragged(seed=3, nrhs=5, K=20, Nt=301):
     return kzgen.make_instance(seed, K, Nt, vr_len_range=(20, 150), snr_db=10.0, nrhs=nrhs)
 
 
+SHAPES = {"config1": None, "ragged": (20, 301), "k12_n400": (12, 400), "k28_n200": (28, 200)}
+
+
+def shaped(case, seed=3, nrhs=5):
+    if case == "config1":
+        return kzgen.config1()
+    K, Nt = SHAPES[case]
+    return ragged(seed=seed, nrhs=nrhs, K=K, Nt=Nt)
+
+
 @pytest.mark.parametrize("algo,sel", ALL)
-@pytest.mark.parametrize("case", ["config1", "ragged"])
+@pytest.mark.parametrize("case", list(SHAPES))
 def test_small_converges_to_rzf(kp, algo, sel, case):
-    inst = kzgen.config1() if case == "config1" else ragged()
+    inst = shaped(case)
     V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
     out = run(kp, inst, algo, sel, tol=1e-6)
     assert out["converged"], out["status"]
@@ -55,8 +70,9 @@ def test_small_converges_to_rzf(kp, algo, sel, case):
                                         ("vr_ogrk", "argmax", 25), ("rk_energy", "paper", 45),
                                         ("rk_swor", "paper", 45)])
 @pytest.mark.parametrize("cols", [0, 1])
-def test_small_fixed_iterations_follow_the_oracle(kp, algo, sel, T, cols):
-    inst = ragged(seed=4, nrhs=6)
+@pytest.mark.parametrize("case", ["config1", "ragged", "k12_n400", "k28_n200"])
+def test_small_fixed_iterations_follow_the_oracle(kp, algo, sel, T, cols, case):
+    inst = shaped(case, seed=4, nrhs=6)
     ref = okz.solve(okz.System.from_instance(inst), inst.S, algo, rule=sel, tol=0.0, max_iter=T, seed=11)
     out = run(kp, inst, algo, sel, tol=0.0, max_iter=T, cols=cols, seed=11)
     assert np.all(out["iters"] == T)
@@ -64,8 +80,9 @@ def test_small_fixed_iterations_follow_the_oracle(kp, algo, sel, T, cols):
     assert np.max(orz.rel_err(out["v"], ref["v"])) <= 1e-5
 
 
-def test_small_iteration_counts_close_to_oracle(kp):
-    inst = ragged(seed=5, nrhs=4)
+@pytest.mark.parametrize("case", ["ragged", "k12_n400"])
+def test_small_iteration_counts_close_to_oracle(kp, case):
+    inst = shaped(case, seed=5, nrhs=4)
     for algo in ("vr_oahk", "ahk"):
         ref = okz.solve(okz.System.from_instance(inst), inst.S, algo, tol=1e-6, max_iter=5000)
         out = run(kp, inst, algo, tol=1e-6)
