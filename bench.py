@@ -78,6 +78,8 @@ def parse(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=6.0, help="seconds per CPU-baseline leg")
     ap.add_argument("--configs", action="store_true",
                     help="measure the other workloads (configs 1, 2, 4, 5) instead of the benchmark line")
+    ap.add_argument("--only", default="config1,config2,config4,config5",
+                    help="with --configs: comma-separated subset of config1, config2, config4, config5")
     ap.add_argument("--sweep", action="store_true",
                     help="fixed-T (T = 15) sum rates on the paper's scenario versus SNR and Nt (Figs. 3-4)")
     return ap.parse_args(argv)
@@ -598,22 +600,31 @@ def run_configs(args):
     def solve(plan, S, xi, algo, tol, max_iter, kernel="auto", sel="paper"):
         return kp.precode(plan, S, xi, algo=algo, sel=sel, tol=tol, max_iter=max_iter, kernel=kernel, sync=False)
 
-    # config 1: single column, latency
+    only = set(args.only.split(","))
+
+    # config 1: single column, latency.  us_per_iter_device is the slope of the
+    # solve time between two fixed iteration counts (tol = 0), free of the
+    # per-solve launch and set-up time
     inst = kzgen.config1()
     V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
     plan = kp.plan_from_instance(inst, device=dev)
     S = kp.rhs_tensor(inst.S, device=dev)
-    for algo in ("grk", "vr_ogrk", "gk", "ahk", "vr_oahk"):
+    for algo in (("rk_energy", "grk", "vr_ogrk", "gk", "ahk", "vr_oahk") if "config1" in only else ()):
+        T1, T2 = (1000, 5000) if algo == "rk_energy" else (50, 250)
         for kernel in ("auto", "small"):
-            out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=4000, kernel=kernel)
+            max_iter = 100000 if algo == "rk_energy" else 4000
+            out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=max_iter, kernel=kernel)
             err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])
-            ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, 4000, kernel), reps=20)
+            ms = _time_ms(lambda: solve(plan, S, inst.xi, algo, 1e-6, max_iter, kernel), reps=20)
+            t1 = _time_ms(lambda: solve(plan, S, inst.xi, algo, 0.0, T1, kernel), reps=20)
+            t2 = _time_ms(lambda: solve(plan, S, inst.xi, algo, 0.0, T2, kernel), reps=20)
             it = int(out["iters"][0].item())
             emit({"workload": "config1 Nt=256 K=16 1 column SNR 10 dB", "algo": algo, "kernel": kernel, "tol": 1e-6,
-                  "us_per_solve": 1000 * ms, "iters": it, "us_per_iter": 1000 * ms / max(it, 1), "rel_err": err})
+                  "us_per_solve": 1000 * ms, "iters": it, "us_per_iter": 1000 * ms / max(it, 1),
+                  "us_per_iter_device": 1000 * (t2 - t1) / (T2 - T1), "rel_err": err})
 
     # config 2: 256 columns sharing one channel, every method, three SNRs
-    for snr in (0.0, 10.0, 20.0):
+    for snr in ((0.0, 10.0, 20.0) if "config2" in only else ()):
         inst = kzgen.config2(snr)
         V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
         plan = kp.plan_from_instance(inst, device=dev)
@@ -632,22 +643,24 @@ def run_configs(args):
                   "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err": err})
 
     # config 4: large array, BF16-mixed vs complex64
-    inst = kzgen.config4()
-    V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
-    S = kp.rhs_tensor(inst.S, device=dev)
-    for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc"), ("c64", "group"), ("bf16", "group")):
-        plan = kp.plan_from_instance(inst, prec=prec, device=dev)
-        try:
-            out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000, kernel=kernel)
-        except kp.KzError as e:  # e.g. the tensor-core kernel's iterate does not fit shared memory
+    for inst in ([kzgen.config4()] if "config4" in only else []):
+        V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
+        S = kp.rhs_tensor(inst.S, device=dev)
+        for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc"), ("c64", "group"), ("bf16", "group")):
+            plan = kp.plan_from_instance(inst, prec=prec, device=dev)
+            try:
+                out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000, kernel=kernel)
+            except kp.KzError as e:  # e.g. the tensor-core kernel's iterate does not fit shared memory
+                emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
+                      "kernel": kernel, "unsupported": str(e)})
+                continue
+            err = float(np.max(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)))
+            ms = _time_ms(lambda: solve(plan, S, inst.xi, "vr_oahk", 1e-6, 3000, kernel), reps=3)
             emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
-                  "kernel": kernel, "unsupported": str(e)})
-            continue
-        err = float(np.max(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)))
-        ms = _time_ms(lambda: solve(plan, S, inst.xi, "vr_oahk", 1e-6, 3000, kernel), reps=3)
-        emit({"workload": "config4 Nt=16384 K=512 VR 1024-4096 64 columns", "algo": "vr_oahk", "prec": prec,
-              "kernel": kernel, "tol": 1e-6, "ms_per_solve": ms, "precoders_per_s": 64 / (ms / 1000.0),
-              "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err_vs_fp64": err})
+                  "kernel": kernel, "tol": 1e-6, "ms_per_solve": ms, "precoders_per_s": 64 / (ms / 1000.0),
+                  "mean_iters": float(out["iters"].float().mean().item()), "max_rel_err_vs_fp64": err})
+    if "config5" not in only:
+        return
 
     # config 5: forward + adjoint of the sum-rate loss over 64 channels
     from oracle import adjoint as oadj
@@ -706,6 +719,24 @@ def run_configs(args):
           "ms_per_batch": ms, "channels_per_s": 64 / (ms / 1000.0),
           "max_rel_err_sinr_vs_fp64_oracle_same_precoder": float(np.max(np.abs(sinr_all[0].cpu().numpy() - ref0) / ref0)),
           "sum_rate_channel0_bits": float(rate_all[0].item())})
+
+    # the precoder matrix of channel 0 by the subarray form (eq. (precoding2))
+    # from its V, against the dense product H^H V (a cuBLAS complex GEMM), with
+    # Table I's FLOP counts for the plan
+    c0, p0 = chans[0], sr_items[0]["plan"]
+    V0 = kp.precode(p0, Ss[0], c0.xi, algo="vr_oahk", tol=1e-6, max_iter=2000)["v"]
+    Hd0 = torch.tensor(c0.dense().astype(np.complex64), device=dev)
+    F_ref = torch.matmul(V0, Hd0.conj())
+    ms_dense = _time_ms(lambda: torch.matmul(V0, Hd0.conj()), reps=20)
+    Fm = torch.empty((c0.K, c0.Nt), dtype=torch.complex64, device=dev)
+    for S_sub in (16, 64):
+        ms_sub = _time_ms(lambda: kp.kz_precoder_matrix(p0, V0, S_sub, Fm), reps=20)
+        err = float(torch.linalg.norm(Fm - F_ref) / torch.linalg.norm(F_ref))
+        emit({"workload": "config5 channel 0 Nt=2048 K=128: precoder matrix F = [H_s]_{Q_s}^H [V]_{Q_s} (eq. (precoding2))",
+              "subarrays": S_sub, "us_subarray_form": 1000 * ms_sub, "us_dense_cublas_HhV": 1000 * ms_dense,
+              "rel_diff_vs_dense": err,
+              "table1_flops_vr_oahk_T15": kp.kz_plan_flops(p0, "vr_oahk", S_sub, 15.0),
+              "table1_flops_rzf": kp.kz_plan_flops(p0, "rzf", S_sub, 0.0)})
 
     # the same gradients through one batched forward and one batched adjoint
     pre = kad.BatchedPrecoder([(c.vr_offset, c.vr_len, c.Nt) for c in chans], 128, tol=1e-6, max_iter=2000)

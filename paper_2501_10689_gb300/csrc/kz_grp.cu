@@ -207,6 +207,7 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     __shared__ int s_abort, s_refresh;
     __shared__ double c_sn2[GNCMAX], c_rt2[GNCMAX], c_sum[3 * GNCMAX];
     __shared__ float c_tmp[3 * GNCMAX * 8];  // chunk sums of sum_partials (AB <= 128)
+    __shared__ float c_sumf[3 * GNCMAX], c_thr[GNCMAX];
     __shared__ float c_kap[GNCMAX], c_sig[GNCMAX], c_isig[GNCMAX], c_tau[GNCMAX], c_gam[GNCMAX], c_coef[GNCMAX];
     __shared__ int c_act[GNCMAX], c_wait[GNCMAX], c_iters[GNCMAX];
     __shared__ float c_numv[GNCMAX], c_phinv[GNCMAX];
@@ -309,10 +310,13 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     put_partial(Q_KAP, 1);
 
     // fixed-order sums of partials over the group's AB CTAs into c_sum[qi * NC + j]
-    // (nq <= 3): every (quantity, column) pair's AB partials (contiguous) are
-    // cut into chunks of 16 added by one thread each (four 16-byte loads), then
-    // the chunk sums are added in chunk order.  With the abort word read here
-    // too, this is where every CTA learns of a failure (at the same barrier).
+    // (and c_sumf, its float value) (nq <= 3): every (quantity, column) pair's
+    // AB partials (contiguous) are cut into chunks of 16 added by one thread
+    // each (four 16-byte loads), then the chunk sums are added in chunk order;
+    // FP32 with TwoSum compensation throughout (no FP64 arithmetic, whose rate
+    // on this GPU is a small fraction of FP32's).  With the abort word read
+    // here too, this is where every CTA learns of a failure (at the same
+    // barrier).
     auto sum_partials = [&](const int* qs, int nq) {
         const int pairs = nq * NC, nch = (AB + 15) / 16, tasks = pairs * nch;
         if (tid == 0) s_abort = (__ldcg(abort_word) <= gen) ? 1 : 0;
@@ -321,24 +325,40 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             const int p = tk / nch, c = tk % nch;
             const float* src = cp + ((size_t)qs[p / NC] * NC + (p % NC)) * AB + 16 * c;
             const int n = min(16, AB - 16 * c);
-            double a = 0.0;
+            float hi = 0.f, lo = 0.f;
+            auto add = [&](float v) {
+                float sm, e;
+                two_sum(hi, v, sm, e);
+                hi = sm;
+                lo += e;
+            };
             if (n == 16 && (AB & 3) == 0) {
-                const float4 x0 = __ldcg(reinterpret_cast<const float4*>(src));
-                const float4 x1 = __ldcg(reinterpret_cast<const float4*>(src) + 1);
-                const float4 x2 = __ldcg(reinterpret_cast<const float4*>(src) + 2);
-                const float4 x3 = __ldcg(reinterpret_cast<const float4*>(src) + 3);
-                a = (((double)x0.x + x0.y) + ((double)x0.z + x0.w)) + (((double)x1.x + x1.y) + ((double)x1.z + x1.w)) +
-                    (((double)x2.x + x2.y) + ((double)x2.z + x2.w)) + (((double)x3.x + x3.y) + ((double)x3.z + x3.w));
+                float4 x[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) x[i] = __ldcg(reinterpret_cast<const float4*>(src) + i);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    add(x[i].x);
+                    add(x[i].y);
+                    add(x[i].z);
+                    add(x[i].w);
+                }
             } else {
-                for (int i = 0; i < n; ++i) a += (double)__ldcg(src + i);
+                for (int i = 0; i < n; ++i) add(__ldcg(src + i));
             }
-            c_tmp[tk] = (float)a;
+            c_tmp[tk] = hi + lo;
         }
         __syncthreads();
         for (int p = tid; p < pairs; p += GT) {
-            double a = 0.0;
-            for (int c = 0; c < nch; ++c) a += (double)c_tmp[p * nch + c];
-            c_sum[p] = a;
+            float hi = 0.f, lo = 0.f;
+            for (int c = 0; c < nch; ++c) {
+                float sm, e;
+                two_sum(hi, c_tmp[p * nch + c], sm, e);
+                hi = sm;
+                lo += e;
+            }
+            c_sum[p] = (double)hi + (double)lo;
+            c_sumf[p] = hi + lo;
         }
         __syncthreads();
     };
@@ -357,6 +377,7 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
         const int j = tid;
         const double sn2 = c_sum[j], kap2 = c_sum[NC + j];
         c_sn2[j] = sn2;
+        c_thr[j] = (float)(L.tol * L.tol * sn2);
         c_rt2[j] = sn2;
         const bool bad = !(sn2 == sn2) || isinf(sn2);
         c_act[j] = (j < ncols) && sn2 > 0.0 && !bad;
@@ -735,17 +756,17 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
             if (tid < NC) {
                 const int j = tid;
                 if (!resumed && c_act[j] && !c_wait[j]) {
-                    const double rv2 = c_sum[j];
+                    const float rv2 = c_sumf[j];
                     if (!(rv2 == rv2) || isinf(rv2)) {
                         c_act[j] = 0;
                         c_iters[j] = t;
                         if (b == 0) flag(L.status, KZ_STATUS_BIT_NUMERIC);
-                    } else if (rv2 <= L.tol * L.tol * c_sn2[j]) {
+                    } else if (rv2 <= c_thr[j]) {
                         c_wait[j] = 1;
                     }
                 }
-                c_numv[j] = (float)c_sum[NC + j];
-                c_phinv[j] = (float)c_sum[2 * NC + j];
+                c_numv[j] = c_sumf[NC + j];
+                c_phinv[j] = c_sumf[2 * NC + j];
             }
             __syncthreads();
             if (tid == 0) {
@@ -777,8 +798,8 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
                 const int j = tid;
                 float gm = 0.f;
                 if (c_act[j] && !c_wait[j] && c_numv[j] > 0.f) {
-                    const double den = c_sum[j] + (double)xi * c_phinv[j];
-                    gm = den > 0.0 ? (float)(c_numv[j] / den) : 0.f;
+                    const float den = c_sumf[j] + xi * c_phinv[j];
+                    gm = den > 0.f ? c_numv[j] / den : 0.f;
                 }
                 c_gam[j] = gm;
                 c_coef[j] = gm * sigH * c_tau[j];
