@@ -190,7 +190,8 @@ kz_status kz_plan_query(const kz_plan* plan, int32_t* K, int32_t* Nt, int64_t* s
  *   xi > 0; tol >= 0; max_iter >= 1; nrhs >= 1.  rhs_per_cta in {0,1,2,4,8}
  *   (0 = the plan's tuned choice).  refresh: recompute m = H^H q every
  *   `refresh` iterations (0 = default: 16 for AHK / VR_OAHK on C64, 6 for
- *   BF16_MIXED, 8 with KZ_KERNEL_TC, 512 for the RK family).
+ *   BF16_MIXED, 8 with KZ_KERNEL_TC, 16 with KZ_KERNEL_GROUP, 512 for the RK
+ *   family).
  * Returns KZ_OK once the work is enqueued. */
 kz_status kz_precode(kz_plan* plan, const kz_cf32* s, int32_t nrhs, float xi, kz_algo algo,
                      kz_select sel, double tol, int32_t max_iter, uint64_t seed, kz_cf32* x,

@@ -500,7 +500,7 @@ kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo
     L.fmt = fmt;
     L.tol = tol;
     L.max_iter = max_iter;
-    L.refresh = refresh ? refresh : 8;
+    L.refresh = refresh ? refresh : 16;  // swept on configs 2 and 4: 8 -> 16 saves 4-6%, iterations +2%
     L.status = status;
     L.Ppart = reinterpret_cast<float2*>(base);
     L.Phi = reinterpret_cast<uint16_t*>(base + b_pp);
