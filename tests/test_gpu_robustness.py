@@ -87,8 +87,8 @@ def test_benchmark_batch_every_channel(kp, config3_batch, launch):
 
 
 # ---------------------------------------------------------------- corrupted inputs
-def _nan_case(kp, where, algo, sel, kernel):
-    inst = kzgen.make_instance(81, 24, 400, vr_len_range=(40, 160), nrhs=8, snr_db=10.0)
+def _nan_case(kp, where, algo, sel, kernel, K=24, Nt=400):
+    inst = kzgen.make_instance(81, K, Nt, vr_len_range=(40, 160), nrhs=8, snr_db=10.0)
     Hp = inst.H_packed.copy()
     S = inst.S.copy()
     if where == "H":
@@ -116,6 +116,17 @@ def _nan_case(kp, where, algo, sel, kernel):
                                              ("vr_ogrk", "argmax", "auto"), ("rk_energy", "paper", "auto")])
 def test_nan_input_sets_numeric_bit(kp, where, algo, sel, kernel):
     out = _nan_case(kp, where, algo, sel, kernel)
+    assert out["status"] & kp.KZ_STATUS_BIT_NUMERIC, out
+
+
+@pytest.mark.parametrize("where", ["H", "s"])
+@pytest.mark.parametrize("algo,sel", [("vr_oahk", "paper"), ("ahk", "paper"), ("grk", "paper"),
+                                      ("vr_ogrk", "argmax"), ("rk_swor", "paper")])
+@pytest.mark.parametrize("shape", [(24, 400), (12, 200)])
+def test_nan_input_small_channel_kernel(kp, where, algo, sel, shape):
+    """Both forms of the small-channel kernel: shared-memory (24 users, 400
+    antennas; RK always) and register-resident (12 users, 200 antennas)."""
+    out = _nan_case(kp, where, algo, sel, "small", K=shape[0], Nt=shape[1])
     assert out["status"] & kp.KZ_STATUS_BIT_NUMERIC, out
 
 
