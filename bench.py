@@ -514,7 +514,7 @@ def run_ours(args):
                     ts.append(a.elapsed_time(b))
         return statistics.median(ts)
 
-    def update_plans(H):  # every channel's set-up in three launches
+    def update_plans(H):  # every channel's set-up in four launches
         kp.kz_batch_update(batch, H)
 
     ms_new = e2e_loop(True)

@@ -282,7 +282,7 @@ kz_status kz_batch_rebind(kz_batch* batch, const kz_batch_item* items, void* str
  * (layout of kz_plan_create) concatenated in item order, item b's at
  * sum_{c<b} sum(vr_len of item c).  Every item's plan is updated as
  * kz_plan_update would (packing, row norms, inner products of overlapping
- * rows), in three kernel launches for the whole batch, asynchronously on
+ * rows), in four kernel launches for the whole batch, asynchronously on
  * `stream` (the first call also uploads a small row table owned by the
  * batch, synchronously).  The items must name distinct plans
  * (KZ_ERR_INVALID_ARG otherwise).  The batch's queue order is kept. */

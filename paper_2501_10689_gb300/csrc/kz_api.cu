@@ -477,7 +477,7 @@ kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo
     const size_t b_phi = align256((size_t)CG * P->K * 2 * NC * sizeof(uint16_t));
     const size_t b_q = align256((size_t)CG * P->K * NC * sizeof(float2));
     const size_t b_cp = align256((size_t)CG * 7 * AB * NC * sizeof(float));
-    const size_t b_bar = align256((size_t)(1 + CG) * sizeof(unsigned));
+    const size_t b_bar = align256((size_t)(2 * CG) * sizeof(unsigned));
     const size_t need = b_pp + b_phi + b_q + b_cp + b_bar;
     if (G.scr_bytes < need) {
         if (G.d_scr) cudaFree(G.d_scr);
@@ -520,8 +520,8 @@ kz_status run_grp(kz_plan* P, const kz_cf32* s, int nrhs, float xi, kz_algo algo
         L.v = v ? reinterpret_cast<float2*>(v) + (size_t)c0 * P->K : nullptr;
         L.iters = iters + c0;
         L.resid = resid + c0;
-        cudaError_t e = cudaMemsetAsync(L.gbar, 0, sizeof(unsigned), st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(L.gbar + 1, 0xff, (size_t)L.CG * sizeof(unsigned), st);
+        cudaError_t e = cudaMemsetAsync(L.gbar, 0, (size_t)L.CG * sizeof(unsigned), st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(L.gbar + L.CG, 0xff, (size_t)L.CG * sizeof(unsigned), st);
         if (e == cudaSuccess) e = kz_launch_grp(L, cluster, smem, st);
         if (e != cudaSuccess) return check_launch(e, "group kernel launch");
     }

@@ -39,24 +39,49 @@ __global__ void pack_dense_kernel(const float2* __restrict__ Hd, int Nt, const i
     }
 }
 
-// ||h_k||^2 with FP64 accumulation (one block per row).
+// ||h_k||^2 (one block per row) with Dot2-compensated FP32 sums: each thread
+// carries (sum, error) words, the warps and then the block combine them with
+// TwoSum in a fixed order; the result is about as accurate as an FP64 sum
+// (GB300's FP64 rate is a small fraction of FP32's).
+__device__ __forceinline__ void dot2_add(float a, float b, float& s, float& c);
+
+__device__ double row_norm2(const float2* __restrict__ h, int len) {
+    __shared__ float2 part[32];
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;
+    for (int p = threadIdx.x; p < len; p += blockDim.x) {
+        const float2 v = h[p];
+        dot2_add(v.x, v.x, s0, c0);
+        dot2_add(v.y, v.y, s1, c1);
+    }
+    float s, e;
+    two_sum(s0, s1, s, e);
+    float c = (c0 + c1) + e;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float rs = __shfl_xor_sync(KZ_FULL, s, o), rc = __shfl_xor_sync(KZ_FULL, c, o);
+        float t;
+        two_sum(s, rs, s, t);
+        c = (c + rc) + t;
+    }
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = make_float2(s, c);
+    __syncthreads();
+    double out = 0.0;
+    if (threadIdx.x == 0) {
+        float hi = 0.f, lo = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+            float t;
+            two_sum(hi, part[w].x, hi, t);
+            lo += part[w].y + t;
+        }
+        out = (double)hi + (double)lo;
+    }
+    return out;  // valid in thread 0
+}
+
 __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows,
                                  const int* __restrict__ rptr, double* out_d, float* out_f) {
-    __shared__ double part[32];
     const int k = blockIdx.x;
-    const int4 rd = rows[k];
-    const int base = rptr[k];
-    double a = 0.0;
-    for (int p = threadIdx.x; p < rd.y; p += blockDim.x) {
-        const float2 h = Hc[base + p];
-        a += (double)h.x * h.x + (double)h.y * h.y;
-    }
-    a = warp_sum_d(a);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
-    __syncthreads();
+    const double t = row_norm2(Hc + rptr[k], rows[k].y);
     if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
         out_d[k] = t;
         out_f[k] = (float)t;
     }
@@ -70,7 +95,8 @@ __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __re
 // second word), the lanes' (sum, error) pairs are combined with compensated
 // additions, and the result is rounded once: about as accurate as an FP64
 // sum, on the FP32 units (GB300's FP64 rate is a small fraction of FP32).
-// One block per row, one warp per entry.
+// One block per row, one warp per entry of the upper half (l >= k); the
+// lower half is the conjugate of the upper (G is Hermitian).
 __device__ __forceinline__ void dot2_add(float a, float b, float& s, float& c) {
     const float p = a * b;
     const float pe = fmaf(a, b, -p);  // a b = p + pe exactly
@@ -79,43 +105,105 @@ __device__ __forceinline__ void dot2_add(float a, float b, float& s, float& c) {
     c += pe + e;
 }
 
-__global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows, const int* __restrict__ rptr,
-                            const int* __restrict__ xptr, const int* __restrict__ xidx, float2* __restrict__ G) {
-    const int k = blockIdx.x;
+// One entry: sum over [lo, hi) of a[n] conj(b[n]) by one warp, four
+// independent Dot2 chains (re re, im im, im re, -re im) with two elements in
+// flight per lane; the value is returned in every lane.
+__device__ __forceinline__ float2 overlap_entry(const float2* __restrict__ hk, const float2* __restrict__ hl, int lo,
+                                                int hi) {
+    const int lane = threadIdx.x & 31;
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f, s2 = 0.f, c2 = 0.f, s3 = 0.f, c3 = 0.f;
+    int n = lo + lane;
+    for (; n + 32 < hi; n += 64) {
+        const float2 a0 = hk[n], b0 = hl[n], a1 = hk[n + 32], b1 = hl[n + 32];
+        dot2_add(a0.x, b0.x, s0, c0);
+        dot2_add(a0.y, b0.y, s1, c1);
+        dot2_add(a0.y, b0.x, s2, c2);
+        dot2_add(-a0.x, b0.y, s3, c3);
+        dot2_add(a1.x, b1.x, s0, c0);
+        dot2_add(a1.y, b1.y, s1, c1);
+        dot2_add(a1.y, b1.x, s2, c2);
+        dot2_add(-a1.x, b1.y, s3, c3);
+    }
+    if (n < hi) {
+        const float2 a0 = hk[n], b0 = hl[n];
+        dot2_add(a0.x, b0.x, s0, c0);
+        dot2_add(a0.y, b0.y, s1, c1);
+        dot2_add(a0.y, b0.x, s2, c2);
+        dot2_add(-a0.x, b0.y, s3, c3);
+    }
+    float sx, sy, ex, ey;
+    two_sum(s0, s1, sx, ex);
+    two_sum(s2, s3, sy, ey);
+    float cx = (c0 + c1) + ex, cy = (c2 + c3) + ey;
+    for (int o = 16; o > 0; o >>= 1) {
+        const float rsx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
+        const float rsy = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
+        float t;
+        two_sum(sx, rsx, sx, t);
+        cx = (cx + rcx) + t;
+        two_sum(sy, rsy, sy, t);
+        cy = (cy + rcy) + t;
+    }
+    return make_float2(sx + cx, sy + cy);
+}
+
+// Row k's entries G_kl for l >= k (G is Hermitian: the others are mirrored
+// by gram_mirror), one warp per entry.
+__device__ __forceinline__ void gram_row_upper(const float2* __restrict__ Hc, const int4* __restrict__ rows,
+                                               const int* __restrict__ rptr, const int* __restrict__ xptr,
+                                               const int* __restrict__ xidx, float2* __restrict__ G, int k) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int4 rk = rows[k];
     const float2* hk = Hc + rptr[k] - rk.x;
-    for (int e = xptr[k] + warp; e < xptr[k + 1]; e += nw) {
+    const int e0 = xptr[k], e1 = xptr[k + 1];
+    // first entry with l >= k (xidx is sorted and holds k)
+    int lo = e0, hi = e1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (xidx[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    for (int e = lo + warp; e < e1; e += nw) {
         const int l = xidx[e];
         const int4 rl = rows[l];
         const float2* hl = Hc + rptr[l] - rl.x;
-        const int lo = max(rk.z, rl.z), hi = min(rk.w, rl.w);
-        float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;  // a conj(b) = (ax bx + ay by) + i (ay bx - ax by)
-        for (int n = lo + lane; n < hi; n += 32) {
-            const float2 a = hk[n], b = hl[n];
-            dot2_add(a.x, b.x, sx, cx);
-            dot2_add(a.y, b.y, sx, cx);
-            dot2_add(a.y, b.x, sy, cy);
-            dot2_add(-a.x, b.y, sy, cy);
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-            const float rsx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
-            const float rsy = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
-            float t;
-            two_sum(sx, rsx, sx, t);
-            cx = (cx + rcx) + t;
-            two_sum(sy, rsy, sy, t);
-            cy = (cy + rcy) + t;
-        }
-        if (lane == 0) G[e] = make_float2(sx + cx, sy + cy);
+        const float2 v = overlap_entry(hk, hl, max(rk.z, rl.z), min(rk.w, rl.w));
+        if (lane == 0) G[e] = v;
     }
+}
+
+// Row k's entries G_kl for l < k: conj(G_lk), found by binary search in X_l.
+__device__ __forceinline__ void gram_row_mirror(const int* __restrict__ xptr, const int* __restrict__ xidx,
+                                                float2* __restrict__ G, int k) {
+    for (int e = xptr[k] + threadIdx.x; e < xptr[k + 1]; e += blockDim.x) {
+        const int l = xidx[e];
+        if (l >= k) break;
+        int lo = xptr[l], hi = xptr[l + 1];
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (xidx[mid] < k) lo = mid + 1;
+            else hi = mid;
+        }
+        const float2 v = G[lo];
+        G[e] = make_float2(v.x, -v.y);
+    }
+}
+
+__global__ void gram_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows, const int* __restrict__ rptr,
+                            const int* __restrict__ xptr, const int* __restrict__ xidx, float2* __restrict__ G) {
+    gram_row_upper(Hc, rows, rptr, xptr, xidx, G, blockIdx.x);
+}
+
+__global__ void gram_mirror_kernel(const int* __restrict__ xptr, const int* __restrict__ xidx, float2* __restrict__ G) {
+    gram_row_mirror(xptr, xidx, G, blockIdx.x);
 }
 
 // Batched set-up (kz_batch_update): block i handles row rowmap[i].y of item
 // rowmap[i].x of the instance table, whose packed channel starts at
 // H_cat + hoff[item].  phase 0 packs the row (as pack_rows_kernel), phase 1
 // forms its norm (as row_norms_kernel), phase 2 its inner products with the
-// overlapping rows (as gram_kernel); the phases are separate launches.
+// overlapping rows of higher index (as gram_kernel), phase 3 mirrors the
+// others (as gram_mirror_kernel); the phases are separate launches.
 __global__ void batch_update_kernel(const KzInst* __restrict__ insts, const int2* __restrict__ rowmap,
                                     const long long* __restrict__ hoff, const float2* __restrict__ H_cat, int phase) {
     const int2 ir = rowmap[blockIdx.x];
@@ -133,49 +221,15 @@ __global__ void batch_update_kernel(const KzInst* __restrict__ insts, const int2
             if (Hb) Hb[p] = __float22bfloat162_rn(h);
         }
     } else if (phase == 1) {
-        __shared__ double part[32];
-        const float2* hk = I.Hc + I.rptr[k];
-        double a = 0.0;
-        for (int p = threadIdx.x; p < rd.y; p += blockDim.x) {
-            const float2 h = hk[p];
-            a += (double)h.x * h.x + (double)h.y * h.y;
-        }
-        a = warp_sum_d(a);
-        if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = a;
-        __syncthreads();
+        const double t = row_norm2(I.Hc + I.rptr[k], rd.y);
         if (threadIdx.x == 0) {
-            double t = 0.0;
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
             const_cast<double*>(I.nrmd)[k] = t;
             const_cast<float*>(I.nrm)[k] = (float)t;
         }
+    } else if (phase == 2) {
+        gram_row_upper(I.Hc, I.rows, I.rptr, I.xptr, I.xidx, const_cast<float2*>(I.G), k);
     } else {
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-        const float2* hk = I.Hc + I.rptr[k] - rd.x;
-        for (int e = I.xptr[k] + warp; e < I.xptr[k + 1]; e += nw) {
-            const int l = I.xidx[e];
-            const int4 rl = I.rows[l];
-            const float2* hl = I.Hc + I.rptr[l] - rl.x;
-            const int lo = max(rd.z, rl.z), hi = min(rd.w, rl.w);
-            float sx = 0.f, cx = 0.f, sy = 0.f, cy = 0.f;
-            for (int n = lo + lane; n < hi; n += 32) {
-                const float2 a = hk[n], b = hl[n];
-                dot2_add(a.x, b.x, sx, cx);
-                dot2_add(a.y, b.y, sx, cx);
-                dot2_add(a.y, b.x, sy, cy);
-                dot2_add(-a.x, b.y, sy, cy);
-            }
-            for (int o = 16; o > 0; o >>= 1) {
-                const float rsx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
-                const float rsy = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
-                float t;
-                two_sum(sx, rsx, sx, t);
-                cx = (cx + rcx) + t;
-                two_sum(sy, rsy, sy, t);
-                cy = (cy + rcy) + t;
-            }
-            if (lane == 0) const_cast<float2*>(I.G)[e] = make_float2(sx + cx, sy + cy);
-        }
+        gram_row_mirror(I.xptr, I.xidx, const_cast<float2*>(I.G), k);
     }
 }
 
@@ -675,13 +729,16 @@ cudaError_t kz_coupling(const KzInst* insts, int n, float* mu, cudaStream_t st) 
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st) {
     gram_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, xptr, xidx, G);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    gram_mirror_kernel<<<K, 128, 0, st>>>(xptr, xidx, G);
     return cudaGetLastError();
 }
 
 cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nrows, const long long* hoff,
                                  const float2* H_cat, cudaStream_t st) {
-    for (int phase = 0; phase < 3; ++phase) {
-        batch_update_kernel<<<nrows, 256, 0, st>>>(insts, rowmap, hoff, H_cat, phase);
+    for (int phase = 0; phase < 4; ++phase) {
+        batch_update_kernel<<<nrows, phase == 3 ? 128 : 256, 0, st>>>(insts, rowmap, hoff, H_cat, phase);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

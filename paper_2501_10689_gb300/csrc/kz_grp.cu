@@ -160,9 +160,12 @@ __global__ void grp_fill_kernel(KzGrpChan C, const float2* __restrict__ Hc, cons
 
 // ---------------------------------------------------------------------------
 // Group synchronisation.  Cluster: hardware barrier with release / acquire.
-// Grid: a monotone arrival counter (every CTA of the cooperative launch),
-// polled with acquire loads for at most WAIT_NS; a timeout raises the status
-// bit and the abort flag, which every CTA reads right after each barrier.
+// Grid: a monotone arrival counter per group (the group's AB CTAs of the
+// cooperative launch; the groups decide their refreshes and their end on
+// their own columns, so they take different numbers of barriers), polled
+// with acquire loads for at most WAIT_NS; a timeout raises the status bit and
+// the group's abort flag, which every CTA of the group reads right after each
+// barrier.
 __device__ __forceinline__ void flag(int* status, int bit) {
     if (status) atomicOr(status, bit);
 }
@@ -180,12 +183,13 @@ __device__ __forceinline__ void group_sync(const KzGrpLaunch& L, unsigned& gen, 
     } else {
         __syncthreads();
         if (threadIdx.x == 0) {
+            unsigned* counter = L.gbar + blockIdx.y;  // this group's arrivals
             __threadfence();
-            atomicAdd(L.gbar, 1u);
+            atomicAdd(counter, 1u);
             const unsigned target = gen * nctas;
             const unsigned long long t0 = gtimer();
             long i = 0;
-            while (kz5::ld_acquire_gpu(L.gbar) < target) {
+            while (kz5::ld_acquire_gpu(counter) < target) {
                 __nanosleep(32);
                 if ((++i & 255) == 0 && gtimer() - t0 > WAIT_NS) {
                     flag(L.status, KZ_STATUS_BIT_TIMEOUT);
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     const int AB = C.AB, K = C.K, Nt = C.Nt, NC = L.NC;
     const int col0 = g * NC;
     const int ncols = min(NC, L.nrhs - col0);
-    const unsigned nctas = gridDim.x * gridDim.y;
+    const unsigned nctas = gridDim.x;  // CTAs of one group
     const int fmt = L.fmt;
     const bool oahk = (L.algo == KZ_VR_OAHK);
     const float xi = L.xi;
@@ -249,7 +253,7 @@ __global__ void __launch_bounds__(GT, 1) kz_grp_kernel(const KzGrpLaunch L) {
     const uint32_t P0 = 0, U0 = (uint32_t)(L.rtmax * 2 * NC), M0 = U0 + 2 * NC;
     const uint32_t idP = kz5::idesc_f16(128, NC, fmt, 0, 1, 0), idPn = kz5::idesc_f16(128, NC, fmt, 0, 1, 1);
     const uint32_t idU = kz5::idesc_f16(128, NC, fmt, 1, 1, 0), idUn = kz5::idesc_f16(128, NC, fmt, 1, 1, 1);
-    unsigned* abort_word = L.gbar + 1 + (CLUSTER ? g : 0);
+    unsigned* abort_word = L.gbar + L.CG + g;
     unsigned gen = 0;
     uint32_t mma_par = 0;
     bool mma_late = false;

@@ -202,7 +202,7 @@ struct KzGrpLaunch {
     uint16_t* Phi;          // [CG][K][2][NC] 16-bit phi / tau
     float2* Qg;             // [CG][K][NC] q at the last refresh
     float* colpart;         // [CG][7][AB][NC] per-CTA column partials
-    unsigned* gbar;         // [0] grid barrier counter (0), [1 + g] abort epochs (0xffffffff)
+    unsigned* gbar;         // [g] group g's grid barrier counter (0), [CG + g] its abort epoch (0xffffffff)
     int rpc, rtmax, tmem_cols;
 };
 
