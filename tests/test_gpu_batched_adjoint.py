@@ -42,7 +42,7 @@ def test_plan_update_matches_fresh_plan(kp):
     # the Bai-Wu sum of GRK reads the updated norms on the device
     out = kp.precode(plan, kp.rhs_tensor(b.S), b.xi, algo="grk", tol=1e-6, max_iter=40000)
     assert out["converged"]
-    assert np.all(orz.rel_err(out["x"].cpu().numpy().T.astype(np.complex128), X) <= 1e-4)
+    assert np.all(orz.rel_err(out["x"].cpu().numpy().T.astype(np.complex128), X) <= TOL_X)
 
 
 def test_plan_update_rejects_bad_input(kp):
@@ -191,8 +191,8 @@ def test_batched_autograd_vs_fp64(kp):
         for c, inst in enumerate(insts):
             L_ref, gH_ref, gxi_ref = oadj.reference_gradient(inst, snr)
             seg = gH[int(pre.h_off[c]):int(pre.h_off[c + 1])]
-            assert np.linalg.norm(seg - gH_ref) <= 1e-3 * np.linalg.norm(gH_ref)
-            assert abs(float(xi.grad[c].item()) - gxi_ref) <= 1e-3 * abs(gxi_ref)
+            assert np.linalg.norm(seg - gH_ref) <= 1e-4 * np.linalg.norm(gH_ref)
+            assert abs(float(xi.grad[c].item()) - gxi_ref) <= 1e-4 * abs(gxi_ref)
         L_tot = sum(oadj.reference_gradient(i, snr)[0] for i in insts)
         assert abs(float(L.item()) - L_tot) <= 1e-5 * abs(L_tot)
 
