@@ -611,7 +611,7 @@ def run_configs(args):
     S = kp.rhs_tensor(inst.S, device=dev)
     for algo in (("rk_energy", "grk", "vr_ogrk", "gk", "ahk", "vr_oahk") if "config1" in only else ()):
         T1, T2 = (1000, 5000) if algo == "rk_energy" else (50, 250)
-        for kernel in ("auto", "small"):
+        for kernel in ("resident", "small"):  # auto picks the small-channel kernel here
             max_iter = 100000 if algo == "rk_energy" else 4000
             out = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=max_iter, kernel=kernel)
             err = float(oracle.rzf.rel_err(out["x"].cpu().numpy().T, X)[0])

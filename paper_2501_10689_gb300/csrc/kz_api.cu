@@ -892,6 +892,12 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         kz_set_error("kz_precode_ex: the tensor-core kernel runs AHK / VR_OAHK on C64 plans");
         return KZ_ERR_UNSUPPORTED;
     }
+    // AUTO on a small channel with at most one column per SM and no fixed
+    // column count per CTA: the small-channel kernel (3-4x less time per
+    // iteration than RESIDENT on 16 users and 256 antennas)
+    if (kernel == KZ_KERNEL_AUTO && rhs_per_cta == 0 && prec == KZ_C64 && plan->K <= 32 && plan->Ntp <= 512 &&
+        !hist_row && nrhs <= plan->sms && kz_smem_small(plan->K, plan->Ntp) <= kSmemLimit)
+        kernel = KZ_KERNEL_SMALL;
     if (kernel == KZ_KERNEL_SMALL) {
         if (prec != KZ_C64 || plan->K > 32 || plan->Ntp > 512 || hist_row) {
             kz_set_error("kz_precode_ex: the small-channel kernel needs a C64 plan with K <= 32 and Nt <= 511");
