@@ -184,8 +184,7 @@ __device__ __forceinline__ void group_sync(const KzGrpLaunch& L, unsigned& gen, 
         __syncthreads();
         if (threadIdx.x == 0) {
             unsigned* counter = L.gbar + blockIdx.y;  // this group's arrivals
-            __threadfence();
-            atomicAdd(counter, 1u);
+            kz5::red_release_gpu_add(counter, 1u);  // publishes the CTA's writes (ordered by the barrier above)
             const unsigned target = gen * nctas;
             const unsigned long long t0 = gtimer();
             long i = 0;
@@ -197,7 +196,8 @@ __device__ __forceinline__ void group_sync(const KzGrpLaunch& L, unsigned& gen, 
                     break;
                 }
             }
-            __threadfence();
+            // the acquire load that saw every arrival orders this CTA's later
+            // reads (through the barrier below) after the other CTAs' writes
         }
         __syncthreads();
     }
