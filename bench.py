@@ -427,6 +427,8 @@ def run_ours(args):
     except Exception:
         hbm_peak, peak_src = 6800.0, "fallback"
     achieved_gbs = alg_bytes / (ms_per_step / 1000.0) / 1e9
+    h_bytes = float(np.sum(col_iters * (2.0 * sumL * 8.0 / NRHS)[:, None]))
+    h_gbs = h_bytes / (ms_per_step / 1000.0) / 1e9
     achieved_tflops = alg_flops / (ms_per_step / 1000.0) / 1e12
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x clock under load
@@ -446,7 +448,13 @@ def run_ours(args):
                            "J = 4 launch only for channels whose J iterate columns do not fit)" if tc
                            else "kz_ahk_kernel (batched VR-OAHK)"),
                 "alu_view": {"achieved_tflops": achieved_tflops, "fp32_fma_peak_tflops": alu_peak,
-                             "frac": achieved_tflops / alu_peak}}
+                             "frac": achieved_tflops / alu_peak},
+                # the channel's bytes alone (2 sumL 8 / 16 per column-iteration;
+                # the iterate term of the bytes above stays in shared memory)
+                "h_bytes_view": {"achieved": h_gbs, "unit": "GB/s", "frac": h_gbs / hbm_peak},
+                # what DRAM actually moved per launch (ncu), over the step time
+                "dram_view": ({"achieved": traffic / (ms_per_step / 1000.0) / 1e9, "unit": "GB/s",
+                               "frac": traffic / (ms_per_step / 1000.0) / 1e9 / hbm_peak} if traffic else None)}
     if tc and "bf16_tflops" in peaks:
         tf32_peak = float(peaks["bf16_tflops"]) / 2.0  # dense TF32 runs at half the BF16 rate
         roofline["tensor_view"] = {"achieved_tflops": achieved_tflops, "tf32_peak_tflops": tf32_peak,
