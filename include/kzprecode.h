@@ -288,6 +288,17 @@ kz_status kz_batch_rebind(kz_batch* batch, const kz_batch_item* items, void* str
  * (KZ_ERR_INVALID_ARG otherwise).  The batch's queue order is kept. */
 kz_status kz_batch_update(kz_batch* batch, const kz_cf32* H_cat, void* stream);
 
+/* kz_batch_update for the items [first, first + count) only (step A0 for
+ * part of a batch): H_cat has the layout of kz_batch_update (all items'
+ * packed channels in item order), but only the range's channels are read, so
+ * a caller can upload the channels of later items while the set-up of
+ * earlier ones runs (the launches of one range go to `stream`).  The items
+ * must name distinct plans; an empty or out-of-range item range returns
+ * KZ_ERR_INVALID_ARG.  Asynchronous on `stream` (the first call of either
+ * form uploads the batch's row table, synchronously). */
+kz_status kz_batch_update_items(kz_batch* batch, const kz_cf32* H_cat, int32_t first, int32_t count,
+                                void* stream);
+
 /* Run a prepared batch: one kernel launch after an 8-byte memset of the
  * queue counters (two launches, the second on a stream forked from `stream`
  * and joined back, when a tensor-core batch holds channels whose columns per

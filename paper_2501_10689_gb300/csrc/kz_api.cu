@@ -162,6 +162,7 @@ struct kz_batch {
     int2* d_rowmap = nullptr;    // kz_batch_update: {item, row} of every row of every item
     long long* d_hoff = nullptr; // kz_batch_update: item b's offset in the concatenated channels
     int n_rows = 0;
+    std::vector<int> row_start;  // kz_batch_update: first rowmap entry of every item (n + 1)
     bool all_v = true;           // every item has a v buffer
     bool gk = false;             // prepared as KZ_GK: GRK with the argmax rule
     std::vector<const kz_plan*> plans;  // the items' plans, fixed at preparation
@@ -1416,16 +1417,21 @@ kz_status kz_batch_set_launch(kz_batch* B, kz_kernel kernel, int32_t rhs_per_cta
     return check_launch(e, "kz_batch_set_launch");
 }
 
-kz_status kz_batch_update(kz_batch* B, const kz_cf32* H_cat, void* stream) {
+static kz_status batch_update_range(kz_batch* B, const kz_cf32* H_cat, int first, int count, void* stream,
+                                    const char* fn) {
     g_err.clear();
     if (!B || !H_cat || !aligned(H_cat, 8)) {
-        kz_set_error("kz_batch_update: need a batch and an 8-byte aligned H_cat");
+        kz_set_error("%s: need a batch and an 8-byte aligned H_cat", fn);
+        return KZ_ERR_INVALID_ARG;
+    }
+    if (first < 0 || count < 1 || first > B->n - count) {
+        kz_set_error("%s: items [%d, %d) are not within the batch's %d items", fn, first, first + count, B->n);
         return KZ_ERR_INVALID_ARG;
     }
     for (int b = 0; b < B->n; ++b)
         for (int c = 0; c < b; ++c)
             if (B->plans[b] == B->plans[c]) {
-                kz_set_error("kz_batch_update: items %d and %d name the same plan", c, b);
+                kz_set_error("%s: items %d and %d name the same plan", fn, c, b);
                 return KZ_ERR_INVALID_ARG;
             }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1433,12 +1439,15 @@ kz_status kz_batch_update(kz_batch* B, const kz_cf32* H_cat, void* stream) {
     if (!B->d_rowmap) {
         std::vector<int2> rm;
         std::vector<long long> hoff(B->n);
+        std::vector<int> rs(B->n + 1, 0);
         long long acc = 0;
         for (int b = 0; b < B->n; ++b) {
             hoff[b] = acc;
             acc += B->plans[b]->sumL;
+            rs[b] = (int)rm.size();
             for (int k = 0; k < B->plans[b]->K; ++k) rm.push_back(make_int2(b, k));
         }
+        rs[B->n] = (int)rm.size();
         e = upload(&B->d_rowmap, rm, st);
         if (e == cudaSuccess) e = upload(&B->d_hoff, hoff, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host vectors go out of scope
@@ -1447,24 +1456,32 @@ kz_status kz_batch_update(kz_batch* B, const kz_cf32* H_cat, void* stream) {
             if (B->d_hoff) cudaFree(B->d_hoff);
             B->d_rowmap = nullptr;
             B->d_hoff = nullptr;
-            return check_launch(e, "kz_batch_update set-up");
+            return check_launch(e, fn);
         }
         B->n_rows = (int)rm.size();
+        B->row_start = rs;
     }
-    e = kz_batch_update_rows(B->d_insts, B->d_rowmap, B->n_rows, B->d_hoff, reinterpret_cast<const float2*>(H_cat), st);
-    if (e != cudaSuccess) return check_launch(e, "kz_batch_update");
-    long long off = 0;
-    for (int b = 0; b < B->n; ++b) {  // a plan that also serves the group kernel keeps its tiles current
+    const int r0 = B->row_start[first], r1 = B->row_start[first + count];
+    e = kz_batch_update_rows(B->d_insts, B->d_rowmap, r0, r1 - r0, B->d_hoff, reinterpret_cast<const float2*>(H_cat),
+                             st);
+    if (e != cudaSuccess) return check_launch(e, fn);
+    for (int b = first; b < first + count; ++b) {  // a plan that also serves the group kernel keeps its tiles current
         kz_plan* P = const_cast<kz_plan*>(B->plans[b]);
         if (P->grp.built) {
             e = kz_grp_prepare(grp_chan(P), P->d_Hc, P->total2, P->d_rows, P->d_rptr, P->d_nrm, P->grp.d_stat,
                                P->grp.fmt, st);
-            if (e != cudaSuccess) return check_launch(e, "kz_batch_update");
+            if (e != cudaSuccess) return check_launch(e, fn);
         }
-        off += P->sumL;
     }
-    (void)off;
     return KZ_OK;
+}
+
+kz_status kz_batch_update(kz_batch* B, const kz_cf32* H_cat, void* stream) {
+    return batch_update_range(B, H_cat, 0, B ? B->n : 0, stream, "kz_batch_update");
+}
+
+kz_status kz_batch_update_items(kz_batch* B, const kz_cf32* H_cat, int32_t first, int32_t count, void* stream) {
+    return batch_update_range(B, H_cat, first, count, stream, "kz_batch_update_items");
 }
 
 kz_status kz_precode_adjoint_batched(kz_batch* B, const kz_adjoint_item* items, double tol, int32_t max_iter,

@@ -205,8 +205,9 @@ __global__ void gram_mirror_kernel(const int* __restrict__ xptr, const int* __re
 // overlapping rows of higher index (as gram_kernel), phase 3 mirrors the
 // others (as gram_mirror_kernel); the phases are separate launches.
 __global__ void batch_update_kernel(const KzInst* __restrict__ insts, const int2* __restrict__ rowmap,
-                                    const long long* __restrict__ hoff, const float2* __restrict__ H_cat, int phase) {
-    const int2 ir = rowmap[blockIdx.x];
+                                    const long long* __restrict__ hoff, const float2* __restrict__ H_cat, int row0,
+                                    int phase) {
+    const int2 ir = rowmap[row0 + blockIdx.x];
     const KzInst& I = insts[ir.x];
     const int k = ir.y;
     const int4 rd = I.rows[k];  // {a, len2, o, e}
@@ -735,10 +736,11 @@ cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const i
     return cudaGetLastError();
 }
 
-cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nrows, const long long* hoff,
+cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int row0, int nrows, const long long* hoff,
                                  const float2* H_cat, cudaStream_t st) {
+    if (nrows <= 0) return cudaSuccess;
     for (int phase = 0; phase < 4; ++phase) {
-        batch_update_kernel<<<nrows, phase == 3 ? 128 : 256, 0, st>>>(insts, rowmap, hoff, H_cat, phase);
+        batch_update_kernel<<<nrows, phase == 3 ? 128 : 256, 0, st>>>(insts, rowmap, hoff, H_cat, row0, phase);
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }

@@ -111,10 +111,11 @@ cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, in
                          float* out_f, cudaStream_t st);
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st);
-// Re-pack every item of a batch from H_cat (item b's packed channel at
-// H_cat + hoff[b]): packing, row norms and inner products of overlapping rows,
-// one launch each over all (item, row) pairs of rowmap.
-cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int nrows, const long long* hoff,
+// Re-pack items of a batch from H_cat (item b's packed channel at
+// H_cat + hoff[b]): packing, row norms and inner products of overlapping rows
+// (upper half, then the mirror), one launch each over the (item, row) pairs
+// rowmap[row0, row0 + nrows).
+cudaError_t kz_batch_update_rows(const KzInst* insts, const int2* rowmap, int row0, int nrows, const long long* hoff,
                                  const float2* H_cat, cudaStream_t st);
 // Subarray-wise precoder F = H^H V over S subarrays (Q_s in CSR qptr / qidx);
 // with beta non-NULL, F is scaled by beta = 1 / ||F||_F (part: S x ceil(ncols / 32) doubles).

@@ -49,7 +49,7 @@ class KzBatchItem(ctypes.Structure):
 EXPORTS = ("kz_plan_create", "kz_plan_dense", "kz_plan_update", "kz_plan_destroy", "kz_plan_query", "kz_precode", "kz_precode_ex",
            "kz_batch_prepare", "kz_precode_batched", "kz_batch_destroy", "kz_batch_tune", "kz_batch_set_launch",
            "kz_batch_query",
-           "kz_batch_rebind", "kz_batch_update", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
+           "kz_batch_rebind", "kz_batch_update", "kz_batch_update_items", "kz_precode_adjoint", "kz_precode_adjoint_batched", "kz_precode_adjoint_noalloc",
            "kz_precode_record", "kz_unrolled_adjoint", "kz_precoder_matrix", "kz_plan_flops", "kz_sum_rate", "kz_sum_rate_batched", "kz_last_error", "kz_version")
 KERNELS = {"auto": 0, "resident": 1, "tc": 3, "group": 4, "small": 5}
 
@@ -89,6 +89,8 @@ def load():
     lib.kz_batch_rebind.restype = I32
     lib.kz_batch_update.argtypes = [P, P, P]
     lib.kz_batch_update.restype = I32
+    lib.kz_batch_update_items.argtypes = [P, P, I32, I32, P]
+    lib.kz_batch_update_items.restype = I32
     lib.kz_plan_update.argtypes = [P, P, P]
     lib.kz_plan_update.restype = I32
     lib.kz_precode_adjoint_batched.argtypes = [P, P, F64, I32, P, P]
@@ -298,6 +300,15 @@ def kz_batch_update(batch: Batch, H_cat, stream=None):
     n = sum(it["plan"].sum_len for it in batch.keep)
     _check_c64(H_cat, (n,), "H_cat")
     return _check(lib.kz_batch_update(batch.handle, _ptr(H_cat), _stream(stream)))
+
+
+def kz_batch_update_items(batch: Batch, H_cat, first, count, stream=None):
+    """kz_batch_update for items [first, first + count): H_cat holds every
+    item's packed channel in item order; only the range's are read."""
+    lib = load()
+    n = sum(it["plan"].sum_len for it in batch.keep)
+    _check_c64(H_cat, (n,), "H_cat")
+    return _check(lib.kz_batch_update_items(batch.handle, _ptr(H_cat), int(first), int(count), _stream(stream)))
 
 
 def kz_precode_batched(batch: Batch, sel, tol, max_iter, seed, refresh=0, status=None, stream=None):

@@ -204,6 +204,47 @@ def test_backward_raises_on_nan_gradient(kp):
 
 
 # ---------------------------------------------------------------- batched channel update
+def test_batch_update_items_in_ranges_equals_whole_update(kp):
+    """kz_batch_update_items over three item ranges, each reading only its
+    own channels from a buffer filled range by range, leaves the plans
+    exactly as one kz_batch_update does (bit-identical solutions)."""
+    rng = np.random.default_rng(6)
+    insts = [kzgen.make_instance(800 + i, int(rng.integers(4, 30)), int(rng.choice([97, 256, 640])),
+                                 vr_frac_range=(0.1, 0.4), nrhs=4) for i in range(7)]
+    new = [kzgen.make_instance(900 + i, inst.K, inst.Nt, vr_override=(inst.vr_offset, inst.vr_len), nrhs=4)
+           for i, inst in enumerate(insts)]
+
+    def batch_for():
+        items = [dict(plan=kp.plan_from_instance(i), s=kp.rhs_tensor(n.S),
+                      x=torch.zeros((4, i.Nt), dtype=torch.complex64, device="cuda"),
+                      v=torch.zeros((4, i.K), dtype=torch.complex64, device="cuda"),
+                      iters=torch.zeros(4, dtype=torch.int32, device="cuda"),
+                      resid=torch.zeros(4, dtype=torch.float64, device="cuda"), xi=n.xi) for i, n in zip(insts, new)]
+        return items, kp.kz_batch_prepare(items, 4, "vr_oahk")
+
+    H_new = np.concatenate([i.H_packed for i in new])
+    items_a, b_a = batch_for()
+    kp.kz_batch_update(b_a, torch.from_numpy(H_new).cuda())
+    items_b, b_b = batch_for()
+    H_b = torch.full((H_new.size,), complex(float("nan"), 0.0), dtype=torch.complex64, device="cuda")
+    off = np.concatenate([[0], np.cumsum([i.vr_len.sum() for i in new])])
+    for first, count in ((0, 2), (2, 4), (6, 1)):  # each range's channels arrive just before its update
+        a, b = int(off[first]), int(off[first + count])
+        H_b[a:b] = torch.from_numpy(H_new[a:b]).cuda()
+        kp.kz_batch_update_items(b_b, H_b, first, count)
+    for b in (b_a, b_b):
+        kp.kz_precode_batched(b, "paper", 1e-7, 3000, 0)
+    torch.cuda.synchronize()
+    for ia, ib, n in zip(items_a, items_b, new):
+        assert torch.equal(ia["x"], ib["x"]) and torch.equal(ia["iters"], ib["iters"])
+        V, X = orz.rzf(n.dense(), n.xi, n.S)
+        assert np.all(orz.rel_err(ib["x"].cpu().numpy().T, X) <= TOL_X)
+    with pytest.raises(kp.KzError):
+        kp.kz_batch_update_items(b_b, H_b, 5, 3)
+    with pytest.raises(kp.KzError):
+        kp.kz_batch_update_items(b_b, H_b, 0, 0)
+
+
 def test_batch_update_matches_fresh_plans(kp):
     """kz_batch_update with a new channel for every item gives bit-identical
     solutions to a batch prepared from plans built on that channel."""
