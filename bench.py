@@ -679,7 +679,7 @@ def run_configs(args):
     for inst in ([kzgen.config4()] if "config4" in only else []):
         V, X = oracle.rzf.rzf(inst.dense(), inst.xi, inst.S)
         S = kp.rhs_tensor(inst.S, device=dev)
-        for prec, kernel in (("bf16", "auto"), ("c64", "auto"), ("c64", "tc"), ("c64", "group"), ("bf16", "group")):
+        for prec, kernel in (("bf16", "resident"), ("c64", "resident"), ("c64", "tc"), ("c64", "group"), ("bf16", "group")):
             plan = kp.plan_from_instance(inst, prec=prec, device=dev)
             try:
                 out = kp.precode(plan, S, inst.xi, algo="vr_oahk", tol=1e-6, max_iter=3000, kernel=kernel)

@@ -119,9 +119,11 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * most 32 users and 511 antennas whose rows fit shared memory): one CTA of 8
  * warps per column with the whole state in shared memory and a few short
  * phases per step, for the latency of single small solves (rhs_per_cta 0
- * or 1).  AUTO for kz_precode: SMALL when it applies, rhs_per_cta is 0 and
- * nrhs is at most the GPU's SM count, else RESIDENT; the batch default is
- * RESIDENT until kz_batch_tune or kz_batch_set_launch chooses. */
+ * or 1).  AUTO for kz_precode (with rhs_per_cta 0): SMALL when it applies
+ * and nrhs is at most the GPU's SM count; GROUP for AHK / VR_OAHK on
+ * channels of 4096 antennas or more (RESIDENT if the group kernel cannot
+ * hold the channel); else RESIDENT.  The batch default is RESIDENT until
+ * kz_batch_tune or kz_batch_set_launch chooses. */
 typedef enum {
     KZ_KERNEL_AUTO = 0,
     KZ_KERNEL_RESIDENT = 1,

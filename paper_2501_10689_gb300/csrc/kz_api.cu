@@ -930,6 +930,15 @@ static kz_status precode_impl(kz_plan* plan, const kz_cf32* s, int32_t nrhs, flo
         return check_launch(kz_launch_small(L, nrhs, smem, static_cast<cudaStream_t>(stream)),
                             "kz_precode small-channel kernel");
     }
+    // AUTO on a large channel (4096 antennas or more) for AHK / VR-OAHK: the
+    // group kernel (measured 1.3-11x faster than RESIDENT from 4096 to 16384
+    // antennas, 16-256 columns); a channel it cannot hold falls back
+    if (kernel == KZ_KERNEL_AUTO && rhs_per_cta == 0 && is_ahk_family(algo) && !hist_row && plan->Ntp >= 4096) {
+        const kz_status rc = run_grp(plan, s, nrhs, xi, algo, tol, max_iter, x, v, iters, resid, status, 0, refresh,
+                                     static_cast<cudaStream_t>(stream));
+        if (rc != KZ_ERR_UNSUPPORTED) return rc;
+        g_err.clear();
+    }
     if (kernel == KZ_KERNEL_GROUP) {
         if (!is_ahk_family(algo)) {
             kz_set_error("kz_precode_ex: the group kernel runs AHK / VR_OAHK");
