@@ -96,3 +96,25 @@ def test_plan_flops_is_table1(kp):
         want = oflops.table1_flops(scheme, inst.K, inst.Nt, T=37.0, **stats)
         got = kp.kz_plan_flops(plan, {"swor_erk": "rk_swor"}.get(scheme, scheme), 20, 37.0)
         assert got == pytest.approx(want, rel=1e-12), scheme
+
+
+def test_auto_routes_small_and_large_channels(kp):
+    """KZ_KERNEL_AUTO in kz_precode: a small channel (16 users, 256 antennas,
+    few columns) runs on the small-channel kernel and a large one (4096
+    antennas, AHK family) on the group kernel: bit-identical to naming them;
+    a fixed column count per CTA keeps the resident kernel."""
+    small = kzgen.make_instance(31, 16, 256, vr_len_range=(64, 192), snr_db=10.0, nrhs=3)
+    large = kzgen.make_instance(32, 128, 4096, vr_len_range=(256, 1024), snr_db=10.0, nrhs=16)
+    for inst, algo, named in ((small, "grk", "small"), (small, "vr_oahk", "small"), (large, "vr_oahk", "group")):
+        plan = kp.plan_from_instance(inst)
+        S = kp.rhs_tensor(inst.S)
+        a = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=20000, kernel="auto")
+        b = kp.precode(plan, S, inst.xi, algo=algo, tol=1e-6, max_iter=20000, kernel=named)
+        assert torch.equal(a["x"], b["x"]) and torch.equal(a["iters"], b["iters"]), (algo, named)
+        V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+        assert np.all(orz.rel_err(a["x"].cpu().numpy().T, X) <= 1e-5)
+    plan = kp.plan_from_instance(small)
+    S = kp.rhs_tensor(small.S)
+    a = kp.precode(plan, S, small.xi, algo="vr_oahk", tol=1e-6, max_iter=20000, kernel="auto", rhs_per_cta=1)
+    b = kp.precode(plan, S, small.xi, algo="vr_oahk", tol=1e-6, max_iter=20000, kernel="resident", rhs_per_cta=1)
+    assert torch.equal(a["x"], b["x"])
