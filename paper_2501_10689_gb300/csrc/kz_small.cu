@@ -862,7 +862,11 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_reg_kernel(const __grid_const
             full = false;
             const float u = draw24(key, t);
             resid(mask);
-            float a = rnorm(allmask);
+            // the paper's rule draws from the running sum of |r_k|^2, whose
+            // total is ||r||^2: one scan serves the stopping test and the draw
+            const bool paper = L.sel == KZ_SEL_PAPER;
+            float incl = paper ? lane_scan(own ? a2 : 0.f) : 0.f;
+            float a = paper ? __shfl_sync(KZ_FULL, incl, 31) : rnorm(allmask);
             if (bad(a)) {
                 numeric = true;
                 break;
@@ -874,6 +878,7 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_reg_kernel(const __grid_const
                     break;
                 }
                 a = ac;
+                if (paper) incl = lane_scan(own ? a2 : 0.f);  // the confirmed residuals
             }
             if (t >= L.max_iter) break;
             const float w2 = own ? a2 : 0.f;
@@ -882,8 +887,8 @@ __global__ void __launch_bounds__(SNT, 1) kz_small_reg_kernel(const __grid_const
             if (L.sel == KZ_SEL_ARGMAX) {
                 float mx;
                 sel = lane_argmax_f(ratio, &mx);
-            } else if (L.sel == KZ_SEL_PAPER) {
-                sel = pick_scan(lane_scan(w2), w2, u);
+            } else if (paper) {
+                sel = pick_scan(incl, w2, u);
             } else {  // Bai-Wu
                 float mx;
                 (void)lane_argmax_f(ratio, &mx);
