@@ -163,3 +163,21 @@ def test_group_rejects_unsupported(kp):
         kp.precode(plan, S, inst.xi, algo="grk", kernel="group")
     with pytest.raises(kp.KzError):
         kp.precode(plan, S, inst.xi, algo="vr_oahk", kernel="group", rhs_per_cta=8)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_group_random_shapes(kp, seed):
+    """Random channels for the group kernel: antennas not a multiple of the
+    128-antenna block, columns not a multiple of the group width, users up to
+    a few hundred."""
+    rng = np.random.default_rng(3000 + seed)
+    Nt = int(rng.integers(300, 3000))
+    K = int(rng.integers(8, min(200, Nt // 4)))
+    nrhs = int(rng.integers(1, 70))
+    inst = kzgen.make_instance(4000 + seed, K, Nt, vr_frac_range=(0.05, 0.5), snr_db=float(rng.uniform(0, 20)),
+                               nrhs=nrhs)
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    for algo in ("vr_oahk", "ahk"):
+        out = run(kp, inst, algo, tol=1e-6, max_iter=3000)
+        assert out["converged"], (Nt, K, nrhs, algo, out["status"])
+        assert np.max(orz.rel_err(out["x"], X)) <= TOL_X, (Nt, K, nrhs, algo)

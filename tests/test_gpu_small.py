@@ -119,3 +119,22 @@ def test_small_rejects_large_channels(kp):
     plan = kp.plan_from_instance(inst)
     with pytest.raises(kp.KzError):
         kp.precode(plan, kp.rhs_tensor(inst.S), inst.xi, algo="grk", kernel="small")
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_small_random_shapes(kp, seed):
+    """Random channels within the kernel's limits (users 1-32, antennas
+    2-511, VRs from 1 antenna to the whole array): every method reaches the
+    FP64 RZF at 1e-5."""
+    rng = np.random.default_rng(1000 + seed)
+    K = int(rng.integers(1, 33))
+    Nt = int(rng.integers(K + 1, 512))
+    lo = int(rng.integers(1, max(2, Nt // 2)))
+    inst = kzgen.make_instance(2000 + seed, K, Nt, vr_len_range=(lo, Nt), snr_db=float(rng.uniform(0, 20)),
+                               nrhs=int(rng.integers(1, 5)))
+    V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+    for algo, sel in (("grk", "paper"), ("vr_ogrk", "argmax"), ("ahk", "paper"), ("vr_oahk", "paper"),
+                      ("rk_energy", "paper")):
+        out = run(kp, inst, algo, sel, tol=1e-6, max_iter=400000)
+        assert out["converged"], (K, Nt, algo, out["status"])
+        assert np.max(orz.rel_err(out["x"], X)) <= 1e-5, (K, Nt, algo)
