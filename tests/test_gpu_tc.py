@@ -281,3 +281,41 @@ def test_tc_scale_range(kp, c):
         st, it, _ = _one_item_batch(kp, inst, J, 512, 1e-6)
         assert st == 0
         _check_rzf(inst, it, 1e-6)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tc_random_batch(kp, seed):
+    """A random uneven batch (antennas 64-4600, users 2-256, VR fractions
+    5-60%, 1-20 columns, SNR 0-20 dB) under the tensor-core launches and the
+    tuner's choice: every column reaches the FP64 RZF at 1e-5."""
+    rng = np.random.default_rng(5000 + seed)
+    insts = []
+    for i in range(10):
+        Nt = int(rng.integers(64, 4600))
+        K = int(rng.integers(2, min(256, Nt // 2)))
+        insts.append(kzgen.make_instance(6000 + 10 * seed + i, K, Nt, vr_frac_range=(0.05, 0.6),
+                                         snr_db=float(rng.uniform(0, 20)), nrhs=NR))
+    for launch in (("tc", 8, 512), ("tc", 4, 256), None):
+        items = []
+        for inst in insts:
+            p = kp.plan_from_instance(inst)
+            items.append(dict(plan=p, s=kp.rhs_tensor(inst.S),
+                              x=torch.empty((NR, inst.Nt), dtype=torch.complex64, device="cuda"),
+                              v=torch.empty((NR, inst.K), dtype=torch.complex64, device="cuda"),
+                              iters=torch.empty(NR, dtype=torch.int32, device="cuda"),
+                              resid=torch.empty(NR, dtype=torch.float64, device="cuda"), xi=inst.xi))
+        b = kp.kz_batch_prepare(items, NR, "vr_oahk")
+        if launch:
+            kp.kz_batch_set_launch(b, *launch)
+        else:
+            kp.kz_batch_tune(b, "paper", 1e-6, 3000, 0)
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        kp.kz_precode_batched(b, "paper", 1e-6, 3000, 0, status=st)
+        torch.cuda.synchronize()
+        assert st.item() == 0, (launch, st.item())
+        for inst, it in zip(insts, items):
+            V, X = orz.rzf(inst.dense(), inst.xi, inst.S)
+            assert np.all(orz.rel_err(it["x"].cpu().numpy().T, X) <= TOL_X), (launch, inst.K, inst.Nt)
+
+
+NR = 13  # columns per channel in the random batches (not a multiple of the launch widths)
