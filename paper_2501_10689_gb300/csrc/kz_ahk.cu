@@ -145,6 +145,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         const int col0 = KZ_ITEM_COL(it.y), ncols = min(W, I.ld - col0);
         const float xi = I.xi;
         const int4* trow4 = I.trow4;
+        // x holds u between the aggregate and its application; whole 128-byte
+        // lines of the item's columns may be dropped from L2 after that
+        const bool xdisc = (Nt & 15) == 0 && ((reinterpret_cast<uintptr_t>(I.x + (size_t)col0 * Nt) & 127) == 0);
         // True residual s - H H^H q - xi q of every row: per-warp sums of |r|^2
         // per column into s_partd; with store_b also the correction right-hand
         // side b = s - H H^H q.  In correction form through the Gram matrix on
@@ -875,6 +878,19 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                                 mp[1].y = fmaf(g, ub[j].y, mp[1].y);
                             }
                         }
+                    }
+                    // u in x is dead once applied (the next aggregate rewrites
+                    // every entry of the tile before it is read, the final
+                    // x = H^H q every entry): its L2 lines are dropped without
+                    // a write-back, so their space goes back to H.  Only whole
+                    // lines of this item's own columns (Nt a multiple of 16,
+                    // the first column 128-byte aligned), each by the first
+                    // lane of the eight that read it, after all eight have.
+                    if (xdisc) {
+                        __syncwarp();
+                        const int nl = tile * KZ_TILE + 2 * lane;
+                        if ((lane & 7) == 0 && nl + 16 <= Nt)
+                            for (int j = 0; j < ncols; ++j) kz_discard_l2(I.x + (size_t)(col0 + j) * Nt + nl);
                     }
                 }
                 for (int e = tid; e < vcount * J; e += NT) {

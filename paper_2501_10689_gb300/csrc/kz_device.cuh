@@ -784,6 +784,12 @@ __device__ __forceinline__ void tc_u_combine(const float (&a)[4], float2& u0, fl
     u1 = make_float2(a[1] + e3, e1 - a[3]);
 }
 
+// Drops the 128-byte L2 line at p (128-byte aligned) without writing it back:
+// for scratch whose content is dead and is rewritten before it is read again.
+__device__ __forceinline__ void kz_discard_l2(const void* p) {
+    asm volatile("discard.global.L2 [%0], 128;" ::"l"(p) : "memory");
+}
+
 // Column `col` of an Nt-long complex output: entries n and n + 1 (n < Nt).
 // One 16-byte store when the pair is inside the column and its address is
 // 16-byte aligned (the caller's buffer need only be 8-byte aligned), else
