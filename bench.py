@@ -411,13 +411,24 @@ def run_ours(args):
         max_err_v = max(max_err_v, float(np.max(oracle.rzf.rel_err(v, V))))
 
     # ---- roofline of the solver kernel (one launch per step)
+    launch_now = (tuned if tuned else (args.kernel, args.rhs_per_cta, args.threads))
+    tc = launch_now[0] == "tc"
     sumL = np.array([p.sum_len for p in plans], dtype=np.float64)
+    # the orthogonal set's share (read in complex64 by every kernel)
+    sumLF = np.array([float(np.sum(insts[b].vr_len[kp.kz_plan_query(p)[0]])) for b, p in enumerate(plans)])
     Nt = np.array([i.Nt for i in insts], dtype=np.float64)
     col_iters = iters.reshape(args.instances, NRHS).astype(np.float64)
-    # per column-iteration: H read twice per iteration, shared by the 16 columns,
-    # plus the iterate column read twice and written twice
-    unit_bytes = (2.0 * sumL * 8.0 / NRHS + 4.0 * Nt * 8.0)
+    # per column-iteration: H read twice per iteration (the orthogonal rows'
+    # dot and update, the other rows' residual and aggregate), shared by the 16
+    # columns, in the width the kernel reads it (the tensor-core kernel: the
+    # V rows from the FP16 copy, 4 bytes an entry; else complex64, 8), plus
+    # the iterate column read twice and written twice
+    h_unit = 2.0 * (sumLF * 8.0 + (sumL - sumLF) * (4.0 if tc else 8.0)) / NRHS
+    unit_bytes = h_unit + 4.0 * Nt * 8.0
     alg_bytes = float(np.sum(col_iters * unit_bytes[:, None]))
+    # the same count with every entry of H at complex64 width (the formula of
+    # the FP32 kernels), for comparison across kernels
+    c64_bytes = float(np.sum(col_iters * (2.0 * sumL * 8.0 / NRHS + 4.0 * Nt * 8.0)[:, None]))
     unit_flops = 16.0 * sumL  # residual + aggregate, 8 real flops per complex MAC
     alg_flops = float(np.sum(col_iters * unit_flops[:, None]))
     peaks = {}
@@ -427,17 +438,15 @@ def run_ours(args):
     except Exception:
         hbm_peak, peak_src = 6800.0, "fallback"
     achieved_gbs = alg_bytes / (ms_per_step / 1000.0) / 1e9
-    h_bytes = float(np.sum(col_iters * (2.0 * sumL * 8.0 / NRHS)[:, None]))
+    h_bytes = float(np.sum(col_iters * h_unit[:, None]))
     h_gbs = h_bytes / (ms_per_step / 1000.0) / 1e9
     achieved_tflops = alg_flops / (ms_per_step / 1000.0) / 1e12
     sm_mhz = clocks.get("sm_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12  # FP32 FMA lanes x clock under load
-    launch_now = (tuned if tuned else (args.kernel, args.rhs_per_cta, args.threads))
     launches_per_step = kp.kz_batch_query(batch)["launches"]
     traffic = None
     if kernel_sources_sha() == TRAFFIC["sources_sha256"] and args.instances == N_INST:
         traffic = TRAFFIC["bytes_per_launch"].get(tuple(launch_now))
-    tc = launch_now[0] == "tc"
     roofline = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": traffic,
                 "traffic_note": "DRAM bytes per launch from ncu (one pass) on this workload and kernel build; "
@@ -449,17 +458,20 @@ def run_ours(args):
                            else "kz_ahk_kernel (batched VR-OAHK)"),
                 "alu_view": {"achieved_tflops": achieved_tflops, "fp32_fma_peak_tflops": alu_peak,
                              "frac": achieved_tflops / alu_peak},
-                # the channel's bytes alone (2 sumL 8 / 16 per column-iteration;
-                # the iterate term of the bytes above stays in shared memory)
+                # the channel's bytes alone (the H term of the bytes above; the
+                # iterate term stays in shared memory)
                 "h_bytes_view": {"achieved": h_gbs, "unit": "GB/s", "frac": h_gbs / hbm_peak},
+                # every entry of H counted at complex64 width
+                "c64_width_view": {"achieved": c64_bytes / (ms_per_step / 1000.0) / 1e9, "unit": "GB/s",
+                                   "frac": c64_bytes / (ms_per_step / 1000.0) / 1e9 / hbm_peak},
                 # what DRAM actually moved per launch (ncu), over the step time
                 "dram_view": ({"achieved": traffic / (ms_per_step / 1000.0) / 1e9, "unit": "GB/s",
                                "frac": traffic / (ms_per_step / 1000.0) / 1e9 / hbm_peak} if traffic else None)}
     if tc and "bf16_tflops" in peaks:
-        tf32_peak = float(peaks["bf16_tflops"]) / 2.0  # dense TF32 runs at half the BF16 rate
-        roofline["tensor_view"] = {"achieved_tflops": achieved_tflops, "tf32_peak_tflops": tf32_peak,
-                                   "peak_source": "measured bf16_tflops (burst) x 1/2, the nominal TF32:BF16 ratio",
-                                   "frac": achieved_tflops / tf32_peak}
+        f16_peak = float(peaks["bf16_tflops"])  # dense FP16 runs at the BF16 rate
+        roofline["tensor_view"] = {"achieved_tflops": achieved_tflops, "fp16_peak_tflops": f16_peak,
+                                   "peak_source": "measured bf16_tflops (burst); dense FP16 runs at the BF16 rate",
+                                   "frac": achieved_tflops / f16_peak}
 
     # ---- GRK on the same batch (comparison arm)
     grk = None
@@ -574,11 +586,13 @@ def run_ours(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "precoders/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-                "vs_baseline": None, "dtype": "f32+tf32" if tc else "f32", "data": "synthetic",
-                "precision": ("complex64 storage; TF32 tensor-core products with FP32 sums inside the "
-                              "correction-form iteration, the correction held in FP16 scaled per column; "
-                              "refresh b = s - H H^H q through the overlap-pattern Gram matrix, true residual "
-                              "and stopping test with compensated FP32 sums" if tc else
+                "vs_baseline": None, "dtype": "f32+f16" if tc else "f32", "data": "synthetic",
+                "precision": ("complex64 storage; inside the correction-form iteration FP16 tensor-core "
+                              "products with FP32 sums, from an FP16 copy of H (each row scaled by a power of "
+                              "two at or above its norm), the correction held in FP16 scaled per column and "
+                              "phi scaled per column; orthogonal half-step in FP32 on complex64 H; refresh "
+                              "b = s - H H^H q through the overlap-pattern Gram matrix, true residual and "
+                              "stopping test with compensated FP32 sums" if tc else
                               "complex64 storage, FP32 arithmetic; true residual with compensated sums"),
                 "config": bench_config(args, insts),
                 "launch": ({"kernel": tuned[0], "rhs_per_cta": tuned[1], "threads": tuned[2],

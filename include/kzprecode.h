@@ -100,10 +100,13 @@ typedef enum { KZ_C64 = 0, KZ_BF16_MIXED = 1 } kz_prec;
  * columns in shared memory and streams H per column group (every method,
  * both precisions).  TC (AHK / VR_OAHK, C64, 4 or 8 columns) is
  * RESIDENT in correction form with the two contractions of each iteration
- * (the V-row residuals and H_V^H phi) on the tensor cores in TF32 with FP32
- * sums; the right-hand side b = s - H m_ref is recomputed from the complex64
- * H every `refresh` iterations and every stop is confirmed on the true
- * residual, so results meet the same tolerance as RESIDENT.  GROUP (AHK /
+ * (the V-row residuals and H_V^H phi) on the tensor cores with FP16 operands
+ * and FP32 sums, reading an FP16 copy of H that every C64 plan keeps (each
+ * row scaled by a power of two at or above its norm; 4 bytes per stored
+ * entry beside the 8 of complex64); the right-hand side b = s - H m_ref is
+ * recomputed from the complex64 H every `refresh` iterations and every stop
+ * is confirmed on the true residual, so results meet the same tolerance as
+ * RESIDENT.  GROUP (AHK /
  * VR_OAHK, one channel shared by many columns) spreads one channel over a
  * group of CTAs -- each owns a 128-antenna block of the iterate for 16, 32
  * or 64 columns and keeps the block's rows in shared memory -- and runs both

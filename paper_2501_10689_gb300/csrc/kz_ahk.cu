@@ -24,15 +24,16 @@
 //
 // The tensor-core mode (MODE 2) runs the same correction form on the
 // complex64 H, with the two contractions of every iteration on the tensor
-// cores (TF32 products, FP32 sums): the V-row residuals as 8-row blocks
+// cores (FP16 products, FP32 sums): the V-row residuals as 8-row blocks
 // (rows sorted by VR centre, so a block's rows share most of their union
-// interval) and the aggregate H_V^H phi per tile.  The F half-step, the
-// refresh and every stopping decision stay in FP32 on the CUDA cores.  Its
+// interval) and the aggregate H_V^H phi per tile.  They read the plan's FP16
+// copy of H (row k scaled by 1 / hs_k, a power of two at or above ||h_k||),
+// half the bytes of complex64.  The F half-step, the refresh and every
+// stopping decision stay in FP32 on the CUDA cores and the complex64 H.  Its
 // correction m is held in FP16 as m / sigma_j (sigma_j: the column's relative
 // residual at the last refresh times an estimate of the RMS of H^H D^-1 s_j,
 // fixed between refreshes), half the shared memory of FP32, so eight columns
-// of a 4096-antenna channel fit one CTA; FP16 keeps the ten mantissa bits the
-// TF32 MMAs read.
+// of a 4096-antenna channel fit one CTA, and read by the MMAs as stored.
 #include "kz_device.cuh"
 
 namespace {
@@ -49,8 +50,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     static_assert(!TC || J == 4 || J == 8, "tensor-core mode takes 4 or 8 columns");
     extern __shared__ __align__(16) unsigned char kz_smem[];
     __shared__ KzInst sI;
-    __shared__ float s_part[NW][3 * J];
-    __shared__ float s_tot[3 * J];
+    // per column: ||r_V||^2, phi^H r, ||phi||^2 and (tensor-core mode) the
+    // sum of hs_i^2 |phi_i|^2 that scales phi for the FP16 products
+    __shared__ float s_part[NW][4 * J];
+    __shared__ float s_tot[4 * J];
     __shared__ double s_partd[NW][J];
     __shared__ double s_sn2[J];
     __shared__ float s_sn2f[J];  // ||s_j||^2 tol^2 for the tentative test
@@ -102,6 +105,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     int* tptr_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE + 1) * sizeof(int)));
     int* tnv_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE) * sizeof(int)));
     int* vs_s = TC ? reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int))) : nullptr;
+    float* hs_s = TC ? reinterpret_cast<float*>(carve((size_t)L.K_max * sizeof(float))) : nullptr;  // FP16 row scales
     // tensor-core V residual: every 8-row block's union interval is cut in
     // two parts (tasks); part 0 sums into p_s, part 1 into pb_s, and the two
     // are added in that order.  Tasks are dealt to warps largest first, each
@@ -242,6 +246,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             rows_s[i] = I.rows[i];
             rptr_s[i] = I.rptr[i];
             order_s[i] = I.order[i];
+            if (TC) hs_s[i] = I.hs[i];
         }
         for (int t2 = tid; t2 <= I.ntiles; t2 += NT) {
             tptr_s[t2] = I.tptr[t2];
@@ -263,10 +268,10 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     lo = min(lo, rd.x);
                     hi = max(hi, rd.x + rd.y);
                 }
-                const int lo8 = lo & ~7;
-                const int steps = (hi - lo8 + 63) >> 6;  // steps of 64 antennas
-                const int cut = lo8 + 64 * ((steps + 1) >> 1);
-                task_s[2 * b] = make_int4(lo8, min(cut, hi), b, 0);
+                const int lo16 = lo & ~15;
+                const int steps = (hi - lo16 + 63) >> 6;  // steps of 64 antennas
+                const int cut = lo16 + 64 * ((steps + 1) >> 1);
+                task_s[2 * b] = make_int4(lo16, min(cut, hi), b, 0);
                 task_s[2 * b + 1] = make_int4(cut, max(cut, hi), b, 1);
                 tcost_s[2 * b] = (steps + 1) >> 1;
                 tcost_s[2 * b + 1] = steps >> 1;
@@ -541,20 +546,28 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     for (int q = s_wptr[warp]; q < s_wptr[warp + 1]; ++q) {
                         const int4 tk = task_s[wlist_s[q]];
                         float d[4];
-                        tc_row_part<J>(I.Hc, rows_s, rptr_s, vs_s, vcount, tk.z, tk.x, tk.y, m16, MS, W, d);
+                        tc_row_part<J>(I.Hh, rows_s, rptr_s, vs_s, vcount, tk.z, tk.x, tk.y, m16, MS, W, d);
                         float2* dst = tk.w ? pb_s : p_s;
                         const int k = 8 * tk.z + 2 * c;
-                        if (g < W) {
+                        if (g < W) {  // true units: times the row's hs and the column's sigma
                             const float sg = s_sig[g];
-                            if (k < vcount) dst[vs_s[k] * J + g] = make_float2(d[0] * sg, d[2] * sg);
-                            if (k + 1 < vcount) dst[vs_s[k + 1] * J + g] = make_float2(d[1] * sg, d[3] * sg);
+                            if (k < vcount) {
+                                const int r = vs_s[k];
+                                const float f = sg * hs_s[r];
+                                dst[r * J + g] = make_float2(d[0] * f, d[2] * f);
+                            }
+                            if (k + 1 < vcount) {
+                                const int r = vs_s[k + 1];
+                                const float f = sg * hs_s[r];
+                                dst[r * J + g] = make_float2(d[1] * f, d[3] * f);
+                            }
                         }
                     }
                 }
                 __syncthreads();
                 // residuals, phi and the column sums; thread tid always has
                 // column j = tid % J (J divides the block size)
-                float spr = 0.f, spn = 0.f, spp = 0.f;
+                float spr = 0.f, spn = 0.f, spp = 0.f, sph = 0.f;
                 const int j = tid % J;
                 const bool on = (act >> j) & 1;
                 for (int e = tid; e < vcount * J; e += NT) {
@@ -570,7 +583,9 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                         ph = on ? make_float2(rx * di, ry * di) : make_float2(0.f, 0.f);
                         spr += r2;
                         spn += on ? r2 * di : 0.f;
-                        spp += ph.x * ph.x + ph.y * ph.y;
+                        const float p2 = ph.x * ph.x + ph.y * ph.y;
+                        spp += p2;
+                        sph += p2 * (hs_s[i] * hs_s[i]);
                     }
                     p_s[i * J + j] = ph;
                 }
@@ -579,11 +594,13 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     spr += __shfl_xor_sync(KZ_FULL, spr, o);
                     spn += __shfl_xor_sync(KZ_FULL, spn, o);
                     spp += __shfl_xor_sync(KZ_FULL, spp, o);
+                    sph += __shfl_xor_sync(KZ_FULL, sph, o);
                 }
                 if (lane < J) {
                     s_part[warp][lane] = spr;
                     s_part[warp][J + lane] = spn;
                     s_part[warp][2 * J + lane] = spp;
+                    s_part[warp][3 * J + lane] = sph;
                 }
             } else {
             // rows v and v + NW go to the same warp together (two loads streams)
@@ -623,7 +640,7 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             }
             }
             __syncthreads();
-            if (tid < 3 * J) {
+            if (tid < (TC ? 4 : 3) * J) {
                 float a = 0.f;
                 for (int w = 0; w < NW; ++w) a += s_part[w][tid];
                 s_tot[tid] = a;
@@ -729,35 +746,60 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     float uu[2 * NB];
 #pragma unroll
                     for (int j = 0; j < 2 * NB; ++j) uu[j] = 0.f;
+                    // phi enters the FP16 products as hs_i phi_ij / tau_j, tau_j the
+                    // RMS of hs_i phi_ij over the V rows (0: a zero column); this
+                    // lane's B column 4 nb + (g & 3), its output columns 4 nb + 2c
+                    // and 4 nb + 2c + 1 (c < 2)
+                    const float rv = 1.f / (float)max(vcount, 1);
+                    auto itau_of = [&](int j) {
+                        const float a = s_tot[3 * J + j] * rv;
+                        return a > 0.f ? rsqrtf(a) : 0.f;
+                    };
+                    float itl[NB], tl0[NB], tl1[NB];
+#pragma unroll
+                    for (int nb = 0; nb < NB; ++nb) {
+                        itl[nb] = itau_of(4 * nb + (g & 3));
+                        const float i0 = itau_of(4 * nb + 2 * (c & 1)), i1 = itau_of(4 * nb + 2 * (c & 1) + 1);
+                        tl0[nb] = i0 > 0.f ? 1.f / i0 : 0.f;
+                        tl1[nb] = i1 > 0.f ? 1.f / i1 : 0.f;
+                    }
                     // tasks: tile halves (32 antennas each)
                     for (int task = warp; task < 2 * I.ntiles; task += NW) {
                         const int tile = task >> 1, part = task & 1;
                         const int k0 = tptr_s[tile];
                         const int k1 = oahk ? k0 + tnv_s[tile] : tptr_s[tile + 1];
                         if (k0 == k1) continue;
-                        float acc[2][2][NB][4];
+                        float acc[4][NB][4];
                         if (trow_s)
-                            tc_tile_aggr<J, true>(I.Hc, trow4, trow_s, rows_s, rptr_s, tile, part, k0, k1, p_s, acc);
+                            tc_tile_aggr<J, true>(I.Hh, trow4, trow_s, rows_s, rptr_s, hs_s, tile, part, k0, k1, p_s,
+                                                  itl, acc);
                         else
-                            tc_tile_aggr<J, false>(I.Hc, trow4, trow_s, rows_s, rptr_s, tile, part, k0, k1, p_s, acc);
-                        // lane (g, c < 2) holds u at the antenna pair (n, n + 1)
-                        // for columns j and j + 1: one 16-byte store per column
+                            tc_tile_aggr<J, false>(I.Hh, trow4, trow_s, rows_s, rptr_s, hs_s, tile, part, k0, k1, p_s,
+                                                   itl, acc);
+                        // lane (g, c < 2) holds u at antennas n .. n + 3 (n =
+                        // s + 4 g) for columns j and j + 1: two 16-byte stores per
+                        // column, after the factor tau_j
 #pragma unroll
-                        for (int sp = 0; sp < 2; ++sp) {
-                            const int n = tile * KZ_TILE + 32 * part + 16 * sp + 2 * g;
+                        for (int q2 = 0; q2 < 4; q2 += 2) {
+                            const int n = tile * KZ_TILE + 32 * part + 4 * g + q2;
 #pragma unroll
                             for (int nb = 0; nb < NB; ++nb) {
-                                float2 u0e, u1e, u0o, u1o;
-                                tc_u_combine(acc[sp][0][nb], u0e, u1e);
-                                tc_u_combine(acc[sp][1][nb], u0o, u1o);
+                                float2 u0a, u1a, u0b, u1b;
+                                tc_u_combine(acc[q2][nb], u0a, u1a);
+                                tc_u_combine(acc[q2 + 1][nb], u0b, u1b);
                                 const int j = 4 * nb + 2 * c;
                                 if (c < 2) {
+                                    const float t0 = tl0[nb], t1 = tl1[nb];
+                                    u0a = make_float2(u0a.x * t0, u0a.y * t0);
+                                    u0b = make_float2(u0b.x * t0, u0b.y * t0);
+                                    u1a = make_float2(u1a.x * t1, u1a.y * t1);
+                                    u1b = make_float2(u1b.x * t1, u1b.y * t1);
                                     if (n < Nt) {
-                                        kz_store_pair(I.x, Nt, col0 + j, n, j < ncols, u0e, u0o);
-                                        kz_store_pair(I.x, Nt, col0 + j + 1, n, j + 1 < ncols, u1e, u1o);
+                                        kz_store_pair(I.x, Nt, col0 + j, n, j < ncols, u0a, u0b);
+                                        kz_store_pair(I.x, Nt, col0 + j + 1, n, j + 1 < ncols, u1a, u1b);
                                     }
-                                    uu[2 * nb] += u0e.x * u0e.x + u0e.y * u0e.y + u0o.x * u0o.x + u0o.y * u0o.y;
-                                    uu[2 * nb + 1] += u1e.x * u1e.x + u1e.y * u1e.y + u1o.x * u1o.x + u1o.y * u1o.y;
+                                    uu[2 * nb] += u0a.x * u0a.x + u0a.y * u0a.y + u0b.x * u0b.x + u0b.y * u0b.y;
+                                    uu[2 * nb + 1] += u1a.x * u1a.x + u1a.y * u1a.y + u1b.x * u1b.x + u1b.y * u1b.y;
                                 }
                             }
                         }
@@ -1060,7 +1102,7 @@ size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow) {
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     const size_t ntask = 2 * (size_t)((K + 7) / 8);
     return kz_smem_ahk(J, Ntp_max, K, KZ_C64) - r16((size_t)J * Ntp_max * sizeof(float2)) +
-           r16((size_t)m_elems * sizeof(__half2)) + r16((size_t)K * sizeof(int)) +
+           r16((size_t)m_elems * sizeof(__half2)) + r16((size_t)K * sizeof(int)) + r16((size_t)K * sizeof(float)) +
            r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int)) +
            r16((size_t)trow * sizeof(unsigned short));
 }

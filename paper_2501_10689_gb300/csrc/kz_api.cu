@@ -95,6 +95,8 @@ struct kz_plan {
     float2* d_G = nullptr;  // H H^H on the X_k pattern
     float2* d_Hc = nullptr;
     __nv_bfloat162* d_Hb = nullptr;
+    __half2* d_Hh = nullptr;  // complex64 plans: FP16 rows scaled by 1 / hs (tensor-core contractions)
+    float* d_hs = nullptr;
     float2* d_scratch = nullptr;  // adjoint right-hand side G~ (grown on demand)
     size_t scratch_elems = 0;
     int sms = 1;
@@ -108,7 +110,7 @@ struct kz_plan {
 
     ~kz_plan() {
         void* ps[] = {d_rows, d_rptr, d_in_off, d_nrm, d_nrmd, d_order, d_xptr, d_xidx,
-                      d_tptr, d_tnv, d_trow4, d_vsort, d_G, d_Hc, d_Hb, d_scratch};
+                      d_tptr, d_tnv, d_trow4, d_vsort, d_G, d_Hc, d_Hb, d_Hh, d_hs, d_scratch};
         for (void* p : ps)
             if (p) cudaFree(p);
         grp.release();
@@ -136,6 +138,8 @@ struct kz_plan {
         I.trow4 = d_trow4;
         I.Hc = d_Hc;
         I.Hb = d_Hb;
+        I.Hh = d_Hh;
+        I.hs = d_hs;
         I.nrmd = d_nrmd;
         I.in_off = d_in_off;
         I.vsort = d_vsort;
@@ -583,13 +587,14 @@ static kz_status plan_build(const char* fn, kz_plan** out, int32_t K, int32_t Nt
     P->Ntp = ((Nt + (Nt & 1)) + KZ_TILE - 1) / KZ_TILE * KZ_TILE;
     P->ntiles = P->Ntp / KZ_TILE;
 
-    // aligned rows
+    // aligned rows: intervals on multiples of four antennas (one 16-byte load
+    // of the FP16 copy is inside a row or outside it), zero-filled outside the VR
     std::vector<int4> rows(K);
     std::vector<int> rptr(K), in_off(K);
     int64_t acc = 0, acc_in = 0;
     for (int k = 0; k < K; ++k) {
         const int o = vr_offset[k], e = vr_offset[k] + vr_len[k];
-        const int a = o & ~1, b = (e + 1) & ~1;
+        const int a = o & ~3, b = (e + 3) & ~3;
         rows[k] = make_int4(a, b - a, o, e);
         rptr[k] = (int)acc;
         in_off[k] = (int)acc_in;
@@ -714,6 +719,10 @@ static kz_status plan_build(const char* fn, kz_plan** out, int32_t K, int32_t Nt
     KZ_TRY(upload(&P->d_vsort, vsort, st));
     KZ_TRY(cudaMalloc((void**)&P->d_Hc, std::max<int64_t>(acc, 2) * sizeof(float2)));
     if (prec == KZ_BF16_MIXED) KZ_TRY(cudaMalloc((void**)&P->d_Hb, std::max<int64_t>(acc, 2) * sizeof(__nv_bfloat162)));
+    if (prec == KZ_C64) {
+        KZ_TRY(cudaMalloc((void**)&P->d_Hh, std::max<int64_t>(acc, 4) * sizeof(__half2)));
+        KZ_TRY(cudaMalloc((void**)&P->d_hs, K * sizeof(float)));
+    }
     KZ_TRY(cudaMalloc((void**)&P->d_nrm, K * sizeof(float)));
     KZ_TRY(cudaMalloc((void**)&P->d_nrmd, K * sizeof(double)));
     if (H_packed)
@@ -722,7 +731,7 @@ static kz_status plan_build(const char* fn, kz_plan** out, int32_t K, int32_t Nt
     else
         KZ_TRY(kz_pack_dense(reinterpret_cast<const float2*>(H_dense), Nt, P->d_rows, P->d_rptr, K, P->d_Hc, P->d_Hb,
                              st));
-    KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, st));
+    KZ_TRY(kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, K, P->d_nrmd, P->d_nrm, P->d_Hh, P->d_hs, st));
     KZ_TRY(cudaMalloc((void**)&P->d_G, std::max<size_t>(P->xidx.size(), 1) * sizeof(float2)));
     KZ_TRY(kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, K, P->d_G, st));
     KZ_TRY(cudaStreamSynchronize(st));
@@ -767,7 +776,8 @@ kz_status kz_plan_update(kz_plan* P, const kz_cf32* H_packed, void* stream) {
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaError_t e = kz_pack_rows(reinterpret_cast<const float2*>(H_packed), P->d_in_off, P->d_rows, P->d_rptr, P->K,
                                  P->total2, P->d_Hc, P->d_Hb, st);
-    if (e == cudaSuccess) e = kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, P->K, P->d_nrmd, P->d_nrm, st);
+    if (e == cudaSuccess)
+        e = kz_row_norms(P->d_Hc, P->d_rows, P->d_rptr, P->K, P->d_nrmd, P->d_nrm, P->d_Hh, P->d_hs, st);
     if (e == cudaSuccess) e = kz_gram(P->d_Hc, P->d_rows, P->d_rptr, P->d_xptr, P->d_xidx, P->K, P->d_G, st);
     if (e == cudaSuccess && P->grp.built)
         e = kz_grp_prepare(grp_chan(P), P->d_Hc, P->total2, P->d_rows, P->d_rptr, P->d_nrm, P->grp.d_stat, P->grp.fmt, st);

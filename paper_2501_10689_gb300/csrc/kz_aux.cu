@@ -77,13 +77,36 @@ __device__ double row_norm2(const float2* __restrict__ h, int len) {
     return out;  // valid in thread 0
 }
 
+// The FP16 copy of row k (len2 entries at h): every entry times 1 / hs_k,
+// hs_k the power of two at or above ||h_k|| (so each scaled entry is below 1
+// and the row's largest entries keep FP16's full 11-bit precision), rounded to
+// nearest even; hs_k = 1 for a zero or non-finite norm.  Called by every
+// thread of the block after the norm t (FP64) is known to all of them.
+__device__ void row_to_f16(const float2* __restrict__ h, int len, double t, __half2* hh, float* hs_k) {
+    int ex = 0;
+    if (t > 0.0 && t < 1e300) (void)frexp(sqrt(t), &ex);  // sqrt(t) < 2^ex
+    ex = max(-126, min(126, ex));
+    const float inv = ldexpf(1.f, -ex);
+    for (int p = threadIdx.x; p < len; p += blockDim.x) {
+        const float2 v = h[p];
+        hh[p] = __float22half2_rn(make_float2(v.x * inv, v.y * inv));
+    }
+    if (threadIdx.x == 0) *hs_k = ldexpf(1.f, ex);
+}
+
 __global__ void row_norms_kernel(const float2* __restrict__ Hc, const int4* __restrict__ rows,
-                                 const int* __restrict__ rptr, double* out_d, float* out_f) {
+                                 const int* __restrict__ rptr, double* out_d, float* out_f, __half2* Hh, float* hs) {
+    __shared__ double s_t;
     const int k = blockIdx.x;
     const double t = row_norm2(Hc + rptr[k], rows[k].y);
     if (threadIdx.x == 0) {
         out_d[k] = t;
         out_f[k] = (float)t;
+        s_t = t;
+    }
+    if (Hh) {
+        __syncthreads();
+        row_to_f16(Hc + rptr[k], rows[k].y, s_t, Hh + rptr[k], hs + k);
     }
 }
 
@@ -222,10 +245,16 @@ __global__ void batch_update_kernel(const KzInst* __restrict__ insts, const int2
             if (Hb) Hb[p] = __float22bfloat162_rn(h);
         }
     } else if (phase == 1) {
+        __shared__ double s_t;
         const double t = row_norm2(I.Hc + I.rptr[k], rd.y);
         if (threadIdx.x == 0) {
             const_cast<double*>(I.nrmd)[k] = t;
             const_cast<float*>(I.nrm)[k] = (float)t;
+            s_t = t;
+        }
+        if (I.Hh) {
+            __syncthreads();
+            row_to_f16(I.Hc + I.rptr[k], rd.y, s_t, const_cast<__half2*>(I.Hh) + I.rptr[k], const_cast<float*>(I.hs) + k);
         }
     } else if (phase == 2) {
         gram_row_upper(I.Hc, I.rows, I.rptr, I.xptr, I.xidx, const_cast<float2*>(I.G), k);
@@ -692,8 +721,8 @@ cudaError_t kz_pack_dense(const float2* Hd, int Nt, const int4* rows, const int*
 }
 
 cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d, float* out_f,
-                         cudaStream_t st) {
-    row_norms_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, out_d, out_f);
+                         __half2* Hh, float* hs, cudaStream_t st) {
+    row_norms_kernel<<<K, 256, 0, st>>>(Hc, rows, rptr, out_d, out_f, Hh, hs);
     return cudaGetLastError();
 }
 

@@ -578,47 +578,58 @@ __device__ __forceinline__ void tile_accum(const KzInst& I, const int4* __restri
 }
 
 // ---------------------------------------------------------------------------
-// Tensor-core inner products (warp-level mma.sync m16n8k8, TF32 operands,
-// FP32 accumulation).  TF32 keeps the top 10 mantissa bits of each FP32
-// operand (the low bits are ignored), so these products serve the inner
-// iteration of the correction form only: its right-hand side b = s - H m_ref
-// is recomputed from the complex64 H in FP32 at every refresh, and stops are
-// confirmed on that true residual.
+// Tensor-core inner products (warp-level mma.sync m16n8k16, FP16 operands,
+// FP32 accumulation).  Every operand carries FP16's 11-bit significand: the
+// channel from its FP16 copy (each row scaled by a power of two, so its
+// entries keep full precision), the correction iterate as stored (FP16,
+// scaled per column) and phi scaled per column by its RMS.  These products
+// serve the inner iteration of the correction form only: its right-hand side
+// b = s - H m_ref is recomputed from the complex64 H at every refresh, and
+// stops are confirmed on that true residual.
 //
-// Fragment ownership (lane = 4 g + c): A (16 x 8, row-major) a0 = (g, c),
-// a1 = (g + 8, c), a2 = (g, c + 4), a3 = (g + 8, c + 4); B (8 x 8) b0 = (c, g),
-// b1 = (c + 4, g); D (16 x 8) d0 = (g, 2c), d1 = (g, 2c + 1), d2 = (g + 8, 2c),
-// d3 = (g + 8, 2c + 1).
-__device__ __forceinline__ void mma_tf32(float (&d)[4], float a0, float a1, float a2, float a3, float b0,
-                                         float b1) {
-    asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+// Fragment ownership (lane = 4 g + c; two FP16 values per register, the
+// lower K index in the low half): A (16 x 16, row-major) a0 = (g, 2c | 2c + 1),
+// a1 = (g + 8, 2c | 2c + 1), a2 = (g, 2c + 8 | 2c + 9), a3 = (g + 8, 2c + 8 | 2c + 9);
+// B (16 x 8) b0 = (2c | 2c + 1, g), b1 = (2c + 8 | 2c + 9, g); D (16 x 8, FP32)
+// d0 = (g, 2c), d1 = (g, 2c + 1), d2 = (g + 8, 2c), d3 = (g + 8, 2c + 1).
+__device__ __forceinline__ void mma_f16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
+                                        unsigned b0, unsigned b1) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
         "{%0, %1, %2, %3};\n"
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(__float_as_uint(a0)), "r"(__float_as_uint(a1)), "r"(__float_as_uint(a2)), "r"(__float_as_uint(a3)),
-          "r"(__float_as_uint(b0)), "r"(__float_as_uint(b1)));
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// An FP16 pair {re, im} as {re, -im} (sign bit of the high half) and as
+// {im, re} (halves swapped).
+__device__ __forceinline__ unsigned h2_conj(unsigned v) { return v ^ 0x80000000u; }
+__device__ __forceinline__ unsigned h2_swap(unsigned v) { return __byte_perm(v, 0u, 0x1032); }
+
+__device__ __forceinline__ unsigned h2_pack(float lo, float hi) {
+    const __half2 t = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<const unsigned*>(&t);
 }
 
 // Products H m_j for a block of 8 rows, vs[8 b .. 8 b + 8) (fewer at the end
 // of the list, nv entries), over the antenna range [nbeg, nend) (nbeg a
-// multiple of 8, nend even; a block's union interval is cut into such parts),
-// eight antennas per pair of MMAs:
-//   A[(j, re)][(n, re)] = Re m_j(n),  A[(j, re)][(n, im)] = -Im m_j(n),
-//   A[(j, im)][(n, re)] = Im m_j(n),  A[(j, im)][(n, im)] =  Re m_j(n)
+// multiple of 16, nend of 4; a block's union interval is cut into such parts),
+// sixteen antennas per pair of MMAs, K = (antenna, re | im):
+//   A[(j, re)][(n, re | im)] = {Re, -Im} m_j(n),  A[(j, im)][(n, re | im)] = {Im, Re} m_j(n)
 // (row j of the 16 for (j, re), row j + 8 for (j, im); j < W, the rest zero),
-// B[(n, re | im)][row] = Re | Im H[row, n] (zero outside the row's interval),
-// so D[(j, re | im)][row] = Re | Im (H m_j)[row] over the range.  Lane (g, c)
-// loads the antenna pair (n0 + 2c, n0 + 2c + 1) of row g and of m_g as one
-// 16-byte load each; the first MMA of the pair takes the even antennas, the
-// second the odd ones, with the K index ordered (n, re) = c, (n, im) = c + 4.
-// (Aligned intervals start and end on even antennas, so both antennas of a
-// pair are inside or outside a row together.)  Lane (g, c) returns column
-// j = g of rows 2c (d[0] + i d[2]) and 2c + 1 (d[1] + i d[3]) of the block.
-// m_s column stride MS (even; columns 16-byte aligned): float2 entries, or
-// FP16 pairs (__half2) of the scaled iterate.
-template <int J, class MT>
-__device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const int4* rows, const int* rptr,
+// B[(n, re | im)][row] = {Re, Im} H[row, n] (zero outside the row's interval),
+// so D[(j, re | im)][row] = Re | Im (H m_j)[row] over the range, in the units
+// of the FP16 copies (times hs_row sigma_j in true units).  Lane (g, c) loads
+// antennas n .. n + 3 (n = n0 + 4c) of row g and of m_g as one 16-byte load
+// each: the first MMA takes n (K = 2c, 2c + 1) and n + 1 (K = 2c + 8, 2c + 9),
+// the second n + 2 and n + 3.  (Aligned intervals start and end on multiples
+// of four antennas, so the four antennas of a load are inside or outside a
+// row together.)  Lane (g, c) returns column j = g of rows 2c (d[0] + i d[2])
+// and 2c + 1 (d[1] + i d[3]) of the block.  m16: the FP16 iterate, column
+// stride MS (a multiple of 4; columns 16-byte aligned).
+template <int J>
+__device__ __forceinline__ void tc_row_part(const __half2* __restrict__ Hh, const int4* rows, const int* rptr,
                                             const int* vs, int nv, int b, int nbeg, int nend,
-                                            const MT* __restrict__ m_s, int MS, int W, float (&d)[4]) {
+                                            const __half2* __restrict__ m16, int MS, int W, float (&d)[4]) {
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
     const int k = 8 * b + g;
     int a = 0, len = 0, hb = 0;
@@ -629,42 +640,38 @@ __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const
         len = rd.y;
         hb = rptr[row] - rd.x;
     }
-    // four accumulator sets (even / odd antenna of the pair x even / odd
-    // step u), so no MMA waits on the one before it
+    // four accumulator sets (first / second MMA of a load x even / odd step
+    // u), so no MMA waits on the one before it
     float e[4] = {0.f, 0.f, 0.f, 0.f}, d2[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int u = 0; u < 4; ++u) d[u] = 0.f;
     const bool jok = g < W;  // W <= J columns of this item
-    const MT* mj = m_s + (jok ? g : 0) * MS;
-    const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-    // eight antenna pairs per lane per step: all eight 16-byte H loads are in
-    // flight before the first MMA of the step; the iterate is read from
+    const __half2* mj = m16 + (jok ? g : 0) * MS;
+    const uint4 z = make_uint4(0u, 0u, 0u, 0u);
+    // eight 16-byte H loads per lane per step (128 antennas of the row), all
+    // in flight before the first MMA of the step; the iterate is read from
     // shared memory next to its MMAs.  Entries at or beyond nend are zero on
     // both sides.
     constexpr int U = 8;
-    for (int n0 = nbeg; n0 < nend; n0 += 8 * U) {
-        float4 h[U];
+    for (int n0 = nbeg; n0 < nend; n0 += 16 * U) {
+        uint4 h[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int n = n0 + 8 * u + 2 * c;
+            const int n = n0 + 16 * u + 4 * c;
             h[u] = (n < nend && (unsigned)(n - a) < (unsigned)len)
-                       ? __ldg(reinterpret_cast<const float4*>(Hc + hb + n))
+                       ? __ldg(reinterpret_cast<const uint4*>(Hh + hb + n))
                        : z;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
-            const int n = n0 + 8 * u + 2 * c;
-            float4 m = z;
-            if (jok && n < nend) {
-                if constexpr (sizeof(MT) == 4) m = m16_pair(reinterpret_cast<const __half2*>(mj + n));
-                else m = *reinterpret_cast<const float4*>(mj + n);
-            }
+            const int n = n0 + 16 * u + 4 * c;
+            const uint4 m = (jok && n < nend) ? *reinterpret_cast<const uint4*>(mj + n) : z;
             if (u & 1) {
-                mma_tf32(d2, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
-                mma_tf32(e2, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
+                mma_f16(d2, h2_conj(m.x), h2_swap(m.x), h2_conj(m.y), h2_swap(m.y), h[u].x, h[u].y);
+                mma_f16(e2, h2_conj(m.z), h2_swap(m.z), h2_conj(m.w), h2_swap(m.w), h[u].z, h[u].w);
             } else {
-                mma_tf32(d, m.x, m.y, -m.y, m.x, h[u].x, h[u].y);
-                mma_tf32(e, m.z, m.w, -m.w, m.z, h[u].z, h[u].w);
+                mma_f16(d, h2_conj(m.x), h2_swap(m.x), h2_conj(m.y), h2_swap(m.y), h[u].x, h[u].y);
+                mma_f16(e, h2_conj(m.z), h2_swap(m.z), h2_conj(m.w), h2_swap(m.w), h[u].z, h[u].w);
             }
         }
     }
@@ -673,40 +680,38 @@ __device__ __forceinline__ void tc_row_part(const float2* __restrict__ Hc, const
 }
 
 // u = H_V^H phi on one half (32 antennas, part 0 or 1) of a 64-antenna
-// tile, antenna-major, eight covering rows (list entries k0..k1 of the tile)
-// per MMA:
+// tile, antenna-major, sixteen covering rows (list entries k0..k1 of the
+// tile) per step, four MMAs per block of four columns:
 //   A[(n, re)][row] = Re H[row, n],  A[(n, im)][row] = Im H[row, n]
-//   (rows g and g + 8 of the 16 for antenna n),
-//   B[row][(j, re)] = Re phi[row][j], B[row][(j, im)] = Im phi[row][j]
+//   (rows g and g + 8 of the 16 for antenna n = s + 4 g + q of MMA q < 4),
+//   B[row][(j, re | im)] = {Re, Im} phi[row][j] hs_row / tau_j
 //   (columns 4 nb .. 4 nb + 3 per block nb of the 8 N entries).
-// Lane (g, c) loads the antenna pair (s + 2g, s + 2g + 1) of rows c and
-// c + 4 as one 16-byte load each, for the two 16-antenna spans s of the
-// half; acc[sp][odd][nb] holds the products of antenna s + 2g + odd, whose
-// sums and differences give u (tc_u_combine).  coef: K x J phi in shared
-// memory.  Two chunks of eight rows per step (eight 16-byte loads of a lane
-// in flight before the MMAs).
+// Lane (g, c) loads antennas s + 4 g .. s + 4 g + 3 of the step's covering
+// rows 2c, 2c + 1, 2c + 8 and 2c + 9 (its K indices), one 16-byte load each,
+// and pairs two rows' real (imaginary) parts of an antenna in one register;
+// acc[q][nb] holds the products of antenna s + 4 g + q, whose sums and
+// differences give u / tau_j (tc_u_combine).  coef: K x J phi in shared
+// memory (FP32); hs: the rows' scales; itau[nb] = 1 / tau_j for this lane's
+// column j = 4 nb + (g & 3) (0 for a column whose phi is zero).
 // STAGED: the entries' row indices come from trow_s and their intervals and
 // offsets from rows / rptr (shared memory) instead of trow4 (global).
 template <int J, bool STAGED>
-__device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, const int4* __restrict__ trow4,
+__device__ __forceinline__ void tc_tile_aggr(const __half2* __restrict__ Hh, const int4* __restrict__ trow4,
                                              const unsigned short* trow_s, const int4* rows, const int* rptr,
-                                             int tile, int part, int k0, int k1, const float2* __restrict__ coef,
-                                             float (&acc)[2][2][J / 4][4]) {
+                                             const float* hs, int tile, int part, int k0, int k1,
+                                             const float2* __restrict__ coef, const float (&itau)[J / 4],
+                                             float (&acc)[4][J / 4][4]) {
     constexpr int NB = J / 4;
-    constexpr int KC = (J == 4) ? 3 : 2;  // chunks of eight rows per step
     const int lane = threadIdx.x & 31, g = lane >> 2, c = lane & 3;
 #pragma unroll
-    for (int sp = 0; sp < 2; ++sp)
+    for (int q = 0; q < 4; ++q)
 #pragma unroll
-        for (int od = 0; od < 2; ++od)
+        for (int nb = 0; nb < NB; ++nb)
 #pragma unroll
-            for (int nb = 0; nb < NB; ++nb)
-#pragma unroll
-                for (int u = 0; u < 4; ++u) acc[sp][od][nb][u] = 0.f;
+            for (int u = 0; u < 4; ++u) acc[q][nb][u] = 0.f;
     const int4 none = make_int4(0, 0, 0, 0);  // empty interval: never matches
-    const float2 z = make_float2(0.f, 0.f);
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    const int nbase = tile * KZ_TILE + 32 * part + 2 * g;
+    const uint4 z4 = make_uint4(0u, 0u, 0u, 0u);
+    const int n = tile * KZ_TILE + 32 * part + 4 * g;
     auto entry = [&](int kk) -> int4 {
         if (kk >= k1) return none;
         if constexpr (STAGED) {
@@ -717,57 +722,52 @@ __device__ __forceinline__ void tc_tile_aggr(const float2* __restrict__ Hc, cons
             return __ldg(trow4 + kk);
         }
     };
-    int4 nxt[KC][2];
+    // list offsets of this lane's four rows in a step
+    int off[4];
 #pragma unroll
-    for (int q = 0; q < KC; ++q)
+    for (int i = 0; i < 4; ++i) off[i] = 2 * c + (i & 1) + 8 * (i >> 1);
+    int4 nxt[4];
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) nxt[q][h2] = entry(k0 + 8 * q + 4 * h2 + c);
-    for (int k = k0; k < k1; k += 8 * KC) {
-        int4 e[KC][2];
+    for (int i = 0; i < 4; ++i) nxt[i] = entry(k0 + off[i]);
+    for (int k = k0; k < k1; k += 16) {
+        int4 e[4];
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-            e[q][0] = nxt[q][0];
-            e[q][1] = nxt[q][1];
-        }
-        float4 h[KC][2][2];
+        for (int i = 0; i < 4; ++i) e[i] = nxt[i];
+        uint4 h[4];
 #pragma unroll
-        for (int q = 0; q < KC; ++q)
-#pragma unroll
-            for (int sp = 0; sp < 2; ++sp) {
-                const int n = nbase + 16 * sp;
-#pragma unroll
-                for (int h2 = 0; h2 < 2; ++h2) {
-                    const int4 en = e[q][h2];
-                    h[q][sp][h2] = (n >= en.z && n < en.w)
-                                       ? __ldg(reinterpret_cast<const float4*>(Hc + en.y + n))
-                                       : z4;
-                }
-            }
+        for (int i = 0; i < 4; ++i)
+            h[i] = (n >= e[i].z && n < e[i].w) ? __ldg(reinterpret_cast<const uint4*>(Hh + e[i].y + n)) : z4;
         // descriptors of the next step, in flight while this one is used
 #pragma unroll
-        for (int q = 0; q < KC; ++q)
+        for (int i = 0; i < 4; ++i) nxt[i] = entry(k + 16 + off[i]);
+        // B: the four rows' phi in this lane's column slots, scaled by the
+        // row's hs and the column's 1 / tau (0 for a list entry past the end)
+        float sc[4];
 #pragma unroll
-            for (int h2 = 0; h2 < 2; ++h2) nxt[q][h2] = entry(k + 8 * KC + 8 * q + 4 * h2 + c);
+        for (int i = 0; i < 4; ++i) sc[i] = (k + off[i] < k1) ? hs[e[i].x] : 0.f;
+        unsigned b0[NB], b1[NB];
 #pragma unroll
-        for (int q = 0; q < KC; ++q) {
-            const bool va = k + 8 * q + c < k1, vb = k + 8 * q + c + 4 < k1;
-            float b0[NB], b1[NB];
+        for (int nb = 0; nb < NB; ++nb) {
+            const int j = 4 * nb + (g & 3);
+            float v[4];
 #pragma unroll
-            for (int nb = 0; nb < NB; ++nb) {
-                const int j = 4 * nb + (g & 3);
-                const float2 pa = va ? coef[e[q][0].x * J + j] : z;
-                const float2 pb = vb ? coef[e[q][1].x * J + j] : z;
-                b0[nb] = (g >> 2) ? pa.y : pa.x;
-                b1[nb] = (g >> 2) ? pb.y : pb.x;
+            for (int i = 0; i < 4; ++i) {
+                const float2 p = sc[i] != 0.f ? coef[e[i].x * J + j] : make_float2(0.f, 0.f);
+                v[i] = ((g >> 2) ? p.y : p.x) * (sc[i] * itau[nb]);
             }
+            b0[nb] = h2_pack(v[0], v[1]);
+            b1[nb] = h2_pack(v[2], v[3]);
+        }
 #pragma unroll
-            for (int sp = 0; sp < 2; ++sp)
+        for (int q = 0; q < 4; ++q) {
+            const unsigned w0 = q == 0 ? h[0].x : q == 1 ? h[0].y : q == 2 ? h[0].z : h[0].w;
+            const unsigned w1 = q == 0 ? h[1].x : q == 1 ? h[1].y : q == 2 ? h[1].z : h[1].w;
+            const unsigned w2 = q == 0 ? h[2].x : q == 1 ? h[2].y : q == 2 ? h[2].z : h[2].w;
+            const unsigned w3 = q == 0 ? h[3].x : q == 1 ? h[3].y : q == 2 ? h[3].z : h[3].w;
+            const unsigned a0 = __byte_perm(w0, w1, 0x5410), a1 = __byte_perm(w0, w1, 0x7632);
+            const unsigned a2 = __byte_perm(w2, w3, 0x5410), a3 = __byte_perm(w2, w3, 0x7632);
 #pragma unroll
-                for (int nb = 0; nb < NB; ++nb) {
-                    const float4 ha = h[q][sp][0], hb = h[q][sp][1];
-                    mma_tf32(acc[sp][0][nb], ha.x, ha.y, hb.x, hb.y, b0[nb], b1[nb]);
-                    mma_tf32(acc[sp][1][nb], ha.z, ha.w, hb.z, hb.w, b0[nb], b1[nb]);
-                }
+            for (int nb = 0; nb < NB; ++nb) mma_f16(acc[q][nb], a0, a1, a2, a3, b0[nb], b1[nb]);
         }
     }
 }

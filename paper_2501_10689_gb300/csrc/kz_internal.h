@@ -24,9 +24,10 @@
 #include "../../include/kzprecode.h"
 
 #define KZ_TILE 64
-// Tensor-core mode: padding of each iterate column in shared memory (entries),
-// so the columns one MMA fragment reads start 16 banks apart
-#define KZ_TC_PAD 8
+// Tensor-core mode: padding of each iterate column in shared memory (entries
+// of 4 bytes), so that the two columns one 8-lane phase of a 16-byte fragment
+// load reads start 64 bytes (16 banks) apart
+#define KZ_TC_PAD 16
 
 struct KzInst {
     // --- channel (fixed at plan creation) ---
@@ -43,6 +44,11 @@ struct KzInst {
     const int4* trow4;         // per entry {row, rptr - a, a, a + len2}
     const float2* Hc;          // aligned complex64 rows
     const __nv_bfloat162* Hb;  // aligned BF16 (re, im) rows, or nullptr
+    // aligned FP16 (re, im) rows scaled by 1 / hs[k] (complex64 plans; the
+    // tensor-core contractions), and hs[k] = the power of two at or above
+    // ||h_k|| (every scaled entry below 1 in magnitude)
+    const __half2* Hh;
+    const float* hs;
     const double* nrmd;        // ||h_k||^2 in FP64
     const int* in_off;         // row k's offset in the caller's packed layout
     const int* vsort;          // V rows (K - nF), then all K rows, each by VR centre
@@ -107,8 +113,9 @@ cudaError_t kz_pack_rows(const float2* Hin, const int* in_off, const int4* rows,
                          int64_t total2, float2* Hc, __nv_bfloat162* Hb, cudaStream_t st);
 cudaError_t kz_pack_dense(const float2* Hd, int Nt, const int4* rows, const int* rptr, int K, float2* Hc,
                           __nv_bfloat162* Hb, cudaStream_t st);
+// Row norms; with Hh, also the scaled FP16 copy of every row and its scale hs.
 cudaError_t kz_row_norms(const float2* Hc, const int4* rows, const int* rptr, int K, double* out_d,
-                         float* out_f, cudaStream_t st);
+                         float* out_f, __half2* Hh, float* hs, cudaStream_t st);
 cudaError_t kz_gram(const float2* Hc, const int4* rows, const int* rptr, const int* xptr, const int* xidx, int K,
                     float2* G, cudaStream_t st);
 // Re-pack items of a batch from H_cat (item b's packed channel at
