@@ -1,4 +1,4 @@
-"""The tensor-core (TF32 correction form) AHK / VR-OAHK kernel against the FP64 oracle (GB300)."""
+"""The tensor-core (FP16 products, correction form) AHK / VR-OAHK kernel against the FP64 oracle (GB300)."""
 import numpy as np
 import pytest
 
@@ -50,7 +50,7 @@ def test_tc_converges_to_rzf(kp, algo, J, nrhs):
 @pytest.mark.parametrize("algo", ["ahk", "vr_oahk"])
 @pytest.mark.parametrize("T", [1, 2, 3])
 def test_tc_first_iterates_follow_the_oracle(kp, algo, T):
-    """Before any refresh the tensor-core iterates are the oracle's up to TF32
+    """Before any refresh the tensor-core iterates are the oracle's up to FP16
     rounding: a wrong fragment layout would miss by O(1)."""
     inst = ragged(seed=3, nrhs=9)
     ref = okz.solve(okz.System.from_instance(inst), inst.S, algo, tol=0.0, max_iter=T)
@@ -319,3 +319,85 @@ def test_tc_random_batch(kp, seed):
 
 
 NR = 13  # columns per channel in the random batches (not a multiple of the launch widths)
+
+
+def test_tc_row_scale_spread(kp):
+    """Rows scaled by factors from 0.1 to 10 (near and far users, 40 dB of
+    power between them): the FP16 copy scales each row by its own power of
+    two, so every row keeps FP16's precision; the tensor-core kernel reaches
+    the FP64 RZF in about the iterations of the FP32 kernel."""
+    import dataclasses
+    base = kzgen.make_instance(760, 40, 2048, vr_frac_range=(0.1, 0.4), snr_db=10.0, nrhs=16)
+    rng = np.random.default_rng(761)
+    c = 10.0 ** rng.uniform(-1.0, 1.0, size=base.K)
+    c[0], c[1] = 0.1, 10.0
+    rp = np.concatenate([[0], np.cumsum(base.vr_len.astype(np.int64))])
+    H = base.H_packed.copy()
+    for k in range(base.K):
+        H[rp[k]:rp[k + 1]] *= np.float32(c[k])
+    inst = dataclasses.replace(base, H_packed=H.astype(np.complex64))
+    ref = run(kp, inst, "vr_oahk", tol=1e-6, kernel="resident")
+    assert ref["converged"]
+    for J in (4, 8):
+        st, it, _ = _one_item_batch(kp, inst, J, 512, 1e-6)
+        iters = it["iters"].cpu().numpy()
+        assert st == 0, (J, st, iters.max(), ref["iters"].max())
+        assert iters.max() <= 1.25 * ref["iters"].max() + 16, (J, iters.max(), ref["iters"].max())
+        _check_rzf(inst, it, 1e-6)
+
+
+def test_tc_after_plan_update_matches_fresh_plan(kp):
+    """kz_plan_update rewrites the FP16 copy with the complex64 rows: the
+    tensor-core kernel on the updated plan equals it on a fresh plan, bit for
+    bit (a stale copy would change the inner iteration)."""
+    a = kzgen.make_instance(770, 48, 1024, vr_frac_range=(0.1, 0.4), snr_db=10.0, nrhs=8)
+    b = kzgen.make_instance(771, a.K, a.Nt, vr_override=(a.vr_offset, a.vr_len), nrhs=8, snr_db=10.0)
+    plan = kp.plan_from_instance(a)
+    kp.kz_plan_update(plan, torch.from_numpy(b.H_packed).cuda())
+    fresh = kp.plan_from_instance(b)
+    outs = []
+    for p in (plan, fresh):
+        o = kp.precode(p, kp.rhs_tensor(b.S), b.xi, algo="vr_oahk", tol=1e-7, max_iter=3000, rhs_per_cta=8,
+                       kernel="tc")
+        assert o["converged"]
+        outs.append(o)
+    assert torch.equal(outs[0]["x"], outs[1]["x"]) and torch.equal(outs[0]["iters"], outs[1]["iters"])
+    V, X = orz.rzf(b.dense(), b.xi, b.S)
+    assert np.all(orz.rel_err(outs[0]["x"].cpu().numpy().T.astype(np.complex128), X) <= TOL_X)
+
+
+def test_tc_after_batch_update_matches_fresh_plans(kp):
+    """kz_batch_update writes every item's FP16 copy with its norms: under the
+    tensor-core launch the updated batch equals a batch of fresh plans, bit
+    for bit."""
+    rng = np.random.default_rng(780)
+    insts = [kzgen.make_instance(781 + i, int(rng.integers(8, 80)), int(rng.choice([256, 640, 1500])),
+                                 vr_frac_range=(0.1, 0.4), nrhs=8) for i in range(6)]
+    new = [kzgen.make_instance(790 + i, inst.K, inst.Nt, vr_override=(inst.vr_offset, inst.vr_len), nrhs=8)
+           for i, inst in enumerate(insts)]
+
+    def items_for(src, plans):
+        return [dict(plan=p, s=kp.rhs_tensor(i.S), x=torch.zeros((8, i.Nt), dtype=torch.complex64, device="cuda"),
+                     v=torch.zeros((8, i.K), dtype=torch.complex64, device="cuda"),
+                     iters=torch.zeros(8, dtype=torch.int32, device="cuda"),
+                     resid=torch.zeros(8, dtype=torch.float64, device="cuda"), xi=i.xi) for i, p in zip(src, plans)]
+
+    old_items = items_for(insts, [kp.plan_from_instance(i) for i in insts])
+    b_old = kp.kz_batch_prepare(old_items, 8, "vr_oahk")
+    kp.kz_batch_update(b_old, torch.from_numpy(np.concatenate([i.H_packed for i in new])).cuda())
+    for it, i in zip(old_items, new):
+        it["s"].copy_(kp.rhs_tensor(i.S))
+    kp.kz_batch_rebind(b_old, [dict(it, xi=i.xi) for it, i in zip(old_items, new)])
+    kp.kz_batch_set_launch(b_old, "tc", 8, 512)
+    fresh_items = items_for(new, [kp.plan_from_instance(i) for i in new])
+    b_new = kp.kz_batch_prepare(fresh_items, 8, "vr_oahk")
+    kp.kz_batch_set_launch(b_new, "tc", 8, 512)
+    for b in (b_old, b_new):
+        st = torch.zeros(1, dtype=torch.int32, device="cuda")
+        kp.kz_precode_batched(b, "paper", 1e-7, 3000, 0, status=st)
+        torch.cuda.synchronize()
+        assert st.item() == 0
+    for a, c, i in zip(old_items, fresh_items, new):
+        assert torch.equal(a["x"], c["x"]) and torch.equal(a["iters"], c["iters"])
+        V, X = orz.rzf(i.dense(), i.xi, i.S)
+        assert np.all(orz.rel_err(a["x"].cpu().numpy().T, X) <= TOL_X)
