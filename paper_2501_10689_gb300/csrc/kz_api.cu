@@ -200,8 +200,9 @@ bool is_ahk_family(kz_algo a) { return a == KZ_AHK || a == KZ_VR_OAHK; }
 bool valid_algo(int a) { return a >= KZ_RK_ENERGY && a <= KZ_GK; }
 
 // Refresh period: the drift correction of C64, the correction-form refresh
-// of BF16_MIXED and of the tensor-core kernel (whose TF32 inner products
-// slow the iteration when the correction grows for longer).
+// of BF16_MIXED and of the tensor-core kernel (whose FP16 products slow the
+// iteration when the correction grows for longer; on the 512-channel batch
+// periods 7 to 10 are within 1% of each other).
 int default_refresh(kz_algo a, kz_prec p, bool tc = false) {
     if (is_ahk_family(a)) return tc ? 8 : (p == KZ_BF16_MIXED ? 6 : 16);
     return 512;

@@ -151,9 +151,9 @@ __device__ __forceinline__ void row_dot2(const KzInst& I, const int4* rows, cons
 // FP16 iterate of the tensor-core mode.  The correction m of the correction
 // form is stored per column as m / sigma_j in FP16 (re, im) pairs, sigma_j the
 // column's relative residual at the last refresh, so the stored values keep
-// the scale of the solution however small the correction gets; the MMAs read
-// ten mantissa bits of their operands either way (TF32).  Antenna pair
-// (n, n+1) of a column, n even: one 8-byte load.
+// the scale of the solution however small the correction gets; the MMAs
+// take it as stored (FP16 operands).  Antenna pair (n, n+1) of a column,
+// n even: one 8-byte load (as FP32 for the CUDA-core half-step).
 __device__ __forceinline__ float4 m16_pair(const __half2* p) {
     const uint2 raw = *reinterpret_cast<const uint2*>(p);
     const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
