@@ -54,10 +54,13 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     // sum of hs_i^2 |phi_i|^2 that scales phi for the FP16 products
     __shared__ float s_part[NW][4 * J];
     __shared__ float s_tot[4 * J];
-    __shared__ double s_partd[NW][J];
+    __shared__ float s_partd[NW][J];  // per-warp sums of |r|^2 of the true residual
     __shared__ double s_sn2[J];
+    __shared__ double s_thr[J];  // tol^2 ||s_j||^2
+    __shared__ float s_isn2[J];  // 1 / ||s_j||^2 (tensor-core mode: the storage scale)
+    __shared__ int s_conf[J];    // the true residual passed the test at the last refresh
     __shared__ float s_sn2f[J];  // ||s_j||^2 tol^2 for the tentative test
-    __shared__ double s_rn2[J];
+    __shared__ float s_rn2[J];
     __shared__ float s_gamma[J];
     __shared__ float s_kap[J];  // tensor-core mode: RMS of H^H D^-1 s_j
     __shared__ float s_sig[J];  // tensor-core mode: storage scale of column j of m
@@ -105,6 +108,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
     int* tptr_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE + 1) * sizeof(int)));
     int* tnv_s = reinterpret_cast<int*>(carve((size_t)(L.Ntp_max / KZ_TILE) * sizeof(int)));
     int* vs_s = TC ? reinterpret_cast<int*>(carve((size_t)L.K_max * sizeof(int))) : nullptr;
+    // correction form: CSR offsets of the overlap sets (the refresh's row passes)
+    int* xptr_s = CORR ? reinterpret_cast<int*>(carve((size_t)(L.K_max + 1) * sizeof(int))) : nullptr;
     float* hs_s = TC ? reinterpret_cast<float*>(carve((size_t)L.K_max * sizeof(float))) : nullptr;  // FP16 row scales
     // tensor-core V residual: every 8-row block's union interval is cut in
     // two parts (tasks); part 0 sums into p_s, part 1 into pb_s, and the two
@@ -163,19 +168,29 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
         // reduce-scatter, the s entries each lane needs fetched first.
         auto true_residual_pass = [&](bool store_b) {
             if constexpr (CORR) {
-                // one row per warp; lanes j < J own column j (its s entry is
-                // fetched before the row's sums)
+                // rows i and i + NW of a warp together (rows warp, warp + NW,
+                // warp + 2 NW, ... in that order); lanes j < J own column j
+                // (its s entries are fetched before the rows' sums)
                 float rpl = 0.f;
                 const int j = lane % J;
-                for (int i = warp; i < K; i += NW) {
+                for (int i0 = warp; i0 < K; i0 += 2 * NW) {
+                    const int i1 = i0 + NW < K ? i0 + NW : -1;
                     const bool mine = lane < J && j < ncols;
-                    const float2 sv = mine ? I.s[(size_t)(col0 + j) * K + i] : make_float2(0.f, 0.f);
-                    float2 hi, lo;
-                    gram_row_t<J>(I, i, q_s, W, hi, lo);
+                    const float2 sv0 = mine ? I.s[(size_t)(col0 + j) * K + i0] : make_float2(0.f, 0.f);
+                    const float2 sv1 = (mine && i1 >= 0) ? I.s[(size_t)(col0 + j) * K + i1] : make_float2(0.f, 0.f);
+                    float2 hi[2], lo[2];
+                    gram_rows_t<J>(I, xptr_s, i0, i1, q_s, W, hi, lo);
                     if (lane < J) {
-                        const float2 r = true_resid(sv, hi, lo, q_s[i * J + j], xi);
-                        rpl += r.x * r.x + r.y * r.y;
-                        if (store_b) b_s[i * J + j] = make_float2((sv.x - hi.x) - lo.x, (sv.y - hi.y) - lo.y);
+#pragma unroll
+                        for (int r = 0; r < 2; ++r) {
+                            const int i = r ? i1 : i0;
+                            if (i < 0) continue;
+                            const float2 sv = r ? sv1 : sv0;
+                            const float2 rr = true_resid(sv, hi[r], lo[r], q_s[i * J + j], xi);
+                            rpl += rr.x * rr.x + rr.y * rr.y;
+                            if (store_b)
+                                b_s[i * J + j] = make_float2((sv.x - hi[r].x) - lo[r].x, (sv.y - hi[r].y) - lo[r].y);
+                        }
                     }
                 }
                 if (lane < J) s_partd[warp][lane] = rpl;
@@ -248,6 +263,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             order_s[i] = I.order[i];
             if (TC) hs_s[i] = I.hs[i];
         }
+        if (CORR)
+            for (int i = tid; i <= K; i += NT) xptr_s[i] = I.xptr[i];
         for (int t2 = tid; t2 <= I.ntiles; t2 += NT) {
             tptr_s[t2] = I.tptr[t2];
             if (t2 < I.ntiles) tnv_s[t2] = I.tnv[t2];
@@ -373,6 +390,8 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
             if (lane == 0) {
                 s_sn2[warp] = a;
                 s_sn2f[warp] = (float)(a * L.tol * L.tol);
+                s_thr[warp] = a * L.tol * L.tol;
+                s_isn2[warp] = a > 0.0 ? (float)(1.0 / a) : 0.f;
             }
         }
         __syncthreads();
@@ -696,13 +715,14 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                 __syncthreads();
                 true_residual_pass(CORR);
                 __syncthreads();
-                if (tid < J) {  // the columns' squared residual norms, one thread each
-                    double a = 0.0;
+                if (tid < J) {  // the columns' squared residual norms and tests, one thread each
+                    float a = 0.f;
                     for (int w = 0; w < NW; ++w) a += s_partd[w][tid];
                     s_rn2[tid] = a;
+                    s_conf[tid] = (double)a <= s_thr[tid];
                     if (TC) {  // the next correction is about rho_j times the solution's scale
-                        const double rho = s_sn2[tid] > 0.0 ? sqrt(a / s_sn2[tid]) : 1.0;
-                        const float sg = (float)(rho * (double)s_kap[tid]);
+                        const float rho = s_isn2[tid] > 0.f ? sqrtf(a * s_isn2[tid]) : 1.f;
+                        const float sg = rho * s_kap[tid];
                         s_sig[tid] = (sg > 1e-30f && isfinite(sg)) ? sg : 1e-30f;
                     }
                 }
@@ -712,12 +732,12 @@ __global__ void __launch_bounds__(NW * 32, (J <= 2 ? 2 : 1) * (512 / (NW * 32)))
                     const int tested = CORR ? a2 : s_pending;
                     for (int j = 0; j < ncols; ++j) {
                         if (!((tested >> j) & 1) || !((a2 >> j) & 1)) continue;
-                        const double rn2 = s_rn2[j];
+                        const float rn2 = s_rn2[j];
                         if (!(rn2 == rn2) || isinf(rn2)) {
                             a2 &= ~(1 << j);
                             s_iters[j] = t - s_wait[j];
                             kz_flag(L.status, KZ_STATUS_BIT_NUMERIC);
-                        } else if (rn2 <= L.tol * L.tol * s_sn2[j]) {
+                        } else if (s_conf[j]) {
                             a2 &= ~(1 << j);
                             s_iters[j] = t - s_wait[j];
                         } else if (!oahk && t >= L.max_iter) {
@@ -1091,11 +1111,11 @@ int occ_nw(int J, int nw, size_t smem) {
 }  // namespace
 
 size_t kz_smem_ahk(int J, int Ntp, int K, int prec) {
-    (void)prec;
     auto r16 = [](size_t b) { return (b + 15) & ~(size_t)15; };
     return r16((size_t)J * Ntp * sizeof(float2)) + 3 * r16((size_t)K * J * sizeof(float2)) +
            r16((size_t)K * sizeof(float)) + r16((size_t)K * sizeof(int4)) + 3 * r16((size_t)K * sizeof(int)) +
-           r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int));
+           r16((size_t)(Ntp / KZ_TILE + 1) * sizeof(int)) + r16((size_t)(Ntp / KZ_TILE) * sizeof(int)) +
+           (prec == KZ_BF16_MIXED ? r16((size_t)(K + 1) * sizeof(int)) : 0);  // correction form: xptr
 }
 
 size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow) {
@@ -1103,6 +1123,7 @@ size_t kz_smem_ahk_tc(int J, int m_elems, int Ntp_max, int K, int trow) {
     const size_t ntask = 2 * (size_t)((K + 7) / 8);
     return kz_smem_ahk(J, Ntp_max, K, KZ_C64) - r16((size_t)J * Ntp_max * sizeof(float2)) +
            r16((size_t)m_elems * sizeof(__half2)) + r16((size_t)K * sizeof(int)) + r16((size_t)K * sizeof(float)) +
+           r16((size_t)(K + 1) * sizeof(int)) +
            r16((size_t)K * J * sizeof(float2)) + r16(ntask * sizeof(int4)) + 2 * r16(ntask * sizeof(int)) +
            r16((size_t)trow * sizeof(unsigned short));
 }

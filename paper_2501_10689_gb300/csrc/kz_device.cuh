@@ -428,53 +428,80 @@ __device__ __forceinline__ void row_dot_c2(const KzInst& I, const int4* rows, co
 // (H H^H q)_i = sum over l in X_i of G_il q_l through the Gram matrix on the
 // overlap pattern (the VRs of rows outside X_i are disjoint from row i's, so
 // their entries are zero): the same sum as h_i . (H^H q) from one pass over
-// the row's overlap set instead of its VR.  Lane (slot, j) = (lane / J,
-// lane % J) takes column j of every (32 / J)-th entry: the warp loads 32
-// entries (index and G value) at a time, coalesced, and hands them round by
-// shuffles, so the q reads of a pass hit consecutive shared-memory words.
-// FP32 complex products; the 32 / J lanes of a column are then added with
-// compensated sums.  Every lane returns hi + lo for its column j (columns
-// j >= jn are not read and return 0).
+// the row's overlap set instead of its VR, for two rows i0 and i1 of a warp
+// at once (i1 < 0: none).  Lane (slot, j) = (lane / J, lane % J) takes column
+// j of every (32 / J)-th entry: the warp loads 32 entries (index and G value)
+// at a time, coalesced, and hands them round by shuffles, so the q reads of a
+// pass hit consecutive shared-memory words.  The loads of up to four such
+// groups of 32 entries of both rows are in flight together (a row's overlap
+// set rarely has more than 128 entries, so one L2 round trip per two rows);
+// xptr: the CSR offsets of the overlap sets (shared memory).  FP32 complex
+// products, each row's entries added in list order; the 32 / J lanes of a
+// column are then added with compensated sums.  Every lane returns hi + lo
+// for its column j of each row (columns j >= jn are not read and return 0).
 template <int J>
-__device__ __forceinline__ void gram_row_t(const KzInst& I, int i, const float2* __restrict__ q_s, int jn,
-                                           float2& hi, float2& lo) {
+__device__ __forceinline__ void gram_rows_t(const KzInst& I, const int* xptr, int i0, int i1,
+                                            const float2* __restrict__ q_s, int jn, float2 (&hi)[2],
+                                            float2 (&lo)[2]) {
     constexpr int EPP = 32 / J;  // entries per pass
+    constexpr int CH = 4;        // groups of 32 entries of a row loaded together
     const int lane = threadIdx.x & 31, slot = lane / J, j = lane % J;
-    float ax = 0.f, ay = 0.f;
-    const int e0 = __ldg(I.xptr + i), e1 = __ldg(I.xptr + i + 1);
-    for (int base = e0; base < e1; base += 32) {
-        const int e = base + lane;
-        int l = 0;
-        float2 g = make_float2(0.f, 0.f);
-        if (e < e1) {
-            l = __ldg(I.xidx + e);
-            g = __ldg(I.G + e);
-        }
+    float ax[2] = {0.f, 0.f}, ay[2] = {0.f, 0.f};
+    int eb[2], ee[2];
+    eb[0] = xptr[i0];
+    ee[0] = xptr[i0 + 1];
+    eb[1] = i1 >= 0 ? xptr[i1] : 0;
+    ee[1] = i1 >= 0 ? xptr[i1 + 1] : 0;
+    for (int round = 0; eb[0] + 32 * CH * round < ee[0] || eb[1] + 32 * CH * round < ee[1]; ++round) {
+        int l[2][CH];
+        float2 g[2][CH];
 #pragma unroll
-        for (int p = 0; p < J; ++p) {
-            const int src = p * EPP + slot;
-            const int ls = __shfl_sync(KZ_FULL, l, src);
-            const float gx = __shfl_sync(KZ_FULL, g.x, src), gy = __shfl_sync(KZ_FULL, g.y, src);
-            if (base + src < e1 && j < jn) {
-                const float2 q = q_s[ls * J + j];
-                ax = fmaf(gx, q.x, fmaf(-gy, q.y, ax));
-                ay = fmaf(gx, q.y, fmaf(gy, q.x, ay));
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int e = eb[r] + 32 * (CH * round + c) + lane;
+                l[r][c] = 0;
+                g[r][c] = make_float2(0.f, 0.f);
+                if (e < ee[r]) {
+                    l[r][c] = __ldg(I.xidx + e);
+                    g[r][c] = __ldg(I.G + e);
+                }
             }
-        }
-    }
-    float cx = 0.f, cy = 0.f;
 #pragma unroll
-    for (int o = J; o < 32; o <<= 1) {
-        const float rx = __shfl_xor_sync(KZ_FULL, ax, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
-        const float ry = __shfl_xor_sync(KZ_FULL, ay, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
-        float e;
-        two_sum(ax, rx, ax, e);
-        cx = (cx + rcx) + e;
-        two_sum(ay, ry, ay, e);
-        cy = (cy + rcy) + e;
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int b0 = eb[r] + 32 * (CH * round + c);
+                if (b0 >= ee[r]) break;  // the same in every lane
+#pragma unroll
+                for (int p = 0; p < J; ++p) {
+                    const int src = p * EPP + slot;
+                    const int ls = __shfl_sync(KZ_FULL, l[r][c], src);
+                    const float gx = __shfl_sync(KZ_FULL, g[r][c].x, src), gy = __shfl_sync(KZ_FULL, g[r][c].y, src);
+                    if (b0 + src < ee[r] && j < jn) {
+                        const float2 q = q_s[ls * J + j];
+                        ax[r] = fmaf(gx, q.x, fmaf(-gy, q.y, ax[r]));
+                        ay[r] = fmaf(gx, q.y, fmaf(gy, q.x, ay[r]));
+                    }
+                }
+            }
     }
-    hi = make_float2(ax, ay);
-    lo = make_float2(cx, cy);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        float sx = ax[r], sy = ay[r], cx = 0.f, cy = 0.f;
+#pragma unroll
+        for (int o = J; o < 32; o <<= 1) {
+            const float rx = __shfl_xor_sync(KZ_FULL, sx, o), rcx = __shfl_xor_sync(KZ_FULL, cx, o);
+            const float ry = __shfl_xor_sync(KZ_FULL, sy, o), rcy = __shfl_xor_sync(KZ_FULL, cy, o);
+            float e;
+            two_sum(sx, rx, sx, e);
+            cx = (cx + rcx) + e;
+            two_sum(sy, ry, sy, e);
+            cy = (cy + rcy) + e;
+        }
+        hi[r] = make_float2(sx, sy);
+        lo[r] = make_float2(cx, cy);
+    }
 }
 
 // b - h_i . m - xi q from row_dot_c's hi + lo: b - hi is exact when the two
