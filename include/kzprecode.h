@@ -143,7 +143,10 @@ typedef struct kz_batch kz_batch;
  * set F as a maximum independent set of the overlap graph (eq. (max_set);
  * exact for contiguous VRs by the earliest-end rule), the antenna-tile
  * covering lists and the device copies of H in the solver's aligned layout
- * (complex64, plus BF16 when prec == KZ_BF16_MIXED).
+ * (each row's VR widened to multiples of four antennas, zero-filled):
+ * complex64, plus BF16 when prec == KZ_BF16_MIXED, plus, when prec ==
+ * KZ_C64, an FP16 copy for the tensor-core kernel (each row scaled by a power
+ * of two at or above its norm; 4 bytes per stored entry against 8).
  *   K, Nt: users and antennas, 1 <= K < Nt (Sec. II).
  *   vr_offset, vr_len: host int32[K]; every VR must satisfy
  *     vr_len >= 1 and 0 <= vr_offset, vr_offset + vr_len <= Nt.
@@ -168,7 +171,8 @@ kz_status kz_plan_dense(kz_plan** out, int32_t K, int32_t Nt, const int32_t* vr_
 
 /* Replace the channel of an existing plan (same K, Nt and VRs): re-pack
  * H_packed (device, layout as in kz_plan_create, 8-byte aligned) into the
- * plan's aligned copy (and BF16 copy) and recompute the row norms, as kernels
+ * plan's aligned copy (and its BF16 or FP16 copy) and recompute the row norms
+ * and the inner products of overlapping rows, as kernels
  * on `stream`; nothing else of the plan changes and no host synchronisation
  * happens, so prepared batches that name the plan stay valid.  Calls that use
  * the plan must be ordered after this one on the stream. */
