@@ -19,11 +19,12 @@ cites the part of the paper it follows:
                  selection (the paper does not name one).
 * ``sinr``       per-user SINR and spectral efficiency (eq. (rate)).
 * ``precoder``   subarray-wise precoder assembly (eq. (precoding2)) and beta.
-* ``flops``      the FLOP counts of Table I (parity unpinned: accounting).
+* ``flops``      the FLOP counts of Table I (partly pinned: accounting).
 
 Parity unpinned: ``kaczmarz.vr_oahk``'s a-priori rate of Theorem 5 (the
 statement is iterate-dependent and garbled; only the Lemma 3 identities,
-monotone error decrease and convergence to RZF are pinned) and ``flops``
-(Table I's accounting formulas, transcribed as printed).
+monotone error decrease and convergence to RZF are pinned) and the
+lower-order terms of ``flops``' RZF, URK, SWOR-ERK and VR-OAHK rows (Table
+I's accounting conventions, transcribed as printed).
 """
 from . import rng, sets, rzf, kaczmarz, sinr, precoder, flops  # noqa: F401

@@ -8,8 +8,12 @@ subarray, eq. (precoding2)), M (VR length; the table's |M| in the VR rows is
 read as |Gamma|, the number of visible antennas), X (|X_k|), F and V (sizes of
 the orthogonal set and its complement).
 
-Parity unpinned: these are accounting formulas; nothing outside the table
-fixes their values, so they are only checked against a second transcription.
+Pinned by what lies outside the table: with full visibility (|Gamma| = Nt,
+|X| = |Q| = K) the VR-OGRK row equals the GK row, and the leading terms that
+Sec. V states hold (8 Nt K^2 against 8 Nt K |Q| for the precoder matrix,
+8 Nt K against 8 |Gamma| |X| for the residuals of an iteration).  Parity
+unpinned for the lower-order terms of the RZF, URK, SWOR-ERK and VR-OAHK
+rows: they follow counting conventions the paper does not state.
 """
 
 
